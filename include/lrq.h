@@ -1,0 +1,181 @@
+/*
+ * lrq.h -- C ABI of liblrq, the GB300 (sm_103a) library for batched
+ * candidate scoring in low-rank discrete quadratic maximisation
+ * (arXiv 2602.20376, "Exploiting Low-Rank Objective Structure in Discrete
+ * Quadratic Optimization").
+ *
+ * Problem (Sec. 1, Eq. 1-2): maximise z^H Q z over z in A_K^n, where
+ * A_K = { exp(2 pi i k / K) : k = 0..K-1 } and Q ~= V V^H, V in C^{n x r}.
+ * With Q = V V^H the objective is ||V^H z||^2 (Sec. 2.2, Eq. 3).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Every function returns an lrq_status (0 = LRQ_OK).  No C++ exception
+ *   crosses the ABI.  On failure lrq_last_error() returns a message for the
+ *   calling thread.
+ * - Argument errors (sizes, null pointers, unsupported K or r) are detected
+ *   on the host before any launch and return LRQ_EINVAL or
+ *   LRQ_EUNSUPPORTED; nothing is launched in that case.
+ * - Calls are asynchronous on `stream` (a cudaStream_t passed as void*; NULL
+ *   means the legacy default stream).  Errors found on the device (non-finite
+ *   input, a bounded wait that ran out) are written as an lrq_status into
+ *   `*dev_status` (a device int32 the caller zeroes and reads after
+ *   synchronising); the first error wins.  dev_status may not be NULL where a
+ *   signature has it.
+ * - The caller owns every buffer.  All array arguments are DEVICE pointers
+ *   unless a comment says "host".  The library allocates no device memory:
+ *   scratch space is the caller's `ws` of `ws_bytes` bytes, sized by the
+ *   matching *_workspace_size query; ws must be 256-byte aligned.
+ * - Complex arrays are interleaved (re, im): complex64 = 2 x float,
+ *   complex128 = 2 x double (the layout of torch.complex64 / complex128).
+ *   Matrices are row-major and contiguous: V is n x r (row i = V_{i,:}),
+ *   C is S x r (row s = candidate direction c_s).
+ * - Assignments z are returned as codes k_i in [0, K), z_i = exp(2 pi i k_i/K),
+ *   one uint8 per coordinate.
+ * - The decision rule (Sec. 3, Eq. 9) maps w = V_i c to the nearest K-th root
+ *   of unity in angle.  Exactly on a boundary several roots are equally
+ *   near; the library then picks one of them (which one is unspecified).
+ */
+#ifndef LRQ_H
+#define LRQ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  LRQ_OK = 0,
+  LRQ_EINVAL = 1,        /* invalid argument, or non-finite input found on the device */
+  LRQ_EUNSUPPORTED = 2,  /* valid but unsupported (K, r, size or mode)                */
+  LRQ_ECUDA = 3,         /* a CUDA runtime call failed                                 */
+  LRQ_ETIMEOUT = 4,      /* a bounded device-side wait ran out                         */
+  LRQ_ENOCONV = 5,       /* an iterative solver did not converge                       */
+  LRQ_EWORKSPACE = 6     /* ws is NULL, misaligned or smaller than required            */
+} lrq_status;
+
+typedef enum {
+  LRQ_MODE_FP32 = 0,     /* CUDA-core FP32 scoring                                      */
+  LRQ_MODE_BF16_TC = 1   /* tcgen05 tensor-core scoring: BF16 operands, FP32 accumulate */
+} lrq_mode;
+
+/* Human-readable name of a status code (static string, never NULL). */
+const char* lrq_status_string(int status);
+
+/* Message describing the most recent failure on the calling thread
+ * (static per-thread buffer; empty string if none). */
+const char* lrq_last_error(void);
+
+/* ABI version of this header (incremented on any signature change). */
+int lrq_abi_version(void);
+
+/* --------------------------------------------------------------------------
+ * lrq_sample_directions -- uniform directions on the unit sphere of C^r.
+ *
+ * Sec. 4.2 (sampling candidates) and App. E (Lemma "innerIsBeta"):
+ * c = Z / ||Z|| with Z ~ CN(0, I_r) is uniform on the complex sphere.
+ * Z is drawn with the counter-based generator Philox4x32-10 (Salmon et al.,
+ * SC'11): component j of candidate s uses counter (lo32(s), hi32(s), j, 0)
+ * and key (lo32(seed), hi32(seed)); output words (0,1) and (2,3) give two
+ * 53-bit uniforms u1, u2 = (top 53 bits + 0.5) / 2^53, and
+ * Z_j = sqrt(-ln u1) * exp(2 pi i u2) (Box-Muller, Re and Im ~ N(0, 1/2)).
+ * The normalisation runs in FP64; the result is rounded once to complex64.
+ *
+ *   C_out : S x r complex64 (device), written.
+ *   1 <= r <= 64, S >= 0 (S = 0 launches nothing).
+ * ------------------------------------------------------------------------ */
+int lrq_sample_directions(uint64_t seed, int64_t S, int r, void* C_out, void* stream);
+
+/* --------------------------------------------------------------------------
+ * lrq_sample_score -- score S candidate directions and select the top m.
+ *
+ * For every direction c_s (Sec. 4.2, Eq. 10):
+ *   w_i = V_i c_s                (i = 1..n)
+ *   k_i = nearest root in angle  (Sec. 3, Eq. 9)
+ *   f_s = || V^H z(c_s) ||^2
+ * then the m best (f_s, s) pairs, f descending, ties to the lower s
+ * ("returns only the best candidate found", Sec. 5; best-of-S, Sec. 4.2).
+ *
+ *   V        : n x r complex64 (device).  Must be finite (checked on the
+ *              device; a non-finite entry sets *dev_status = LRQ_EINVAL).
+ *   n, r, K  : n >= 1; K in [2, 64]; r in [1, 8].
+ *   C        : S x r complex64 (device).  If generate_C != 0 the call first
+ *              fills C exactly as lrq_sample_directions(seed, S, r, C) would;
+ *              otherwise C is read as given (rows need not be unit norm).
+ *   S        : number of candidates, S >= 1, S < 2^31.
+ *   mode     : LRQ_MODE_FP32 or LRQ_MODE_BF16_TC.  The BF16 mode rounds the
+ *              operands of the two contractions (w = V c and the per-class
+ *              sums of V^H z) to bfloat16 and accumulates in FP32 (partial
+ *              sums are combined in FP64); it supports K <= 8 and r <= 8.
+ *              FP32 mode computes w and V^H z in FP32 with FP64 partials.
+ *   top_m    : 1 <= top_m <= 512 and top_m <= S.
+ *   scores_out  : optional S floats (device) receiving f_s; may be NULL.
+ *   top_idx_out : top_m int64 (device): candidate indices, best first.
+ *   top_f_out   : top_m floats (device): their scores.
+ *   ws, ws_bytes: scratch, at least lrq_sample_score_workspace_size(...).
+ * ------------------------------------------------------------------------ */
+int lrq_sample_score_workspace_size(int64_t n, int r, int K, int64_t S, int mode, int top_m,
+                                    size_t* bytes /* host */);
+int lrq_sample_score(const void* V, int64_t n, int r, int K, void* C, int generate_C, uint64_t seed,
+                     int64_t S, int mode, int top_m, float* scores_out, int64_t* top_idx_out,
+                     float* top_f_out, void* ws, size_t ws_bytes, int32_t* dev_status, void* stream);
+
+/* --------------------------------------------------------------------------
+ * lrq_rescore -- FP64 re-scoring of selected candidates.
+ *
+ * For each of the m candidates idx[t] (rows of C), recompute w = V c, the
+ * decision rule (Eq. 9) and f = || V^H z ||^2 (Eq. 10) to FP64 accuracy from
+ * the complex64 V and C upcast exactly; the decisions are exact FP64
+ * decisions.  Also returns the best of the m (largest f, ties to the earlier
+ * position t), i.e. the winner of the "top-m candidates are re-scored"
+ * step.
+ *
+ *   idx      : m int64 (device), each in [0, S) (checked on the device).
+ *   f_out    : m doubles (device).
+ *   z_out    : optional m x n uint8 codes (device); may be NULL.
+ *   best_out : 1 int64 (device): idx[t*] of the best candidate.
+ *   best_f_out : 1 double (device): its f.
+ *   1 <= m <= 4096; K in [2, 64]; r in [1, 8].
+ * ------------------------------------------------------------------------ */
+int lrq_rescore_workspace_size(int64_t n, int r, int m, size_t* bytes /* host */);
+int lrq_rescore(const void* V, int64_t n, int r, int K, const void* C, int64_t S, const int64_t* idx,
+                int m, double* f_out, uint8_t* z_out, int64_t* best_out, double* best_f_out, void* ws,
+                size_t ws_bytes, int32_t* dev_status, void* stream);
+
+/* --------------------------------------------------------------------------
+ * lrq_cut_count -- exact Max-K-Cut value of an assignment on a graph.
+ *
+ * Sec. 1: for K = 3 and Q the graph Laplacian the problem is Max-3-Cut.
+ * cut(z) = #{ undirected edges {i, j} : k_i != k_j }, counted exactly in
+ * int64 from a symmetric CSR adjacency (each edge stored in both rows; self
+ * loops never count).  With unit weights and K = 3, z^H L z = 3 cut(z),
+ * since |z_i - z_j|^2 is 3 for different labels and 0 otherwise.
+ *
+ *   rowptr : n+1 int32 (device), colidx : rowptr[n] int32 (device),
+ *   z      : n uint8 codes (device), cut_out : 1 int64 (device), written.
+ * ------------------------------------------------------------------------ */
+int lrq_cut_count(const int32_t* rowptr, const int32_t* colidx, int64_t n, const uint8_t* z,
+                  int64_t* cut_out, void* stream);
+
+/* --------------------------------------------------------------------------
+ * Measurement hooks (no counterpart in the paper).
+ *
+ * lrq_set_timing_events: for the calling thread, makes every later scoring
+ * call (lrq_sample_score) record `start_event` just before and `stop_event`
+ * just after its main scoring kernel, on the call's stream.  Both are
+ * cudaEvent_t handles passed as void*, created by the caller; NULL, NULL
+ * turns the hook off.  Lets a benchmark time the dominant kernel alone.
+ *
+ * lrq_kernel_launches: number of CUDA kernels this library has launched in
+ * the process so far (all threads).
+ * ------------------------------------------------------------------------ */
+int lrq_set_timing_events(void* start_event, void* stop_event);
+uint64_t lrq_kernel_launches(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LRQ_H */

@@ -1,0 +1,712 @@
+// k_score_tc.cu -- tensor-core (tcgen05 + TMEM + TMA) candidate scoring.
+//
+// The scoring of Sec. 4.2, Eq. 10 is cast as two contractions per
+// (128-candidate tile, coordinate tile):
+//
+// GEMM1 (boundary projections).  The augmented real matrix of Eq. 6 has one
+// row per (coordinate i, boundary m): [Im(rho_m V_i), Re(rho_m V_i)] with
+// rho_m = exp(-i theta_m), theta_m = pi(2m+1)/K, m < B_K (Definition 2.1).
+// Against c~ = [Re c; Im c] a row gives p_m = Im(rho_m V_i c), whose sign says
+// on which side of decision boundary m the value w_i = V_i c lies.  So
+//   D1[s, (m, i)] = sum_k C~[s, k] * Vaug[(m, i), k]     (M = 128, K = 2r -> 16)
+// and the decision rule (Sec. 3, Eq. 9) becomes a sign test per row.
+//
+// Sector rounding in the epilogue.  With N_m the sign mask of p_m:
+//   odd K  : class k in 1..K-1 iff p_{k-1} > 0 and p_k < 0  -> indicator 1/0
+//   even K : z = sum_m beta_m sign(p_m), beta_m = (w^{m+1} - w^m)/2   -> +-1
+// (w = exp(2 pi i/K)).  Indicators are exact in BF16; pairs of rows are
+// turned into packed BF16 words with byte permutes (sign replication) and
+// one 3-input logic op -- no trigonometry, no branches.
+//
+// GEMM2 (per-class sums).  V^H z = T + sum_k (w^k - 1) P_k (odd K, T the
+// column sum of conj(V)) or sum_m beta_m S_m (even K), where P_k / S_m are
+// sums of conj(V_i) selected or signed by the indicators:
+//   D2[s, :] += sum_{(g, i)} Ind[s, (g, i)] * B2[(g, i), :]   (N = 16 >= 2r)
+// with B2 rows the real form of beta_g conj(V_i).  D2 accumulates in TMEM
+// (FP32) for at most `flush` tiles, then is folded into FP32 two-sum
+// registers (error-free) and written as FP64 partials per coordinate chunk.
+//
+// Pipeline (one CTA per SM, persistent over (chunk, candidate tile) items):
+//   warp 0  : TMA producer (augmented rows + B2 rows per coordinate tile,
+//             directions per item), ring of kStages shared-memory stages;
+//   warp 1  : TMEM allocation and MMA issue (one elected thread);
+//   warps 4+: NE epilogue warpgroups; each reads its slice of the D1 tile
+//             from TMEM, builds indicator words, stores them to shared memory
+//             as GEMM2's A operand; warpgroup 0 also folds the D2 partials.
+// D1 and the indicator buffers are double-buffered so GEMM1 of tile t+1 and
+// GEMM2 of tile t-1 run on the tensor core while tile t is being rounded.
+// Every wait is bounded; on expiry the kernel records LRQ_ETIMEOUT, drains
+// its in-flight copies and MMAs, frees TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "lrq_device.cuh"
+#include "lrq_internal.h"
+#include "ptx_sm100.cuh"
+
+namespace lrq {
+
+constexpr int kTcM = 128;
+constexpr int kTcStages = 8;
+constexpr int kTcFlush = 64;
+constexpr int kTcNE = 2;  // epilogue warpgroups
+constexpr long long kWaitLimit = 2000000000LL;
+
+template <int K>
+struct TcShape {
+  static constexpr int BK = (K % 2 == 0) ? K / 2 : K;
+  static constexpr int G = (K % 2 == 0) ? K / 2 : K - 1;
+  static constexpr int ROWS = (BK <= 3) ? 64 : 32;
+  static constexpr int N1 = BK * ROWS;   // GEMM1 N
+  static constexpr int KD2 = G * ROWS;   // GEMM2 reduction length per tile
+  static_assert(N1 % 16 == 0 && N1 <= 256, "GEMM1 N");
+  static_assert(KD2 % 16 == 0, "GEMM2 K");
+};
+
+constexpr int align1k(int x) { return (x + 1023) / 1024 * 1024; }
+
+template <int K, int KCH>
+struct TcLayout {
+  using Sh = TcShape<K>;
+  static constexpr int N2R = (KCH == 1) ? 8 : 16;         // B2 rows stored per K-chunk
+  static constexpr int B2ROWS = Sh::KD2 / 8 * N2R;        // 16-byte rows of B2 per tile
+  static constexpr int B2BOX = (B2ROWS <= 256) ? B2ROWS : B2ROWS / 2;
+  static_assert(B2ROWS % B2BOX == 0 && B2BOX <= 256, "B2 box");
+  static constexpr int B1_BYTES = Sh::N1 * 16 * KCH;
+  static constexpr int B2_BYTES = B2ROWS * 16;
+  static constexpr int B1_OFF_IN_STAGE = 0;
+  static constexpr int B2_OFF_IN_STAGE = align1k(B1_BYTES);
+  static constexpr int STAGE_BYTES = align1k(B2_OFF_IN_STAGE + B2_BYTES);
+  static constexpr uint32_t STAGE_TX = B1_BYTES + B2_BYTES;
+  static constexpr int A1_BYTES = kTcM * 16 * KCH;
+  static constexpr int A2_BYTES = kTcM * Sh::KD2 * 2;
+  static constexpr int ZERO_BYTES = 4096;
+  static constexpr int STAGES_OFF = 0;
+  static constexpr int A1_OFF = STAGES_OFF + kTcStages * STAGE_BYTES;
+  static constexpr int A2_OFF = A1_OFF + align1k(2 * A1_BYTES);
+  static constexpr int ZERO_OFF = A2_OFF + align1k(2 * A2_BYTES);
+  static constexpr int BAR_OFF = ZERO_OFF + ZERO_BYTES;
+  static constexpr int NBARS = 2 * kTcStages + 16 + 1;  // stage pairs, 8 double-buffered pairs, drain
+  static constexpr int USED = BAR_OFF + NBARS * 8 + 16;
+  // at least 120 KB so that two CTAs never share an SM (each holds all 512
+  // TMEM columns)
+  static constexpr int TOTAL = USED < 120 * 1024 ? 120 * 1024 : USED;
+  static_assert(Sh::N1 * 16 <= ZERO_BYTES && kTcM * 16 <= ZERO_BYTES && Sh::KD2 * 16 <= ZERO_BYTES, "zero pad");
+  static_assert(TOTAL <= 227 * 1024, "shared memory");
+};
+
+struct TcParams {
+  int64_t n_tiles;
+  int64_t c_tiles;
+  int64_t tiles_per_chunk;
+  int64_t num_items;
+  int64_t S_pad;
+  int r;
+  int flush;
+};
+
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
+  s = a + b;
+  float bb = s - a;
+  e = (a - (s - bb)) + (b - bb);
+}
+
+template <int RPE>
+__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t* v) {
+  if constexpr (RPE == 32) {
+    ptx::tmem_ld_x32(taddr, v);
+  } else {
+    static_assert(RPE == 16, "slice width");
+    uint32_t (&vv)[16] = *reinterpret_cast<uint32_t(*)[16]>(v);
+    ptx::tmem_ld_x16(taddr, vv);
+  }
+}
+
+template <int K, int KCH>
+__global__ void __launch_bounds__(128 * (1 + kTcNE), 1)
+    score_tc_kernel(const __grid_constant__ CUtensorMap tm_vt, const __grid_constant__ CUtensorMap tm_b2,
+                    const __grid_constant__ CUtensorMap tm_ct, TcParams prm, double* __restrict__ partial,
+                    int32_t* status) {
+  using Sh = TcShape<K>;
+  using L = TcLayout<K, KCH>;
+  constexpr int ROWS = Sh::ROWS;
+  constexpr int N1 = Sh::N1;
+  constexpr int BK = Sh::BK;
+  constexpr int G = Sh::G;
+  constexpr int RPE = ROWS / kTcNE;
+  constexpr uint32_t D1_COL0 = 32;  // D2 double buffer occupies columns 0..31
+
+  extern __shared__ __align__(1024) uint8_t smem[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+  uint64_t* full_b = bars;
+  uint64_t* empty_b = bars + kTcStages;
+  uint64_t* a1_full = bars + 2 * kTcStages;
+  uint64_t* a1_empty = a1_full + 2;
+  uint64_t* d1_full = a1_full + 4;
+  uint64_t* d1_empty = a1_full + 6;
+  uint64_t* a2_full = a1_full + 8;
+  uint64_t* a2_empty = a1_full + 10;
+  uint64_t* d2_full = a1_full + 12;
+  uint64_t* d2_empty = a1_full + 14;
+  uint64_t* drain_bar = a1_full + 16;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + L::NBARS);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+
+  const int warp = threadIdx.x >> 5;
+  const int lane = threadIdx.x & 31;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < kTcStages; ++s) {
+      ptx::mbar_init(&full_b[s], 1);
+      ptx::mbar_init(&empty_b[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      ptx::mbar_init(&a1_full[b], 1);
+      ptx::mbar_init(&a1_empty[b], 1);
+      ptx::mbar_init(&d1_full[b], 1);
+      ptx::mbar_init(&d1_empty[b], kTcNE * 128);
+      ptx::mbar_init(&a2_full[b], kTcNE * 128);
+      ptx::mbar_init(&a2_empty[b], 1);
+      ptx::mbar_init(&d2_full[b], 1);
+      ptx::mbar_init(&d2_empty[b], 128);
+    }
+    ptx::mbar_init(drain_bar, 1);
+    *abort_flag = 0;
+    ptx::fence_mbar_init();
+  }
+  {
+    uint4* z = reinterpret_cast<uint4*>(smem + L::ZERO_OFF);
+    for (int i = threadIdx.x; i < L::ZERO_BYTES / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+  }
+  ptx::fence_proxy_async_smem();
+  if (warp == 0 && lane == 0) {
+    ptx::tma_prefetch_desc(&tm_vt);
+    ptx::tma_prefetch_desc(&tm_b2);
+    ptx::tma_prefetch_desc(&tm_ct);
+  }
+  if (warp == 1) {
+    ptx::tmem_alloc(tmem_slot, 512);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+  const uint32_t smem_base = ptx::smem_u32(smem);
+
+  const int64_t c_tiles = prm.c_tiles;
+  const int64_t tpc = prm.tiles_per_chunk;
+  const int F = prm.flush;
+
+  auto give_up = [&]() {
+    *abort_flag = 1;
+    dev_fail(status, LRQ_ETIMEOUT);
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------------------ producer
+    uint32_t issued = 0, a1_issued = 0;
+    if (lane == 0) {
+      uint32_t stage = 0, sphase = 0;
+      bool ok = true;
+      for (int64_t item = blockIdx.x; item < prm.num_items && ok; item += gridDim.x) {
+        const int64_t chunk = item / c_tiles, ct = item % c_tiles;
+        const int64_t t0 = chunk * tpc, t1 = min(prm.n_tiles, t0 + tpc);
+        const uint32_t ab = a1_issued & 1u;
+        if (!ptx::mbar_wait(&a1_empty[ab], ((a1_issued >> 1) & 1u) ^ 1u, abort_flag, kWaitLimit)) {
+          give_up();
+          break;
+        }
+        ptx::mbar_arrive_expect_tx(&a1_full[ab], L::A1_BYTES);
+        for (int ch = 0; ch < KCH; ++ch)
+          ptx::tma_load_2d(smem + L::A1_OFF + ab * L::A1_BYTES + ch * kTcM * 16, &tm_ct, 0,
+                           static_cast<int>((ct * KCH + ch) * kTcM), &a1_full[ab]);
+        ++a1_issued;
+        for (int64_t t = t0; t < t1; ++t) {
+          if (!ptx::mbar_wait(&empty_b[stage], sphase ^ 1u, abort_flag, kWaitLimit)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          uint8_t* st = smem + L::STAGES_OFF + stage * L::STAGE_BYTES;
+          ptx::mbar_arrive_expect_tx(&full_b[stage], L::STAGE_TX);
+          for (int ch = 0; ch < KCH; ++ch)
+            ptx::tma_load_2d(st + L::B1_OFF_IN_STAGE + ch * N1 * 16, &tm_vt, 0,
+                             static_cast<int>((t * KCH + ch) * N1), &full_b[stage]);
+          for (int p = 0; p < L::B2ROWS; p += L::B2BOX)
+            ptx::tma_load_2d(st + L::B2_OFF_IN_STAGE + p * 16, &tm_b2, 0, static_cast<int>(t * L::B2ROWS + p),
+                             &full_b[stage]);
+          ++issued;
+          if (++stage == kTcStages) {
+            stage = 0;
+            sphase ^= 1u;
+          }
+        }
+      }
+      // drain: every issued copy must have landed before the CTA exits
+      for (uint32_t s = 0; s < kTcStages && s < issued; ++s) {
+        uint32_t cnt = issued / kTcStages + (s < issued % kTcStages ? 1u : 0u);
+        volatile int never = 0;
+        ptx::mbar_wait(&full_b[s], (cnt - 1) & 1u, &never, kWaitLimit);
+      }
+      for (uint32_t b = 0; b < 2 && b < a1_issued; ++b) {
+        uint32_t cnt = a1_issued / 2 + (b < a1_issued % 2 ? 1u : 0u);
+        volatile int never = 0;
+        ptx::mbar_wait(&a1_full[b], (cnt - 1) & 1u, &never, kWaitLimit);
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc1 = ptx::idesc_bf16_f32(kTcM, N1);
+      constexpr uint32_t idesc2 = ptx::idesc_bf16_f32(kTcM, 16);
+      uint32_t stage = 0, sphase = 0, g = 0, pc = 0, a1c = 0;
+      bool ok = true;
+      struct Pend {
+        uint32_t stage, g, pc;
+        bool first, last;
+      } pend{0, 0, 0, false, false};
+      bool has_pend = false;
+      auto issue_gemm2 = [&](const Pend& P) -> bool {
+        const uint32_t b = P.g & 1u;
+        if (!ptx::mbar_wait(&a2_full[b], (P.g >> 1) & 1u, abort_flag, kWaitLimit)) return false;
+        const uint32_t db = P.pc & 1u;
+        if (P.first && !ptx::mbar_wait(&d2_empty[db], ((P.pc >> 1) & 1u) ^ 1u, abort_flag, kWaitLimit))
+          return false;
+        ptx::tc_fence_after();
+        const uint32_t a2 = smem_base + L::A2_OFF + b * L::A2_BYTES;
+        const uint32_t b2 = smem_base + L::STAGES_OFF + P.stage * L::STAGE_BYTES + L::B2_OFF_IN_STAGE;
+        constexpr uint32_t lbo_b2 = L::N2R * 16;
+#pragma unroll
+        for (int q = 0; q < Sh::KD2 / 16; ++q) {
+          const uint64_t ad = ptx::smem_desc(a2 + q * 2 * 2048, 2048, 128);
+          const uint32_t bstart = b2 + q * 2 * lbo_b2;
+          const uint32_t sbo_b2 = (KCH == 2) ? 128u : (smem_base + L::ZERO_OFF - bstart);
+          const uint64_t bd = ptx::smem_desc(bstart, lbo_b2, sbo_b2);
+          ptx::mma_bf16_ss(tmem + db * 16, ad, bd, idesc2, (q > 0 || !P.first) ? 1u : 0u);
+        }
+        ptx::mma_commit(&a2_empty[b]);
+        ptx::mma_commit(&empty_b[P.stage]);
+        if (P.last) ptx::mma_commit(&d2_full[db]);
+        return true;
+      };
+      for (int64_t item = blockIdx.x; item < prm.num_items && ok; item += gridDim.x) {
+        const int64_t chunk = item / c_tiles;
+        const int64_t t0 = chunk * tpc, t1 = min(prm.n_tiles, t0 + tpc);
+        const uint32_t ab = a1c & 1u;
+        if (!ptx::mbar_wait(&a1_full[ab], (a1c >> 1) & 1u, abort_flag, kWaitLimit)) {
+          give_up();
+          break;
+        }
+        const uint32_t a1 = smem_base + L::A1_OFF + ab * L::A1_BYTES;
+        const uint32_t lbo_a1 = (KCH == 2) ? kTcM * 16u : (smem_base + L::ZERO_OFF - a1);
+        const uint64_t adesc = ptx::smem_desc(a1, lbo_a1, 128);
+        for (int64_t t = t0; t < t1; ++t) {
+          const int64_t j = t - t0;
+          const uint32_t b = g & 1u;
+          if (!ptx::mbar_wait(&full_b[stage], sphase, abort_flag, kWaitLimit) ||
+              !ptx::mbar_wait(&d1_empty[b], ((g >> 1) & 1u) ^ 1u, abort_flag, kWaitLimit)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t b1 = smem_base + L::STAGES_OFF + stage * L::STAGE_BYTES + L::B1_OFF_IN_STAGE;
+          const uint32_t lbo_b1 = (KCH == 2) ? N1 * 16u : (smem_base + L::ZERO_OFF - b1);
+          const uint64_t bdesc = ptx::smem_desc(b1, lbo_b1, 128);
+          ptx::mma_bf16_ss(tmem + D1_COL0 + b * N1, adesc, bdesc, idesc1, 0u);
+          ptx::mma_commit(&d1_full[b]);
+          if (t == t1 - 1) ptx::mma_commit(&a1_empty[ab]);
+          if (has_pend && !issue_gemm2(pend)) {
+            give_up();
+            ok = false;
+            break;
+          }
+          const bool first = (j % F) == 0;
+          const bool last = ((j % F) == F - 1) || (t == t1 - 1);
+          pend = Pend{stage, g, pc, first, last};
+          has_pend = true;
+          if (last) ++pc;
+          ++g;
+          if (++stage == kTcStages) {
+            stage = 0;
+            sphase ^= 1u;
+          }
+        }
+        ++a1c;
+      }
+      if (ok && has_pend && !issue_gemm2(pend)) give_up();
+      // drain: all issued MMAs complete before TMEM is released
+      ptx::mma_commit(drain_bar);
+      volatile int never = 0;
+      ptx::mbar_wait(drain_bar, 0u, &never, kWaitLimit);
+    }
+  } else if (warp >= 4) {
+    // ------------------------------------------------------------ epilogue
+    const int e = (warp - 4) >> 2;   // warpgroup
+    const int qtr = warp & 3;        // TMEM lane quarter
+    const int row = qtr * 32 + lane; // candidate row within the tile
+    const uint32_t lane_base = static_cast<uint32_t>(qtr * 32) << 16;
+    uint32_t g = 0, pc = 0;
+    float hi[2 * kMaxRank], lo[2 * kMaxRank];
+#pragma unroll
+    for (int jj = 0; jj < 2 * kMaxRank; ++jj) hi[jj] = lo[jj] = 0.f;
+    bool ok = true;
+    for (int64_t item = blockIdx.x; item < prm.num_items && ok; item += gridDim.x) {
+      const int64_t chunk = item / c_tiles, ct = item % c_tiles;
+      const int64_t t0 = chunk * tpc, t1 = min(prm.n_tiles, t0 + tpc);
+      for (int64_t t = t0; t < t1; ++t) {
+        const int64_t j = t - t0;
+        const uint32_t b = g & 1u;
+        if (!__all_sync(0xffffffffu, ptx::mbar_wait(&d1_full[b], (g >> 1) & 1u, abort_flag, kWaitLimit))) {
+          give_up();
+          ok = false;
+          break;
+        }
+        ptx::tc_fence_after();
+        uint32_t pl[BK][RPE];
+#pragma unroll
+        for (int m = 0; m < BK; ++m)
+          tmem_ld_cols<RPE>(tmem + lane_base + D1_COL0 + b * N1 + m * ROWS + e * RPE, pl[m]);
+        ptx::tmem_wait_ld();
+        ptx::tc_fence_before();
+        ptx::mbar_arrive(&d1_empty[b]);
+        // indicator words: word p holds rows (2p, 2p+1) of this slice
+        uint32_t wv[G][RPE / 2];
+#pragma unroll
+        for (int p = 0; p < RPE / 2; ++p) {
+          uint32_t nm[BK];
+#pragma unroll
+          for (int m = 0; m < BK; ++m) nm[m] = ptx::prmt(pl[m][2 * p], pl[m][2 * p + 1], 0xFFBBu);
+#pragma unroll
+          for (int gc = 0; gc < G; ++gc) {
+            if constexpr (K % 2 == 1)
+              wv[gc][p] = ~nm[gc] & nm[gc + 1] & 0x3F803F80u;  // p_{k-1} > 0 and p_k < 0, k = gc+1
+            else
+              wv[gc][p] = (nm[gc] & 0x80008000u) | 0x3F803F80u;  // sign(p_m) as +-1
+          }
+        }
+        if (!__all_sync(0xffffffffu, ptx::mbar_wait(&a2_empty[b], ((g >> 1) & 1u) ^ 1u, abort_flag, kWaitLimit))) {
+          give_up();
+          ok = false;
+          break;
+        }
+        uint8_t* a2 = smem + L::A2_OFF + b * L::A2_BYTES + (row >> 3) * 128 + (row & 7) * 16;
+#pragma unroll
+        for (int gc = 0; gc < G; ++gc) {
+#pragma unroll
+          for (int c = 0; c < RPE / 8; ++c) {
+            const int kchunk = (gc * ROWS + e * RPE) / 8 + c;
+            *reinterpret_cast<uint4*>(a2 + kchunk * 2048) =
+                make_uint4(wv[gc][4 * c], wv[gc][4 * c + 1], wv[gc][4 * c + 2], wv[gc][4 * c + 3]);
+          }
+        }
+        ptx::fence_proxy_async_smem();
+        ptx::mbar_arrive(&a2_full[b]);
+        const bool last = ((j % F) == F - 1) || (t == t1 - 1);
+        if (e == 0 && last) {
+          const uint32_t db = pc & 1u;
+          if (!__all_sync(0xffffffffu, ptx::mbar_wait(&d2_full[db], (pc >> 1) & 1u, abort_flag, kWaitLimit))) {
+            give_up();
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          uint32_t dv[16];
+          ptx::tmem_ld_x16(tmem + lane_base + db * 16, dv);
+          ptx::tmem_wait_ld();
+          ptx::tc_fence_before();
+          ptx::mbar_arrive(&d2_empty[db]);
+#pragma unroll
+          for (int jj = 0; jj < 2 * kMaxRank; ++jj) {
+            float s, er;
+            two_sum_f(hi[jj], __uint_as_float(dv[jj]), s, er);
+            hi[jj] = s;
+            lo[jj] += er;
+          }
+          if (t == t1 - 1) {
+            const int r2 = 2 * prm.r;
+            double* out = partial + (chunk * prm.S_pad + ct * kTcM + row) * r2;
+#pragma unroll
+            for (int jj = 0; jj < 2 * kMaxRank; ++jj)
+              if (jj < r2) out[jj] = static_cast<double>(hi[jj]) + static_cast<double>(lo[jj]);
+#pragma unroll
+            for (int jj = 0; jj < 2 * kMaxRank; ++jj) hi[jj] = lo[jj] = 0.f;
+          }
+        }
+        if (last) ++pc;
+        ++g;
+      }
+    }
+  }
+  // ------------------------------------------------------------ teardown
+  ptx::tc_fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    __syncwarp();
+    ptx::tc_fence_after();
+    ptx::tmem_dealloc(tmem, 512);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Operand packing (run once per call): bf16 tiles in the exact shared-memory
+// order the MMA descriptors expect, so each stage is one TMA box.
+// ---------------------------------------------------------------------------
+struct PackTables {
+  float bcos[8], bsin[8];    // boundary directions theta_m, m < B_K
+  float beta_r[8], beta_i[8];  // per-indicator coefficients
+};
+
+// augmented rows: tile t, chunk ch, row (m*ROWS + i), 8 slots
+template <int K, int KCH>
+__global__ void pack_vaug_kernel(const float2* __restrict__ V, int64_t n, int r, int64_t n_tiles, PackTables tb,
+                                 __nv_bfloat16* __restrict__ vt) {
+  using Sh = TcShape<K>;
+  const int64_t total = n_tiles * Sh::N1;
+  int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= total) return;
+  const int64_t t = q / Sh::N1;
+  const int rowin = static_cast<int>(q % Sh::N1);
+  const int m = rowin / Sh::ROWS, i = rowin % Sh::ROWS;
+  const int64_t ig = t * Sh::ROWS + i;
+  float slot[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) slot[k] = 0.f;
+  if (ig < n) {
+    const float bc = tb.bcos[m], bs = tb.bsin[m];
+    for (int jj = 0; jj < r; ++jj) {
+      float2 v = V[ig * r + jj];
+      // rho_m V = (bc - i bs)(vr + i vi)
+      slot[jj] = fmaf(bc, v.y, -bs * v.x);     // Im(rho_m V_ij)
+      slot[r + jj] = fmaf(bc, v.x, bs * v.y);  // Re(rho_m V_ij)
+    }
+  }
+#pragma unroll
+  for (int ch = 0; ch < KCH; ++ch) {
+    __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) h[k] = __float2bfloat16_rn(slot[ch * 8 + k]);
+    *reinterpret_cast<uint4*>(vt + ((t * KCH + ch) * Sh::N1 + rowin) * 8) = *reinterpret_cast<uint4*>(h);
+  }
+}
+
+// GEMM2 B rows: tile t, K-chunk kc, output column nc: 8 reduction entries
+template <int K, int KCH>
+__global__ void pack_b2_kernel(const float2* __restrict__ V, int64_t n, int r, int64_t n_tiles, PackTables tb,
+                               __nv_bfloat16* __restrict__ b2) {
+  using Sh = TcShape<K>;
+  using L = TcLayout<K, KCH>;
+  const int64_t total = n_tiles * L::B2ROWS;
+  int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= total) return;
+  const int64_t t = q / L::B2ROWS;
+  const int within = static_cast<int>(q % L::B2ROWS);
+  const int kc = within / L::N2R, nc = within % L::N2R;
+  __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const int kk = kc * 8 + k;
+    const int gc = kk / Sh::ROWS, i = kk % Sh::ROWS;
+    const int64_t ig = t * Sh::ROWS + i;
+    const int jj = nc >> 1;
+    float val = 0.f;
+    if (ig < n && jj < r) {
+      float2 v = V[ig * r + jj];
+      const float br = tb.beta_r[gc], bi = tb.beta_i[gc];
+      // beta conj(V) = (br vr + bi vi) + i (bi vr - br vi)
+      val = (nc & 1) ? fmaf(bi, v.x, -br * v.y) : fmaf(br, v.x, bi * v.y);
+    }
+    h[k] = __float2bfloat16_rn(val);
+  }
+  *reinterpret_cast<uint4*>(b2 + (t * L::B2ROWS + within) * 8) = *reinterpret_cast<uint4*>(h);
+}
+
+// directions: candidate tile ct, chunk ch, row s: slots [Re c, Im c, 0...]
+template <int KCH>
+__global__ void pack_dirs_kernel(const float2* __restrict__ C, int64_t S, int r, int64_t c_tiles,
+                                 __nv_bfloat16* __restrict__ ctp) {
+  const int64_t total = c_tiles * kTcM;
+  int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= total) return;
+  const int64_t ct = q / kTcM;
+  const int row = static_cast<int>(q % kTcM);
+  float slot[16];
+#pragma unroll
+  for (int k = 0; k < 16; ++k) slot[k] = 0.f;
+  if (q < S) {
+    for (int jj = 0; jj < r; ++jj) {
+      float2 c = C[q * r + jj];
+      slot[jj] = c.x;
+      slot[r + jj] = c.y;
+    }
+  }
+#pragma unroll
+  for (int ch = 0; ch < KCH; ++ch) {
+    __align__(16) __nv_bfloat16 h[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) h[k] = __float2bfloat16_rn(slot[ch * 8 + k]);
+    *reinterpret_cast<uint4*>(ctp + ((ct * KCH + ch) * kTcM + row) * 8) = *reinterpret_cast<uint4*>(h);
+  }
+}
+
+static PackTables make_pack_tables(const Alphabet& a) {
+  PackTables tb;
+  for (int m = 0; m < 8; ++m) {
+    tb.bcos[m] = m < a.BK ? a.bcos[m] : 0.f;
+    tb.bsin[m] = m < a.BK ? a.bsin[m] : 0.f;
+    tb.beta_r[m] = m < a.G ? static_cast<float>(a.beta_r[m]) : 0.f;
+    tb.beta_i[m] = m < a.G ? static_cast<float>(a.beta_i[m]) : 0.f;
+  }
+  return tb;
+}
+
+template <int K, int KCH>
+static int pack_impl(const ScorePlan& p, const Alphabet& a, const float2* V, const float2* C, void* vt, void* b2,
+                     void* ct, cudaStream_t st) {
+  using Sh = TcShape<K>;
+  using L = TcLayout<K, KCH>;
+  PackTables tb = make_pack_tables(a);
+  int64_t nv = p.n_tiles * Sh::N1;
+  pack_vaug_kernel<K, KCH><<<static_cast<unsigned>(ceil_div(nv, 256)), 256, 0, st>>>(
+      V, p.n, p.r, p.n_tiles, tb, static_cast<__nv_bfloat16*>(vt));
+  count_launch();
+  int64_t nb = p.n_tiles * L::B2ROWS;
+  pack_b2_kernel<K, KCH><<<static_cast<unsigned>(ceil_div(nb, 256)), 256, 0, st>>>(
+      V, p.n, p.r, p.n_tiles, tb, static_cast<__nv_bfloat16*>(b2));
+  count_launch();
+  int64_t nc = p.c_tiles * kTcM;
+  pack_dirs_kernel<KCH><<<static_cast<unsigned>(ceil_div(nc, 256)), 256, 0, st>>>(C, p.S, p.r, p.c_tiles,
+                                                                                  static_cast<__nv_bfloat16*>(ct));
+  count_launch();
+  return cuda_check(cudaGetLastError(), "tc pack kernels");
+}
+
+// ---------------------------------------------------------------------------
+// Tensor maps: every packed operand is viewed as a 2-D bf16 array of 16-byte
+// rows ([rows][8]); a box of `box_rows` rows lands in shared memory exactly in
+// the no-swizzle core-matrix order.
+// ---------------------------------------------------------------------------
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn get_encode_fn() {
+  static std::once_flag once;
+  static EncodeTiledFn fn = nullptr;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  });
+  return fn;
+}
+
+static int make_rows_map(CUtensorMap* map, const void* base, int64_t rows, int box_rows) {
+  EncodeTiledFn enc = get_encode_fn();
+  if (!enc) return fail(LRQ_ECUDA, "cuTensorMapEncodeTiled is unavailable");
+  cuuint64_t dims[2] = {8, static_cast<cuuint64_t>(rows)};
+  cuuint64_t strides[1] = {16};
+  cuuint32_t box[2] = {8, static_cast<cuuint32_t>(box_rows)};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return fail(LRQ_ECUDA, "cuTensorMapEncodeTiled failed");
+  return LRQ_OK;
+}
+
+template <int K, int KCH>
+static int score_impl(const ScorePlan& p, const void* vt, const void* b2, const void* ct, double* partial,
+                      int32_t* status, cudaStream_t st) {
+  using Sh = TcShape<K>;
+  using L = TcLayout<K, KCH>;
+  CUtensorMap m_vt, m_b2, m_ct;
+  int e;
+  if ((e = make_rows_map(&m_vt, vt, p.n_tiles * KCH * Sh::N1, Sh::N1))) return e;
+  if ((e = make_rows_map(&m_b2, b2, p.n_tiles * L::B2ROWS, L::B2BOX))) return e;
+  if ((e = make_rows_map(&m_ct, ct, p.c_tiles * KCH * kTcM, kTcM))) return e;
+  static std::once_flag attr_once;
+  static cudaError_t attr_err = cudaSuccess;
+  std::call_once(attr_once, []() {
+    attr_err = cudaFuncSetAttribute(score_tc_kernel<K, KCH>, cudaFuncAttributeMaxDynamicSharedMemorySize, L::TOTAL);
+  });
+  if ((e = cuda_check(attr_err, "cudaFuncSetAttribute(score_tc_kernel)"))) return e;
+  TcParams prm;
+  prm.n_tiles = p.n_tiles;
+  prm.c_tiles = p.c_tiles;
+  prm.tiles_per_chunk = p.tiles_per_chunk;
+  prm.num_items = p.c_tiles * p.nsplit;
+  prm.S_pad = p.c_tiles * kTcM;
+  prm.r = p.r;
+  prm.flush = kTcFlush;
+  int grid = static_cast<int>(std::min<int64_t>(prm.num_items, num_sms_current()));
+  score_tc_kernel<K, KCH><<<grid, 128 * (1 + kTcNE), L::TOTAL, st>>>(m_vt, m_b2, m_ct, prm, partial, status);
+  count_launch();
+  return cuda_check(cudaGetLastError(), "score_tc_kernel");
+}
+
+int tc_rows_per_tile(int K) {
+  switch (K) {
+    case 2: return TcShape<2>::ROWS;
+    case 3: return TcShape<3>::ROWS;
+    case 4: return TcShape<4>::ROWS;
+    case 5: return TcShape<5>::ROWS;
+    case 6: return TcShape<6>::ROWS;
+    case 7: return TcShape<7>::ROWS;
+    case 8: return TcShape<8>::ROWS;
+    default: return 0;
+  }
+}
+
+size_t tc_bytes_vaug(int K, int r, int64_t n_tiles) {
+  int kch = r <= 4 ? 1 : 2;
+  int bk = (K % 2 == 0) ? K / 2 : K;
+  return static_cast<size_t>(n_tiles) * kch * bk * tc_rows_per_tile(K) * 16;
+}
+
+size_t tc_bytes_b2(int K, int r, int64_t n_tiles) {
+  int n2r = r <= 4 ? 8 : 16;
+  int g = (K % 2 == 0) ? K / 2 : K - 1;
+  return static_cast<size_t>(n_tiles) * (g * tc_rows_per_tile(K) / 8) * n2r * 16;
+}
+
+size_t tc_bytes_dirs(int r, int64_t c_tiles) {
+  int kch = r <= 4 ? 1 : 2;
+  return static_cast<size_t>(c_tiles) * kch * kTcM * 16;
+}
+
+#define LRQ_TC_DISPATCH(FN, ...)                                        \
+  do {                                                                  \
+    const bool two = p.r > 4;                                           \
+    switch (p.K) {                                                      \
+      case 2: return two ? FN<2, 2>(__VA_ARGS__) : FN<2, 1>(__VA_ARGS__); \
+      case 3: return two ? FN<3, 2>(__VA_ARGS__) : FN<3, 1>(__VA_ARGS__); \
+      case 4: return two ? FN<4, 2>(__VA_ARGS__) : FN<4, 1>(__VA_ARGS__); \
+      case 5: return two ? FN<5, 2>(__VA_ARGS__) : FN<5, 1>(__VA_ARGS__); \
+      case 6: return two ? FN<6, 2>(__VA_ARGS__) : FN<6, 1>(__VA_ARGS__); \
+      case 7: return two ? FN<7, 2>(__VA_ARGS__) : FN<7, 1>(__VA_ARGS__); \
+      case 8: return two ? FN<8, 2>(__VA_ARGS__) : FN<8, 1>(__VA_ARGS__); \
+      default: return fail(LRQ_EUNSUPPORTED, "tensor-core path supports 2 <= K <= 8"); \
+    }                                                                   \
+  } while (0)
+
+int launch_tc_pack(const ScorePlan& p, const Alphabet& a, const float2* V, const float2* C, void* vt, void* b2,
+                   void* ct, cudaStream_t st) {
+  LRQ_TC_DISPATCH(pack_impl, p, a, V, C, vt, b2, ct, st);
+}
+
+int launch_score_tc(const ScorePlan& p, const Alphabet& a, const void* vt, const void* b2, const void* ct,
+                    double* partial, int32_t* status, cudaStream_t st) {
+  (void)a;
+  LRQ_TC_DISPATCH(score_impl, p, vt, b2, ct, partial, status, st);
+}
+
+}  // namespace lrq

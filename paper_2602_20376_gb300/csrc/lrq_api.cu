@@ -1,0 +1,342 @@
+// lrq_api.cu -- the extern "C" entry points of liblrq (declared in
+// include/lrq.h): argument validation, workspace planning, alphabet tables
+// and the launch sequence of each call.  No entry point allocates device
+// memory or synchronises the stream.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <string>
+
+#include "lrq_internal.h"
+
+namespace lrq {
+
+int tc_rows_per_tile(int K);
+size_t tc_bytes_vaug(int K, int r, int64_t n_tiles);
+size_t tc_bytes_b2(int K, int r, int64_t n_tiles);
+size_t tc_bytes_dirs(int r, int64_t c_tiles);
+
+static thread_local char g_last_error[512] = {0};
+static std::atomic<uint64_t> g_launches{0};
+static thread_local cudaEvent_t g_t_start = nullptr;
+static thread_local cudaEvent_t g_t_stop = nullptr;
+
+void count_launch(int k) { g_launches.fetch_add(static_cast<uint64_t>(k), std::memory_order_relaxed); }
+
+void timing_start(cudaStream_t st) {
+  if (g_t_start) cudaEventRecord(g_t_start, st);
+}
+
+void timing_stop(cudaStream_t st) {
+  if (g_t_stop) cudaEventRecord(g_t_stop, st);
+}
+
+void set_error(const std::string& msg) {
+  std::snprintf(g_last_error, sizeof(g_last_error), "%s", msg.c_str());
+}
+
+int fail(int status, const std::string& msg) {
+  set_error(msg);
+  return status;
+}
+
+int cuda_check(cudaError_t e, const char* what) {
+  if (e == cudaSuccess) return LRQ_OK;
+  return fail(LRQ_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+int num_sms_current() {
+  static std::mutex mu;
+  static int cache[64] = {0};
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 148;
+  std::lock_guard<std::mutex> lock(mu);
+  if (cache[dev] == 0) {
+    int v = 0;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) v = 148;
+    cache[dev] = v;
+  }
+  return cache[dev];
+}
+
+static double snap(double v) { return std::fabs(v) < 1e-15 ? 0.0 : v; }
+
+Alphabet make_alphabet(int K) {
+  Alphabet a;
+  std::memset(&a, 0, sizeof(a));
+  a.K = K;
+  a.BK = (K % 2 == 0) ? K / 2 : K;
+  a.G = (K % 2 == 0) ? K / 2 : K - 1;
+  for (int m = 0; m < K && m < kMaxK; ++m) {
+    double th = kPi * (2.0 * m + 1.0) / K;  // decision boundary theta_m
+    a.bcos64[m] = snap(std::cos(th));
+    a.bsin64[m] = snap(std::sin(th));
+    a.bcos[m] = static_cast<float>(a.bcos64[m]);
+    a.bsin[m] = static_cast<float>(a.bsin64[m]);
+    double ph = 2.0 * kPi * m / K;  // root omega^m
+    a.zr64[m] = snap(std::cos(ph));
+    a.zi64[m] = snap(std::sin(ph));
+    a.zr[m] = static_cast<float>(a.zr64[m]);
+    a.zi[m] = static_cast<float>(a.zi64[m]);
+  }
+  for (int g = 0; g < a.G && g < kMaxK; ++g) {
+    if (K % 2 == 1) {  // odd K: indicator of class g+1, coefficient omega^{g+1} - 1
+      a.beta_r[g] = a.zr64[g + 1] - 1.0;
+      a.beta_i[g] = a.zi64[g + 1];
+    } else {  // even K: sign of boundary g, coefficient (omega^{g+1} - omega^g) / 2
+      double r1 = snap(std::cos(2.0 * kPi * (g + 1) / K)), i1 = snap(std::sin(2.0 * kPi * (g + 1) / K));
+      a.beta_r[g] = 0.5 * (r1 - a.zr64[g]);
+      a.beta_i[g] = 0.5 * (i1 - a.zi64[g]);
+    }
+  }
+  return a;
+}
+
+static size_t take(size_t& cursor, size_t bytes) {
+  size_t off = cursor;
+  cursor = align_up(cursor + bytes, 256);
+  return off;
+}
+
+int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_sms, ScorePlan* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->n = n;
+  p->S = S;
+  p->r = r;
+  p->K = K;
+  p->mode = mode;
+  p->top_m = top_m;
+  p->c_tiles = ceil_div(S, 128);
+  const int64_t S_pad = p->c_tiles * 128;
+  if (mode == LRQ_MODE_BF16_TC) {
+    p->rows_per_tile = tc_rows_per_tile(K);
+    p->n_tiles = ceil_div(n, p->rows_per_tile);
+    // coordinate chunks: balance (chunk, candidate tile) items over the SMs
+    int best_ns = 1;
+    double best_eff = -1.0;
+    for (int ns = 1; ns <= 64 && ns <= p->n_tiles; ++ns) {
+      int64_t tpc = ceil_div(p->n_tiles, ns);
+      int64_t ns_eff = ceil_div(p->n_tiles, tpc);
+      int64_t items = p->c_tiles * ns_eff;
+      int64_t waves = ceil_div(items, num_sms);
+      double eff = static_cast<double>(items) / static_cast<double>(waves * num_sms);
+      // a longer chunk amortises the pipeline fill of an item
+      eff *= static_cast<double>(tpc) / static_cast<double>(tpc + 2);
+      if (eff > best_eff + 1e-3) {
+        best_eff = eff;
+        best_ns = ns;
+      }
+    }
+    p->tiles_per_chunk = ceil_div(p->n_tiles, best_ns);
+    p->nsplit = static_cast<int>(ceil_div(p->n_tiles, p->tiles_per_chunk));
+  } else {
+    p->fp32_block = 256;
+    int64_t blocks_x = ceil_div(S, 256);
+    int64_t want = std::max<int64_t>(1, ceil_div(int64_t(8) * num_sms, blocks_x));
+    want = std::min<int64_t>(want, 64);
+    int64_t rows = align_up(static_cast<size_t>(ceil_div(n, want)), 256);
+    p->fp32_rows_per_chunk = std::max<int64_t>(rows, 256);
+    p->nsplit = static_cast<int>(ceil_div(n, p->fp32_rows_per_chunk));
+  }
+  size_t cur = 0;
+  p->sz_partial = static_cast<size_t>(p->nsplit) * S_pad * 2 * r * sizeof(double);
+  p->off_partial = take(cur, p->sz_partial);
+  p->sz_T = 2 * kMaxRank * sizeof(double);
+  p->off_T = take(cur, p->sz_T);
+  p->sz_Tpart = 256 * 2 * kMaxRank * sizeof(double);
+  p->off_Tpart = take(cur, p->sz_Tpart);
+  if (mode == LRQ_MODE_BF16_TC) {
+    p->sz_vt = tc_bytes_vaug(K, r, p->n_tiles);
+    p->off_vt = take(cur, p->sz_vt);
+    p->sz_b2 = tc_bytes_b2(K, r, p->n_tiles);
+    p->off_b2 = take(cur, p->sz_b2);
+    p->sz_ct = tc_bytes_dirs(r, p->c_tiles);
+    p->off_ct = take(cur, p->sz_ct);
+  }
+  p->sz_scores = static_cast<size_t>(S) * sizeof(float);
+  p->off_scores = take(cur, p->sz_scores);
+  p->sz_keys = (static_cast<size_t>(S) + topm_scratch_keys(S, top_m)) * sizeof(uint64_t);
+  p->off_keys = take(cur, p->sz_keys);
+  p->total = cur;
+  return LRQ_OK;
+}
+
+int plan_rescore(int64_t n, int r, int m, RescorePlan* p) {
+  std::memset(p, 0, sizeof(*p));
+  p->n = n;
+  p->r = r;
+  p->m = m;
+  const int64_t max_rows = int64_t(256) * 256;  // at most 256 rows per thread
+  int64_t nchunk = std::max<int64_t>(ceil_div(2432, m), ceil_div(n, max_rows));
+  nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, std::max<int64_t>(1, ceil_div(n, 256))));
+  p->rows_per_chunk = ceil_div(n, nchunk);
+  p->nchunk = static_cast<int>(ceil_div(n, p->rows_per_chunk));
+  size_t cur = 0;
+  p->sz_part = static_cast<size_t>(m) * p->nchunk * 2 * kMaxRank * sizeof(double);
+  p->off_part = take(cur, p->sz_part);
+  p->total = cur;
+  return LRQ_OK;
+}
+
+static int check_ws(const void* ws, size_t ws_bytes, size_t need) {
+  if (need == 0) return LRQ_OK;
+  if (ws == nullptr) return fail(LRQ_EWORKSPACE, "workspace pointer is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(LRQ_EWORKSPACE, "workspace must be 256-byte aligned");
+  if (ws_bytes < need)
+    return fail(LRQ_EWORKSPACE, "workspace too small: need " + std::to_string(need) + " bytes, got " +
+                                    std::to_string(ws_bytes));
+  return LRQ_OK;
+}
+
+static int check_score_args(int64_t n, int r, int K, int64_t S, int mode, int top_m) {
+  if (n < 1) return fail(LRQ_EINVAL, "n must be >= 1");
+  if (r < 1 || r > kMaxRank) return fail(LRQ_EINVAL, "r must be in [1, 8]");
+  if (K < 2 || K > kMaxK) return fail(LRQ_EINVAL, "K must be in [2, 64]");
+  if (S < 1 || S >= (int64_t(1) << 31)) return fail(LRQ_EINVAL, "S must be in [1, 2^31)");
+  if (mode != LRQ_MODE_FP32 && mode != LRQ_MODE_BF16_TC) return fail(LRQ_EINVAL, "unknown mode");
+  if (top_m < 1 || top_m > kMaxTopM || top_m > S) return fail(LRQ_EINVAL, "top_m must be in [1, min(512, S)]");
+  if (mode == LRQ_MODE_BF16_TC && K > kMaxTcK)
+    return fail(LRQ_EUNSUPPORTED, "the tensor-core mode supports 2 <= K <= 8");
+  if (n > (int64_t(1) << 40)) return fail(LRQ_EUNSUPPORTED, "n too large");
+  return LRQ_OK;
+}
+
+}  // namespace lrq
+
+using namespace lrq;
+
+extern "C" {
+
+const char* lrq_status_string(int status) {
+  switch (status) {
+    case LRQ_OK: return "LRQ_OK";
+    case LRQ_EINVAL: return "LRQ_EINVAL: invalid argument or non-finite input";
+    case LRQ_EUNSUPPORTED: return "LRQ_EUNSUPPORTED: unsupported size, alphabet, rank or mode";
+    case LRQ_ECUDA: return "LRQ_ECUDA: CUDA runtime error";
+    case LRQ_ETIMEOUT: return "LRQ_ETIMEOUT: a bounded device wait ran out";
+    case LRQ_ENOCONV: return "LRQ_ENOCONV: iterative solver did not converge";
+    case LRQ_EWORKSPACE: return "LRQ_EWORKSPACE: workspace missing, misaligned or too small";
+    default: return "LRQ_UNKNOWN";
+  }
+}
+
+const char* lrq_last_error(void) { return g_last_error; }
+
+int lrq_abi_version(void) { return 1; }
+
+int lrq_sample_directions(uint64_t seed, int64_t S, int r, void* C_out, void* stream) {
+  if (S < 0) return fail(LRQ_EINVAL, "S must be >= 0");
+  if (r < 1 || r > kMaxK) return fail(LRQ_EINVAL, "r must be in [1, 64]");
+  if (S > 0 && C_out == nullptr) return fail(LRQ_EINVAL, "C_out is NULL");
+  return launch_sample_directions(seed, S, r, static_cast<float2*>(C_out), static_cast<cudaStream_t>(stream));
+}
+
+int lrq_sample_score_workspace_size(int64_t n, int r, int K, int64_t S, int mode, int top_m, size_t* bytes) {
+  if (!bytes) return fail(LRQ_EINVAL, "bytes is NULL");
+  int e = check_score_args(n, r, K, S, mode, top_m);
+  if (e) return e;
+  ScorePlan p;
+  plan_score(n, r, K, S, mode, top_m, num_sms_current(), &p);
+  *bytes = p.total;
+  return LRQ_OK;
+}
+
+int lrq_sample_score(const void* V, int64_t n, int r, int K, void* C, int generate_C, uint64_t seed, int64_t S,
+                     int mode, int top_m, float* scores_out, int64_t* top_idx_out, float* top_f_out, void* ws,
+                     size_t ws_bytes, int32_t* dev_status, void* stream) {
+  int e = check_score_args(n, r, K, S, mode, top_m);
+  if (e) return e;
+  if (!V || !C || !top_idx_out || !top_f_out || !dev_status) return fail(LRQ_EINVAL, "NULL pointer argument");
+  ScorePlan p;
+  plan_score(n, r, K, S, mode, top_m, num_sms_current(), &p);
+  if ((e = check_ws(ws, ws_bytes, p.total))) return e;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  const float2* Vf = static_cast<const float2*>(V);
+  float2* Cf = static_cast<float2*>(C);
+  double* partial = reinterpret_cast<double*>(w + p.off_partial);
+  double* T = reinterpret_cast<double*>(w + p.off_T);
+  float* scores = scores_out ? scores_out : reinterpret_cast<float*>(w + p.off_scores);
+  uint64_t* keys = reinterpret_cast<uint64_t*>(w + p.off_keys);
+  uint64_t* keys_scratch = keys + S;
+  Alphabet a = make_alphabet(K);
+
+  if (generate_C && (e = launch_sample_directions(seed, S, r, Cf, st))) return e;
+  if ((e = launch_check_finite(reinterpret_cast<const float*>(V), 2 * n * r, dev_status, st))) return e;
+  if ((e = launch_check_finite(reinterpret_cast<const float*>(C), 2 * S * r, dev_status, st))) return e;
+  const double* Tuse = nullptr;
+  if (mode == LRQ_MODE_BF16_TC) {
+    if (K % 2 == 1) {
+      int nb = static_cast<int>(std::min<int64_t>(256, std::max<int64_t>(1, ceil_div(n, 4096))));
+      if ((e = launch_colsum(Vf, n, r, reinterpret_cast<double*>(w + p.off_Tpart), T, nb, st))) return e;
+      Tuse = T;
+    }
+    if ((e = launch_tc_pack(p, a, Vf, Cf, w + p.off_vt, w + p.off_b2, w + p.off_ct, st))) return e;
+    timing_start(st);
+    if ((e = launch_score_tc(p, a, w + p.off_vt, w + p.off_b2, w + p.off_ct, partial, dev_status, st))) return e;
+    timing_stop(st);
+  } else {
+    timing_start(st);
+    if ((e = launch_score_fp32(p, a, Vf, Cf, partial, st))) return e;
+    timing_stop(st);
+  }
+  if ((e = launch_finalize(p, a, partial, Tuse, scores, keys, st))) return e;
+  return launch_topm(keys, S, top_m, keys_scratch, top_idx_out, top_f_out, st);
+}
+
+int lrq_rescore_workspace_size(int64_t n, int r, int m, size_t* bytes) {
+  if (!bytes) return fail(LRQ_EINVAL, "bytes is NULL");
+  if (n < 1 || r < 1 || r > kMaxRank || m < 1 || m > kMaxRescoreM) return fail(LRQ_EINVAL, "bad sizes");
+  RescorePlan p;
+  plan_rescore(n, r, m, &p);
+  *bytes = p.total;
+  return LRQ_OK;
+}
+
+int lrq_rescore(const void* V, int64_t n, int r, int K, const void* C, int64_t S, const int64_t* idx, int m,
+                double* f_out, uint8_t* z_out, int64_t* best_out, double* best_f_out, void* ws, size_t ws_bytes,
+                int32_t* dev_status, void* stream) {
+  if (n < 1) return fail(LRQ_EINVAL, "n must be >= 1");
+  if (r < 1 || r > kMaxRank) return fail(LRQ_EINVAL, "r must be in [1, 8]");
+  if (K < 2 || K > kMaxK) return fail(LRQ_EINVAL, "K must be in [2, 64]");
+  if (m < 1 || m > kMaxRescoreM) return fail(LRQ_EINVAL, "m must be in [1, 4096]");
+  if (S < 1) return fail(LRQ_EINVAL, "S must be >= 1");
+  if (!V || !C || !idx || !f_out || !best_out || !best_f_out || !dev_status)
+    return fail(LRQ_EINVAL, "NULL pointer argument");
+  RescorePlan p;
+  plan_rescore(n, r, m, &p);
+  int e = check_ws(ws, ws_bytes, p.total);
+  if (e) return e;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  uint8_t* w = static_cast<uint8_t*>(ws);
+  Alphabet a = make_alphabet(K);
+  if ((e = launch_check_finite(reinterpret_cast<const float*>(V), 2 * n * r, dev_status, st))) return e;
+  return launch_rescore(p, a, static_cast<const float2*>(V), static_cast<const float2*>(C), S, idx,
+                        reinterpret_cast<double*>(w + p.off_part), f_out, z_out, best_out, best_f_out, dev_status,
+                        st);
+}
+
+int lrq_cut_count(const int32_t* rowptr, const int32_t* colidx, int64_t n, const uint8_t* z, int64_t* cut_out,
+                  void* stream) {
+  if (n < 0) return fail(LRQ_EINVAL, "n must be >= 0");
+  if (!cut_out || (n > 0 && (!rowptr || !colidx || !z))) return fail(LRQ_EINVAL, "NULL pointer argument");
+  return launch_cut_count(rowptr, colidx, n, z, cut_out, static_cast<cudaStream_t>(stream));
+}
+
+int lrq_set_timing_events(void* start_event, void* stop_event) {
+  if ((start_event == nullptr) != (stop_event == nullptr))
+    return fail(LRQ_EINVAL, "pass both timing events or neither");
+  g_t_start = static_cast<cudaEvent_t>(start_event);
+  g_t_stop = static_cast<cudaEvent_t>(stop_event);
+  return LRQ_OK;
+}
+
+uint64_t lrq_kernel_launches(void) { return g_launches.load(std::memory_order_relaxed); }
+
+}  // extern "C"

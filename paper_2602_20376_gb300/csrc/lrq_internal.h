@@ -1,0 +1,116 @@
+// lrq_internal.h -- shared declarations of the CUDA library (not part of the
+// public ABI).  Host launch helpers for every kernel translation unit, the
+// workspace planner, device status helpers and the alphabet tables.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/lrq.h"
+
+namespace lrq {
+
+constexpr double kPi = 3.14159265358979323846264338327950288;
+constexpr int kMaxRank = 8;         // r supported by the scoring kernels
+constexpr int kMaxK = 64;           // alphabet sizes supported by FP32 / FP64 paths
+constexpr int kMaxTcK = 8;          // alphabet sizes supported by the tensor-core path
+constexpr int kMaxTopM = 512;
+constexpr int kMaxRescoreM = 4096;
+
+// Thread-local error message (lrq_last_error).
+void set_error(const std::string& msg);
+int fail(int status, const std::string& msg);
+int cuda_check(cudaError_t e, const char* what);
+
+// First device-side error wins.
+__device__ __forceinline__ void dev_fail(int32_t* status, int code) {
+  if (status) atomicCAS(reinterpret_cast<int*>(status), 0, code);
+}
+
+// Alphabet A_K and its decision boundaries (Sec. 2.3).  theta_m = pi(2m+1)/K,
+// m = 0..B_K-1, with B_K = K/2 for even K and K for odd K (Definition 2.1).
+// The boundary projection of w is p_m = Im(exp(-i theta_m) w)
+//   = y cos(theta_m) - x sin(theta_m), positive on the counter-clockwise side.
+struct Alphabet {
+  int K;
+  int BK;                  // distinct boundary lines
+  int G;                   // tensor-core indicator columns per coordinate (K-1 odd, K/2 even)
+  float bcos[kMaxK], bsin[kMaxK];     // boundary line directions, FP32 (|v| < 1e-7 -> 0)
+  double bcos64[kMaxK], bsin64[kMaxK];
+  float zr[kMaxK], zi[kMaxK];         // omega^k, FP32
+  double zr64[kMaxK], zi64[kMaxK];    // omega^k, FP64
+  double beta_r[kMaxK], beta_i[kMaxK];  // per-indicator coefficients (tensor path)
+};
+Alphabet make_alphabet(int K);
+
+// Byte offsets into the caller's workspace.
+struct ScorePlan {
+  int64_t n, S;
+  int r, K, mode, top_m;
+  // tensor-core tiling
+  int rows_per_tile;       // coordinates per pipeline stage
+  int64_t n_tiles;         // ceil(n / rows_per_tile)
+  int64_t c_tiles;         // ceil(S / 128)
+  int nsplit;              // coordinate chunks (partial sums)
+  int64_t tiles_per_chunk;
+  // FP32 tiling
+  int fp32_block;          // candidates per block
+  int64_t fp32_rows_per_chunk;
+  // workspace layout
+  size_t off_partial, sz_partial;   // nsplit x S_pad x 2r doubles
+  size_t off_T, sz_T;               // 2r doubles (column sums of conj(V), odd K)
+  size_t off_Tpart, sz_Tpart;       // per-block partial column sums
+  size_t off_vt, sz_vt;             // packed augmented rows (bf16)
+  size_t off_b2, sz_b2;             // packed per-class coefficient rows (bf16)
+  size_t off_ct, sz_ct;             // packed directions (bf16)
+  size_t off_scores, sz_scores;     // S floats (when the caller passes none)
+  size_t off_keys, sz_keys;         // selection keys
+  size_t total;
+};
+int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_sms, ScorePlan* p);
+
+struct RescorePlan {
+  int64_t n;
+  int r, m, nchunk;
+  int64_t rows_per_chunk;
+  size_t off_part, sz_part;  // m x nchunk x 2r doubles
+  size_t total;
+};
+int plan_rescore(int64_t n, int r, int m, RescorePlan* p);
+
+int num_sms_current();
+
+// Kernel-launch accounting (lrq_kernel_launches) and the timing hook.
+void count_launch(int k = 1);
+void timing_start(cudaStream_t st);
+void timing_stop(cudaStream_t st);
+
+// ---- launch helpers (return lrq_status; never synchronise) -----------------
+int launch_sample_directions(uint64_t seed, int64_t S, int r, float2* C, cudaStream_t st);
+int launch_check_finite(const float* x, int64_t count, int32_t* status, cudaStream_t st);
+int launch_colsum(const float2* V, int64_t n, int r, double* Tpart, double* T, int nblocks,
+                  cudaStream_t st);
+int launch_score_fp32(const ScorePlan& p, const Alphabet& a, const float2* V, const float2* C,
+                      double* partial, cudaStream_t st);
+int launch_finalize(const ScorePlan& p, const Alphabet& a, const double* partial, const double* T,
+                    float* scores, uint64_t* keys, cudaStream_t st);
+int launch_topm(const uint64_t* keys_in, int64_t count, int m, uint64_t* scratch, int64_t* top_idx,
+                float* top_f, cudaStream_t st);
+size_t topm_scratch_keys(int64_t count, int m);
+int launch_rescore(const RescorePlan& p, const Alphabet& a, const float2* V, const float2* C,
+                   int64_t S, const int64_t* idx, double* part, double* f_out, uint8_t* z_out,
+                   int64_t* best_out, double* best_f_out, int32_t* status, cudaStream_t st);
+int launch_cut_count(const int32_t* rowptr, const int32_t* colidx, int64_t n, const uint8_t* z,
+                     int64_t* cut_out, cudaStream_t st);
+// tensor-core path
+int launch_tc_pack(const ScorePlan& p, const Alphabet& a, const float2* V, const float2* C,
+                   void* vt, void* b2, void* ct, cudaStream_t st);
+int launch_score_tc(const ScorePlan& p, const Alphabet& a, const void* vt, const void* b2,
+                    const void* ct, double* partial, int32_t* status, cudaStream_t st);
+
+__host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+__host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }
+
+}  // namespace lrq

@@ -1,0 +1,231 @@
+"""ctypes binding of liblrq (C ABI in include/lrq.h).
+
+Argument marshalling only: every function below has the name of the C entry
+point it calls, takes torch tensors where the C function takes device
+pointers, and raises LrqError when the call returns a non-zero lrq_status.
+All computation happens in the CUDA kernels of liblrq.so; there is no
+fallback -- if the library is missing, loading fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblrq.so")
+
+LRQ_OK = 0
+LRQ_EINVAL = 1
+LRQ_EUNSUPPORTED = 2
+LRQ_ECUDA = 3
+LRQ_ETIMEOUT = 4
+LRQ_ENOCONV = 5
+LRQ_EWORKSPACE = 6
+
+LRQ_MODE_FP32 = 0
+LRQ_MODE_BF16_TC = 1
+
+_lock = threading.Lock()
+_lib = None
+
+
+class LrqError(RuntimeError):
+    def __init__(self, status: int, where: str, message: str):
+        super().__init__("%s failed with status %d: %s" % (where, status, message))
+        self.status = status
+
+
+def load() -> ctypes.CDLL:
+    """Load liblrq.so from the package directory (built by build.build())."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("liblrq.so is not built (expected at %s); run __graft_entry__.build()" % LIB_PATH)
+        lib = ctypes.CDLL(LIB_PATH)
+        P, I, I64, U64, SZ = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_size_t
+        lib.lrq_status_string.argtypes = [I]
+        lib.lrq_status_string.restype = ctypes.c_char_p
+        lib.lrq_last_error.argtypes = []
+        lib.lrq_last_error.restype = ctypes.c_char_p
+        lib.lrq_abi_version.argtypes = []
+        lib.lrq_abi_version.restype = I
+        lib.lrq_sample_directions.argtypes = [U64, I64, I, P, P]
+        lib.lrq_sample_directions.restype = I
+        lib.lrq_sample_score_workspace_size.argtypes = [I64, I, I, I64, I, I, ctypes.POINTER(SZ)]
+        lib.lrq_sample_score_workspace_size.restype = I
+        lib.lrq_sample_score.argtypes = [P, I64, I, I, P, I, U64, I64, I, I, P, P, P, P, SZ, P, P]
+        lib.lrq_sample_score.restype = I
+        lib.lrq_rescore_workspace_size.argtypes = [I64, I, I, ctypes.POINTER(SZ)]
+        lib.lrq_rescore_workspace_size.restype = I
+        lib.lrq_rescore.argtypes = [P, I64, I, I, P, I64, P, I, P, P, P, P, P, SZ, P, P]
+        lib.lrq_rescore.restype = I
+        lib.lrq_cut_count.argtypes = [P, P, I64, P, P, P]
+        lib.lrq_cut_count.restype = I
+        lib.lrq_set_timing_events.argtypes = [P, P]
+        lib.lrq_set_timing_events.restype = I
+        lib.lrq_kernel_launches.argtypes = []
+        lib.lrq_kernel_launches.restype = ctypes.c_uint64
+        _lib = lib
+        return lib
+
+
+def exported_symbols():
+    """Names of the entry points include/lrq.h declares."""
+    return ["lrq_status_string", "lrq_last_error", "lrq_abi_version", "lrq_sample_directions",
+            "lrq_sample_score_workspace_size", "lrq_sample_score", "lrq_rescore_workspace_size",
+            "lrq_rescore", "lrq_cut_count", "lrq_set_timing_events", "lrq_kernel_launches"]
+
+
+def _check(status: int, where: str):
+    if status != LRQ_OK:
+        lib = load()
+        raise LrqError(status, where, lib.lrq_last_error().decode())
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("device tensor expected")
+    if not t.is_contiguous():
+        raise ValueError("contiguous tensor expected")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def lrq_status_string(status: int) -> str:
+    return load().lrq_status_string(int(status)).decode()
+
+
+def lrq_last_error() -> str:
+    return load().lrq_last_error().decode()
+
+
+def lrq_abi_version() -> int:
+    return int(load().lrq_abi_version())
+
+
+def lrq_sample_directions(seed: int, S: int, r: int, C_out: torch.Tensor, stream=None):
+    assert C_out.dtype == torch.complex64 and C_out.numel() >= S * r
+    _check(load().lrq_sample_directions(int(seed), int(S), int(r), _ptr(C_out), _stream(stream)),
+           "lrq_sample_directions")
+
+
+def lrq_sample_score_workspace_size(n: int, r: int, K: int, S: int, mode: int, top_m: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().lrq_sample_score_workspace_size(int(n), int(r), int(K), int(S), int(mode), int(top_m),
+                                                  ctypes.byref(out)), "lrq_sample_score_workspace_size")
+    return int(out.value)
+
+
+def lrq_sample_score(V: torch.Tensor, K: int, C: torch.Tensor, generate_C: bool, seed: int, mode: int,
+                     top_m: int, scores_out, top_idx_out: torch.Tensor, top_f_out: torch.Tensor,
+                     ws: torch.Tensor, dev_status: torch.Tensor, stream=None):
+    n, r = V.shape
+    S = C.shape[0]
+    assert V.dtype == torch.complex64 and C.dtype == torch.complex64 and C.shape[1] == r
+    assert top_idx_out.dtype == torch.int64 and top_f_out.dtype == torch.float32
+    assert dev_status.dtype == torch.int32
+    _check(load().lrq_sample_score(_ptr(V), n, r, int(K), _ptr(C), int(bool(generate_C)), int(seed), S,
+                                   int(mode), int(top_m), _ptr(scores_out), _ptr(top_idx_out), _ptr(top_f_out),
+                                   _ptr(ws), ws.numel() * ws.element_size(), _ptr(dev_status), _stream(stream)),
+           "lrq_sample_score")
+
+
+def lrq_rescore_workspace_size(n: int, r: int, m: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().lrq_rescore_workspace_size(int(n), int(r), int(m), ctypes.byref(out)),
+           "lrq_rescore_workspace_size")
+    return int(out.value)
+
+
+def lrq_rescore(V: torch.Tensor, K: int, C: torch.Tensor, idx: torch.Tensor, f_out: torch.Tensor, z_out,
+                best_out: torch.Tensor, best_f_out: torch.Tensor, ws: torch.Tensor, dev_status: torch.Tensor,
+                stream=None):
+    n, r = V.shape
+    S = C.shape[0]
+    m = idx.numel()
+    assert idx.dtype == torch.int64 and f_out.dtype == torch.float64
+    _check(load().lrq_rescore(_ptr(V), n, r, int(K), _ptr(C), S, _ptr(idx), m, _ptr(f_out), _ptr(z_out),
+                              _ptr(best_out), _ptr(best_f_out), _ptr(ws), ws.numel() * ws.element_size(),
+                              _ptr(dev_status), _stream(stream)), "lrq_rescore")
+
+
+def lrq_cut_count(rowptr: torch.Tensor, colidx: torch.Tensor, z: torch.Tensor, cut_out: torch.Tensor,
+                  stream=None):
+    assert rowptr.dtype == torch.int32 and colidx.dtype == torch.int32 and z.dtype == torch.uint8
+    _check(load().lrq_cut_count(_ptr(rowptr), _ptr(colidx), rowptr.numel() - 1, _ptr(z), _ptr(cut_out),
+                                _stream(stream)), "lrq_cut_count")
+
+
+def lrq_set_timing_events(start_event, stop_event):
+    """start_event / stop_event: torch.cuda.Event(enable_timing=True) or None."""
+    a = None if start_event is None else ctypes.c_void_p(start_event.cuda_event)
+    b = None if stop_event is None else ctypes.c_void_p(stop_event.cuda_event)
+    _check(load().lrq_set_timing_events(a, b), "lrq_set_timing_events")
+
+
+def lrq_kernel_launches() -> int:
+    return int(load().lrq_kernel_launches())
+
+
+# --------------------------------------------------------------------------
+# Convenience wrappers (allocate outputs and workspace with torch).
+# --------------------------------------------------------------------------
+def workspace(nbytes: int, device) -> torch.Tensor:
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def check_status(dev_status: torch.Tensor, where: str = "device"):
+    s = int(dev_status.item())
+    if s != LRQ_OK:
+        raise LrqError(s, where, lrq_status_string(s))
+
+
+def sample_score(V, K, C=None, S=None, seed=0, mode=LRQ_MODE_BF16_TC, top_m=64, want_scores=False,
+                 ws=None, dev_status=None, stream=None):
+    """Score S directions (given in C, or drawn from `seed` into a new C).
+    Returns dict(C, top_idx, top_f, scores, dev_status)."""
+    dev = V.device
+    n, r = V.shape
+    generate = C is None
+    if generate:
+        C = torch.empty((int(S), r), dtype=torch.complex64, device=dev)
+    S = C.shape[0]
+    need = lrq_sample_score_workspace_size(n, r, K, S, mode, top_m)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    if dev_status is None:
+        dev_status = torch.zeros(1, dtype=torch.int32, device=dev)
+    top_idx = torch.empty(top_m, dtype=torch.int64, device=dev)
+    top_f = torch.empty(top_m, dtype=torch.float32, device=dev)
+    scores = torch.empty(S, dtype=torch.float32, device=dev) if want_scores else None
+    lrq_sample_score(V, K, C, generate, seed, mode, top_m, scores, top_idx, top_f, ws, dev_status, stream)
+    return dict(C=C, top_idx=top_idx, top_f=top_f, scores=scores, dev_status=dev_status, ws=ws)
+
+
+def rescore(V, K, C, idx, want_z=False, ws=None, dev_status=None, stream=None):
+    dev = V.device
+    n, r = V.shape
+    m = idx.numel()
+    need = lrq_rescore_workspace_size(n, r, m)
+    if ws is None or ws.numel() < need:
+        ws = workspace(need, dev)
+    if dev_status is None:
+        dev_status = torch.zeros(1, dtype=torch.int32, device=dev)
+    f = torch.empty(m, dtype=torch.float64, device=dev)
+    z = torch.empty((m, n), dtype=torch.uint8, device=dev) if want_z else None
+    best = torch.empty(1, dtype=torch.int64, device=dev)
+    best_f = torch.empty(1, dtype=torch.float64, device=dev)
+    lrq_rescore(V, K, C, idx, f, z, best, best_f, ws, dev_status, stream)
+    return dict(f=f, z=z, best=best, best_f=best_f, dev_status=dev_status, ws=ws)

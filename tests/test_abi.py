@@ -1,0 +1,95 @@
+"""C-ABI checks that need no GPU: the library loads, exports every entry
+point include/lrq.h declares, and rejects invalid arguments on the host
+before launching anything."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2602_20376_gb300 import build, lrq
+    build.build()
+    return lrq.load()
+
+
+def _declared():
+    text = open(os.path.join(ROOT, "include", "lrq.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(lrq_[a-z0-9_]+)\s*\(", text)))
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    for must in ("lrq_sample_score", "lrq_rescore", "lrq_sample_directions", "lrq_cut_count"):
+        assert must in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    from paper_2602_20376_gb300 import lrq
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert name in lrq.exported_symbols()
+
+
+def test_status_strings(lib):
+    from paper_2602_20376_gb300 import lrq
+    assert lrq.lrq_abi_version() == 1
+    for s in range(7):
+        assert lrq.lrq_status_string(s).startswith("LRQ_")
+    assert "UNKNOWN" in lrq.lrq_status_string(99)
+
+
+def _call_score(lib, **kw):
+    P = ctypes.c_void_p
+    a = dict(V=P(256), n=1000, r=4, K=3, C=P(512), gen=0, seed=0, S=100, mode=1, top_m=10,
+             scores=None, idx=P(1024), f=P(2048), ws=P(4096), ws_bytes=1 << 30, status=P(8192), stream=None)
+    a.update(kw)
+    return lib.lrq_sample_score(a["V"], a["n"], a["r"], a["K"], a["C"], a["gen"], a["seed"], a["S"], a["mode"],
+                                a["top_m"], a["scores"], a["idx"], a["f"], a["ws"], a["ws_bytes"], a["status"],
+                                a["stream"])
+
+
+@pytest.mark.parametrize("kw,code", [
+    (dict(n=0), 1), (dict(r=0), 1), (dict(r=9), 1), (dict(K=1), 1), (dict(K=65), 1),
+    (dict(S=0), 1), (dict(top_m=0), 1), (dict(top_m=101), 1), (dict(top_m=513, S=1000), 1),
+    (dict(mode=7), 1), (dict(K=9), 2), (dict(V=None), 1), (dict(status=None), 1),
+    (dict(ws=None), 6), (dict(ws_bytes=10), 6), (dict(ws=ctypes.c_void_p(4096 + 16)), 6),
+])
+def test_sample_score_rejects_bad_arguments_on_host(lib, kw, code):
+    # invalid arguments return before any launch (no GPU is touched)
+    assert _call_score(lib, **kw) == code
+    assert len(lib.lrq_last_error()) > 0
+
+
+def test_rescore_and_cut_reject_bad_arguments(lib):
+    P = ctypes.c_void_p
+    args = [P(256), 100, 4, 3, P(512), 10, P(1024), 4, P(2048), None, P(4096), P(4100), P(8192), 1 << 20, P(9000),
+            None]
+    bad_m = list(args)
+    bad_m[7] = 0
+    assert lib.lrq_rescore(*bad_m) == 1
+    bad_k = list(args)
+    bad_k[3] = 1
+    assert lib.lrq_rescore(*bad_k) == 1
+    bad_ws = list(args)
+    bad_ws[13] = 1
+    assert lib.lrq_rescore(*bad_ws) == 6
+    assert lib.lrq_cut_count(None, None, 10, None, P(256), None) == 1
+    assert lib.lrq_sample_directions(0, -1, 4, P(256), None) == 1
+    assert lib.lrq_sample_directions(0, 10, 0, P(256), None) == 1
+    assert lib.lrq_set_timing_events(P(256), None) == 1
+
+
+def test_workspace_queries(lib):
+    from paper_2602_20376_gb300 import lrq
+    a = lrq.lrq_sample_score_workspace_size(1 << 20, 4, 3, 1 << 16, lrq.LRQ_MODE_BF16_TC, 64)
+    b = lrq.lrq_sample_score_workspace_size(1 << 20, 4, 3, 1 << 16, lrq.LRQ_MODE_FP32, 64)
+    assert a > b > 0
+    assert lrq.lrq_rescore_workspace_size(1 << 20, 4, 64) > 0
+    with pytest.raises(lrq.LrqError):
+        lrq.lrq_sample_score_workspace_size(1 << 20, 4, 9, 1 << 16, lrq.LRQ_MODE_BF16_TC, 64)

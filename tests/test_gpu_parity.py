@@ -1,0 +1,294 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
+same seeded inputs.
+
+Tolerances (stated here, derived in the design doc):
+* FP32 scoring: f within 1e-5 relative of the oracle.
+* FP64 re-scoring: f within 1e-9 relative; codes equal the oracle's except
+  where the oracle's own angle margin to a boundary is below 1e-9 rad (a tie
+  in FP64 arithmetic).
+* BF16 tensor-core scoring: per-candidate relative error of f below 2e-2
+  (max) and 3e-3 (median) -- the operands are rounded to bfloat16; the
+  winner is decided after the FP64 re-scoring above.
+* Sampler: within 1e-6 of the oracle's Philox + Box-Muller stream.
+* Cuts: exact integers.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2602_20376_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lrq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_20376_gb300 import lrq as L
+    L.load()
+    return L
+
+
+DEV = "cuda:0"
+FP32 = 0
+BF16 = 1
+
+
+def _dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def _score(lrq, V, K, C, mode, top_m, want_scores=True):
+    out = lrq.sample_score(_dev(V), K, C=_dev(C), mode=mode, top_m=top_m, want_scores=want_scores)
+    torch.cuda.synchronize()
+    lrq.check_status(out["dev_status"])
+    return out
+
+
+# ---------------------------------------------------------------------------
+# sampler
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("r,S,seed", [(1, 1000, 3), (4, 4096, 1), (7, 777, 2**40 + 5)])
+def test_sample_directions_match_oracle(lrq, r, S, seed):
+    C = torch.empty((S, r), dtype=torch.complex64, device=DEV)
+    lrq.lrq_sample_directions(seed, S, r, C)
+    torch.cuda.synchronize()
+    ref = O.sphere_sample(seed, S, r)
+    assert np.abs(C.cpu().numpy() - ref).max() < 1e-6
+
+
+# ---------------------------------------------------------------------------
+# FP32 scoring
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,r,K,S", [
+    (1000, 4, 3, 700), (257, 1, 2, 300), (3001, 2, 4, 129), (999, 8, 5, 256), (1500, 3, 8, 100),
+    (700, 4, 13, 64), (2048, 6, 6, 512), (5, 4, 7, 33),
+])
+def test_score_fp32_matches_oracle(lrq, n, r, K, S):
+    V = I.factor(n, r, seed=n + K, scales=np.linspace(2.0, 0.5, r), dtype=np.complex64)
+    C = I.directions(S, r, seed=S + r)
+    out = _score(lrq, V, K, C, FP32, min(16, S))
+    f = out["scores"].cpu().numpy().astype(np.float64)
+    ref = O.score(V, K, C)
+    rel = np.abs(f - ref) / ref
+    assert rel.max() < 1e-5, rel.max()
+    # top-m are the m largest scores, ties to the lower index
+    order = np.lexsort((np.arange(S), -out["scores"].cpu().numpy()))
+    assert np.array_equal(out["top_idx"].cpu().numpy(), order[:min(16, S)])
+
+
+# ---------------------------------------------------------------------------
+# FP64 re-scoring
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("n,r,K,m", [(5000, 4, 3, 40), (1234, 2, 2, 7), (777, 8, 8, 16), (3000, 3, 11, 5)])
+def test_rescore_matches_oracle(lrq, n, r, K, m):
+    V = I.factor(n, r, seed=7 * n + K, dtype=np.complex64)
+    S = 300
+    C = I.directions(S, r, seed=9)
+    idx = I.rng(4).choice(S, m, replace=False).astype(np.int64)
+    res = lrq.rescore(_dev(V), K, _dev(C), _dev(idx), want_z=True)
+    torch.cuda.synchronize()
+    lrq.check_status(res["dev_status"])
+    f_ref, z_ref = O.score(V, K, C[idx], want_z=True)
+    f = res["f"].cpu().numpy()
+    assert np.all(np.abs(f - f_ref) <= 1e-9 * f_ref)
+    marg, _ = O.margins(V, K, C[idx])
+    z = res["z"].cpu().numpy()
+    clear = marg > 1e-9
+    assert np.array_equal(z[clear], z_ref[clear])
+    t = int(np.argmax(f_ref))
+    assert int(res["best"].item()) == idx[t]
+    assert abs(float(res["best_f"].item()) - f_ref[t]) <= 1e-9 * f_ref[t]
+
+
+def test_rescore_rejects_out_of_range_index(lrq):
+    V = I.factor(100, 2, seed=1, dtype=np.complex64)
+    C = I.directions(10, 2, seed=2)
+    idx = np.array([3, 10, 1], dtype=np.int64)
+    res = lrq.rescore(_dev(V), 3, _dev(C), _dev(idx))
+    torch.cuda.synchronize()
+    assert int(res["dev_status"].item()) == lrq.LRQ_EINVAL
+
+
+# ---------------------------------------------------------------------------
+# tensor-core scoring (tcgen05 + TMEM + TMA)
+# ---------------------------------------------------------------------------
+def _check_bf16(lrq, n, r, K, S, top_m, seed=0):
+    V = I.factor(n, r, seed=seed + 11 * n + K, scales=np.linspace(2.0, 0.5, r), dtype=np.complex64)
+    C = I.directions(S, r, seed=seed + S + r)
+    out = _score(lrq, V, K, C, BF16, top_m)
+    f = out["scores"].cpu().numpy().astype(np.float64)
+    ref = O.score(V, K, C)
+    rel = np.abs(f - ref) / ref
+    assert rel.max() < 2e-2, (rel.max(), np.argmax(rel))
+    assert np.median(rel) < 3e-3, np.median(rel)
+    idx = out["top_idx"].cpu().numpy()
+    res = lrq.rescore(_dev(V), K, _dev(C), out["top_idx"])
+    torch.cuda.synchronize()
+    lrq.check_status(res["dev_status"])
+    f64 = res["f"].cpu().numpy()
+    assert np.all(np.abs(f64 - ref[idx]) <= 1e-9 * ref[idx])
+    return rel, ref, idx
+
+
+def test_score_bf16_single_tile(lrq):
+    _check_bf16(lrq, 64, 4, 3, 128, 8)
+
+
+@pytest.mark.parametrize("n,r,K,S", [
+    (1000, 4, 3, 700), (4096, 4, 3, 1024), (333, 1, 3, 200), (2000, 2, 2, 300), (1777, 4, 4, 513),
+    (900, 3, 5, 129), (1300, 5, 6, 260), (640, 8, 7, 128), (2500, 6, 8, 384), (100, 4, 3, 1),
+])
+def test_score_bf16_matches_oracle(lrq, n, r, K, S):
+    _check_bf16(lrq, n, r, K, S, min(8, S))
+
+
+def test_score_bf16_best_of_s_in_top_m(lrq):
+    rel, ref, idx = _check_bf16(lrq, 20000, 4, 3, 2048, 64, seed=5)
+    best = int(np.argmax(ref))
+    srt = np.sort(ref)[::-1]
+    if (srt[0] - srt[63]) / srt[0] > 1e-3:
+        assert best in set(idx.tolist())
+
+
+def test_score_bf16_many_chunks(lrq):
+    # long coordinate axis: several accumulation periods and chunks per item
+    _check_bf16(lrq, 200000, 4, 3, 256, 16)
+
+
+# ---------------------------------------------------------------------------
+# full size of the scale workload (n = 2^20, r = 4, K = 3, S = 2^16), as timed
+# ---------------------------------------------------------------------------
+@pytest.mark.slow
+def test_full_scale_sampled_parity(lrq):
+    n, r, K, S, m = 1 << 20, 4, 3, 1 << 16, 64
+    V = I.factor(n, r, seed=0, scales=(4, 2, 1, 0.5), dtype=np.complex64)
+    Vd = _dev(V)
+    out = lrq.sample_score(Vd, K, S=S, seed=1, mode=BF16, top_m=m, want_scores=True)
+    res = lrq.rescore(Vd, K, out["C"], out["top_idx"])
+    torch.cuda.synchronize()
+    lrq.check_status(out["dev_status"])
+    lrq.check_status(res["dev_status"])
+    C = out["C"].cpu().numpy()
+    assert np.abs(C[:4096] - O.sphere_sample(1, 4096, r)).max() < 1e-6
+    idx = out["top_idx"].cpu().numpy()
+    ref = O.score(V, K, C[idx])
+    f64 = res["f"].cpu().numpy()
+    assert np.all(np.abs(f64 - ref) <= 1e-9 * ref)
+    t = int(np.argmax(ref))
+    assert int(res["best"].item()) == idx[t]
+    # sampled candidates: BF16 scores against the oracle
+    samp = I.rng(3).choice(S, 48, replace=False)
+    f = out["scores"].cpu().numpy()[samp].astype(np.float64)
+    ref_s = O.score(V, K, C[samp])
+    rel = np.abs(f - ref_s) / ref_s
+    assert rel.max() < 2e-2 and np.median(rel) < 3e-3, (rel.max(), np.median(rel))
+
+
+@pytest.mark.slow
+def test_full_scale_planted_rank1(lrq):
+    # V_i = a_i w^{k_i} u^T: every direction scores (sum_i |V_i|)^2 up to the
+    # complex64 rounding of V, and the rounded codes are k_i + j
+    n, r, K, S, m = 1 << 20, 4, 3, 1 << 16, 64
+    V, a, k, u = I.planted_rank1(n, r, K, seed=3)
+    Vd = _dev(V)
+    out = lrq.sample_score(Vd, K, S=S, seed=2, mode=BF16, top_m=m)
+    res = lrq.rescore(Vd, K, out["C"], out["top_idx"], want_z=True)
+    torch.cuda.synchronize()
+    lrq.check_status(out["dev_status"])
+    closed = np.linalg.norm(V.astype(np.complex128), axis=1).sum() ** 2
+    f64 = res["f"].cpu().numpy()
+    assert np.all(np.abs(f64 - closed) <= 1e-6 * closed)
+    C = out["C"].cpu().numpy()
+    idx = out["top_idx"].cpu().numpy()
+    z = res["z"].cpu().numpy()
+    for t in range(4):
+        ang = np.angle(u @ C[idx[t]].astype(np.complex128))
+        j = int(np.round(K * ang / (2 * np.pi))) % K
+        agree = np.mean(z[t] == (k + j) % K)
+        assert agree > 0.999
+
+
+# ---------------------------------------------------------------------------
+# graphs
+# ---------------------------------------------------------------------------
+def test_cut_count_matches_oracle(lrq):
+    rowptr, colidx, labels = I.sbm_graph(100000, 4, 8, seed=2)
+    z = I.rng(9).integers(0, 3, 100000).astype(np.uint8)
+    cut = torch.zeros(1, dtype=torch.int64, device=DEV)
+    lrq.lrq_cut_count(_dev(rowptr), _dev(colidx), _dev(z), cut)
+    torch.cuda.synchronize()
+    assert int(cut.item()) == O.cut_count(rowptr, colidx, z)
+    lrq.lrq_cut_count(_dev(rowptr), _dev(colidx), _dev(labels.astype(np.uint8)), cut)
+    torch.cuda.synchronize()
+    assert int(cut.item()) == O.cut_count(rowptr, colidx, labels.astype(np.uint8))
+
+
+def test_cut_count_torus_checkerboard(lrq):
+    k1, k2 = 100, 60
+    rowptr, colidx = I.torus_graph(k1, k2)
+    z = ((np.arange(k1)[:, None] + np.arange(k2)[None, :]) % 2).ravel().astype(np.uint8)
+    cut = torch.zeros(1, dtype=torch.int64, device=DEV)
+    lrq.lrq_cut_count(_dev(rowptr), _dev(colidx), _dev(z), cut)
+    torch.cuda.synchronize()
+    assert int(cut.item()) == 2 * k1 * k2
+
+
+# ---------------------------------------------------------------------------
+# edge cases
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("mode", [FP32, BF16])
+def test_non_finite_input_reported(lrq, mode):
+    V = I.factor(500, 4, seed=1, dtype=np.complex64)
+    V[123, 2] = np.nan
+    C = I.directions(64, 4, seed=2)
+    out = lrq.sample_score(_dev(V), 3, C=_dev(C), mode=mode, top_m=4)
+    torch.cuda.synchronize()
+    assert int(out["dev_status"].item()) == lrq.LRQ_EINVAL
+
+
+@pytest.mark.parametrize("mode", [FP32, BF16])
+def test_zero_rows_and_tiny_sizes(lrq, mode):
+    V = I.factor(300, 4, seed=5, dtype=np.complex64)
+    V[::7] = 0
+    C = I.directions(1, 4, seed=6)
+    out = _score(lrq, V, 3, C, mode, 1)
+    ref = O.score(V, 3, C)
+    tol = 1e-5 if mode == FP32 else 2e-2
+    assert abs(float(out["scores"][0]) - ref[0]) <= tol * ref[0]
+    assert int(out["top_idx"][0]) == 0
+    V1 = I.factor(1, 2, seed=8, dtype=np.complex64)
+    C1 = I.directions(5, 2, seed=9)
+    out = _score(lrq, V1, 3, C1, mode, 5)
+    ref = O.score(V1, 3, C1)
+    assert np.allclose(out["scores"].cpu().numpy(), ref, rtol=tol)
+    res = lrq.rescore(_dev(V), 3, _dev(I.directions(3, 4, seed=1)), _dev(np.array([0, 1, 2])), want_z=True)
+    torch.cuda.synchronize()
+    assert np.all(res["z"].cpu().numpy()[:, ::7] == 0)  # w = 0 decodes to k = 0
+
+
+def test_generated_directions_are_the_sampler_stream(lrq):
+    V = I.factor(2000, 4, seed=3, dtype=np.complex64)
+    out = lrq.sample_score(_dev(V), 3, S=1000, seed=77, mode=BF16, top_m=4)
+    C = torch.empty((1000, 4), dtype=torch.complex64, device=DEV)
+    lrq.lrq_sample_directions(77, 1000, 4, C)
+    torch.cuda.synchronize()
+    assert torch.equal(out["C"], C)
+
+
+def test_timing_hook_and_launch_counter(lrq):
+    V = _dev(I.factor(4096, 4, seed=3, dtype=np.complex64))
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    n0 = lrq.lrq_kernel_launches()
+    lrq.lrq_set_timing_events(a, b)
+    try:
+        out = lrq.sample_score(V, 3, S=2048, seed=1, mode=BF16, top_m=8)
+    finally:
+        lrq.lrq_set_timing_events(None, None)
+    torch.cuda.synchronize()
+    assert a.elapsed_time(b) > 0
+    assert lrq.lrq_kernel_launches() - n0 >= 5
+    lrq.check_status(out["dev_status"])
