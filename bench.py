@@ -150,6 +150,8 @@ def run_reference(args):
 
 
 def run_ours(args):
+    global S
+    S = args.candidates
     import torch
     import torch.distributed as dist
 
@@ -280,6 +282,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--mode", choices=["bf16", "fp32"], default="bf16")
+    ap.add_argument("--candidates", type=int, default=S,
+                    help="directions per step per GPU (default 2^16; smaller only for profiling runs)")
     ap.add_argument("--cpu-sample", type=int, default=256)
     ap.add_argument("--ref-sample", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")

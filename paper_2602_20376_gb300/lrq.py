@@ -170,6 +170,9 @@ def lrq_cut_count(rowptr: torch.Tensor, colidx: torch.Tensor, z: torch.Tensor, c
 
 def lrq_set_timing_events(start_event, stop_event):
     """start_event / stop_event: torch.cuda.Event(enable_timing=True) or None."""
+    for ev in (start_event, stop_event):
+        if ev is not None and not ev.cuda_event:
+            ev.record()  # torch creates the underlying cudaEvent lazily, on first record
     a = None if start_event is None else ctypes.c_void_p(start_event.cuda_event)
     b = None if stop_event is None else ctypes.c_void_p(stop_event.cuda_event)
     _check(load().lrq_set_timing_events(a, b), "lrq_set_timing_events")

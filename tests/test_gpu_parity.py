@@ -6,9 +6,11 @@ Tolerances (stated here, derived in the design doc):
 * FP64 re-scoring: f within 1e-9 relative; codes equal the oracle's except
   where the oracle's own angle margin to a boundary is below 1e-9 rad (a tie
   in FP64 arithmetic).
-* BF16 tensor-core scoring: per-candidate relative error of f below 2e-2
-  (max) and 3e-3 (median) -- the operands are rounded to bfloat16; the
-  winner is decided after the FP64 re-scoring above.
+* BF16 tensor-core scoring: per candidate, |sqrt(f) - sqrt(f_oracle)| within
+  the bfloat16 error bound of _bf16_bound (decision flips only where the
+  oracle's margin is inside the bf16 projection error, plus operand
+  rounding of the per-class sums); median relative error below 3e-3 for
+  n >= 1000.  The winner is decided after the FP64 re-scoring above.
 * Sampler: within 1e-6 of the oracle's Philox + Box-Muller stream.
 * Cuts: exact integers.
 """
@@ -115,15 +117,44 @@ def test_rescore_rejects_out_of_range_index(lrq):
 # ---------------------------------------------------------------------------
 # tensor-core scoring (tcgen05 + TMEM + TMA)
 # ---------------------------------------------------------------------------
+def _bf16_bound(V, K, C):
+    """Per-candidate bound on |sqrt(f_bf16) - sqrt(f)| for the BF16 mode.
+
+    GEMM1 rounds both operands to bfloat16 (8-bit significand, unit roundoff
+    2^-8), so a projection carries an error of at most
+    2^-7 sum_k |V~_ik| |c~_k| <= 2^-7 sum_j |V_ij|_1 |c_j|_1 (taken here with a
+    factor-2 margin as e_i = 2^-6 sum_j |V_ij|_1 |c_j|_1); a code can differ
+    from the FP64 decision only where |w_i| sin(margin_i) <= e_i.  Each such
+    coordinate moves ||V^H z|| by at most 2 sin(pi/K) |V_i|.  GEMM2 rounds
+    beta_g conj(V_i) to bfloat16: at most 2^-8 sqrt(2) max|beta| |V_i| per
+    coordinate.  FP32 accumulation adds < 1e-5 relative."""
+    V = V.astype(np.complex128)
+    C = C.astype(np.complex128)
+    marg, absw = O.margins(V, K, C)
+    l1v = np.abs(V.real) + np.abs(V.imag)
+    l1c = np.abs(C.real) + np.abs(C.imag)
+    err = 2.0 ** -6 * (l1c @ l1v.T)  # S x n
+    unsure = absw * np.sin(np.minimum(marg, np.pi / 2)) <= err
+    rown = np.linalg.norm(V, axis=1)
+    flip = 2 * np.sin(np.pi / K) * (unsure * rown[None, :]).sum(axis=1)
+    w = np.exp(2j * np.pi * np.arange(K) / K)
+    beta = np.abs(w - 1).max() if K % 2 else np.abs(np.diff(np.append(w, w[0]))).max() / 2
+    rnd = 2.0 ** -8 * np.sqrt(2) * beta * rown.sum()
+    return flip + rnd
+
+
 def _check_bf16(lrq, n, r, K, S, top_m, seed=0):
     V = I.factor(n, r, seed=seed + 11 * n + K, scales=np.linspace(2.0, 0.5, r), dtype=np.complex64)
     C = I.directions(S, r, seed=seed + S + r)
     out = _score(lrq, V, K, C, BF16, top_m)
     f = out["scores"].cpu().numpy().astype(np.float64)
     ref = O.score(V, K, C)
+    bound = _bf16_bound(V, K, C) + 1e-5 * np.sqrt(ref)
+    dev = np.abs(np.sqrt(f) - np.sqrt(ref))
+    assert np.all(dev <= bound), (np.max(dev / bound), np.argmax(dev / bound))
     rel = np.abs(f - ref) / ref
-    assert rel.max() < 2e-2, (rel.max(), np.argmax(rel))
-    assert np.median(rel) < 3e-3, np.median(rel)
+    if n >= 1000:  # statistical: decision flips average out over many coordinates
+        assert np.median(rel) < 3e-3, np.median(rel)
     idx = out["top_idx"].cpu().numpy()
     res = lrq.rescore(_dev(V), K, _dev(C), out["top_idx"])
     torch.cuda.synchronize()
