@@ -145,6 +145,29 @@ int lrq_rescore(const void* V, int64_t n, int r, int K, const void* C, int64_t S
                 size_t ws_bytes, int32_t* dev_status, void* stream);
 
 /* --------------------------------------------------------------------------
+ * lrq_rescore_no_alloc -- lrq_rescore without a workspace argument.
+ *
+ * The paper has no counterpart: this entry point exists for callers that
+ * cannot allocate device memory (a plugin whose host framework owns all
+ * device allocations, a latency-critical path where cudaMalloc / cudaFree may
+ * synchronise the device, a service that forbids allocation after start-up).
+ * It computes exactly what lrq_rescore computes, with the same arguments
+ * minus ws / ws_bytes, and allocates nothing.
+ *
+ * Scratch: a fixed 4 MiB array inside the library (each GPU that loads the
+ * library holds it until the process exits).  Sizes whose scratch need,
+ * lrq_rescore_workspace_size(n, r, m), exceeds 4194304 bytes are rejected
+ * with LRQ_EUNSUPPORTED (e.g. m = 64 works up to n = 2^25).  The first call
+ * on each device looks up the array's device address; make that first call
+ * before any stream capture.  All calls on a device share the array: calls
+ * that overlap on the GPU (e.g. on two streams) race and must be serialised
+ * by the caller.
+ * ------------------------------------------------------------------------ */
+int lrq_rescore_no_alloc(const void* V, int64_t n, int r, int K, const void* C, int64_t S,
+                         const int64_t* idx, int m, double* f_out, uint8_t* z_out, int64_t* best_out,
+                         double* best_f_out, int32_t* dev_status, void* stream);
+
+/* --------------------------------------------------------------------------
  * lrq_cut_count -- exact Max-K-Cut value of an assignment on a graph.
  *
  * Sec. 1: for K = 3 and Q the graph Laplacian the problem is Max-3-Cut.

@@ -64,6 +64,8 @@ def load() -> ctypes.CDLL:
         lib.lrq_rescore_workspace_size.restype = I
         lib.lrq_rescore.argtypes = [P, I64, I, I, P, I64, P, I, P, P, P, P, P, SZ, P, P]
         lib.lrq_rescore.restype = I
+        lib.lrq_rescore_no_alloc.argtypes = [P, I64, I, I, P, I64, P, I, P, P, P, P, P, P]
+        lib.lrq_rescore_no_alloc.restype = I
         lib.lrq_cut_count.argtypes = [P, P, I64, P, P, P]
         lib.lrq_cut_count.restype = I
         lib.lrq_set_timing_events.argtypes = [P, P]
@@ -78,7 +80,7 @@ def exported_symbols():
     """Names of the entry points include/lrq.h declares."""
     return ["lrq_status_string", "lrq_last_error", "lrq_abi_version", "lrq_sample_directions",
             "lrq_sample_score_workspace_size", "lrq_sample_score", "lrq_rescore_workspace_size",
-            "lrq_rescore", "lrq_cut_count", "lrq_set_timing_events", "lrq_kernel_launches"]
+            "lrq_rescore", "lrq_rescore_no_alloc", "lrq_cut_count", "lrq_set_timing_events", "lrq_kernel_launches"]
 
 
 def _check(status: int, where: str):
@@ -159,6 +161,20 @@ def lrq_rescore(V: torch.Tensor, K: int, C: torch.Tensor, idx: torch.Tensor, f_o
     _check(load().lrq_rescore(_ptr(V), n, r, int(K), _ptr(C), S, _ptr(idx), m, _ptr(f_out), _ptr(z_out),
                               _ptr(best_out), _ptr(best_f_out), _ptr(ws), ws.numel() * ws.element_size(),
                               _ptr(dev_status), _stream(stream)), "lrq_rescore")
+
+
+def lrq_rescore_no_alloc(V: torch.Tensor, K: int, C: torch.Tensor, idx: torch.Tensor, f_out: torch.Tensor,
+                         z_out, best_out: torch.Tensor, best_f_out: torch.Tensor, dev_status: torch.Tensor,
+                         stream=None):
+    """lrq_rescore for callers that cannot allocate device memory: the library
+    uses its own fixed 4 MiB scratch array instead of a workspace."""
+    n, r = V.shape
+    S = C.shape[0]
+    m = idx.numel()
+    assert idx.dtype == torch.int64 and f_out.dtype == torch.float64
+    _check(load().lrq_rescore_no_alloc(_ptr(V), n, r, int(K), _ptr(C), S, _ptr(idx), m, _ptr(f_out), _ptr(z_out),
+                                       _ptr(best_out), _ptr(best_f_out), _ptr(dev_status), _stream(stream)),
+           "lrq_rescore_no_alloc")
 
 
 def lrq_cut_count(rowptr: torch.Tensor, colidx: torch.Tensor, z: torch.Tensor, cut_out: torch.Tensor,
