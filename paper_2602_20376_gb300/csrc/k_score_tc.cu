@@ -51,20 +51,34 @@
 namespace lrq {
 
 constexpr int kTcM = 128;
-constexpr int kTcStages = 8;
+constexpr int kTcStages = 12;
 constexpr int kTcFlush = 64;
-constexpr int kTcNE = 2;  // epilogue warpgroups
 constexpr long long kWaitLimit = 2000000000LL;
 
+// Tile shape per alphabet.  TMEM (512 columns) holds, per CTA:
+//   D2  : 2 x 16 columns       GEMM2 accumulators (double-buffered by period)
+//   A2  : 2 x KD2/2 columns    indicator operand of GEMM2 (bf16 pairs)
+//   D1  : 2 x N1 columns       GEMM1 projections
+// ROWS (coordinates per tile) is the largest size whose buffers fit.  NE
+// epilogue warpgroups each round RPE = ROWS / NE coordinates of a tile.
 template <int K>
 struct TcShape {
   static constexpr int BK = (K % 2 == 0) ? K / 2 : K;
   static constexpr int G = (K % 2 == 0) ? K / 2 : K - 1;
-  static constexpr int ROWS = (BK <= 3) ? 64 : 32;
+  static constexpr int ROWS = K == 2 ? 128 : K == 3 ? 48 : K == 4 ? 64 : K == 5 ? 32 : K == 6 ? 48 : K == 7 ? 16 : 32;
+  static constexpr int NE = (ROWS / 16) < 4 ? (ROWS / 16) : 4;
+  static constexpr int RPE = ROWS / NE;
   static constexpr int N1 = BK * ROWS;   // GEMM1 N
   static constexpr int KD2 = G * ROWS;   // GEMM2 reduction length per tile
+  static constexpr int A2COLS = KD2 / 2;
+  static constexpr int D2_COL0 = 0;
+  static constexpr int A2_COL0 = 32;
+  static constexpr int D1_COL0 = A2_COL0 + 2 * A2COLS;
+  static_assert(D1_COL0 + 2 * N1 <= 512, "TMEM budget");
   static_assert(N1 % 16 == 0 && N1 <= 256, "GEMM1 N");
   static_assert(KD2 % 16 == 0, "GEMM2 K");
+  static_assert(RPE == 16 || RPE == 32, "epilogue slice");
+  static constexpr int THREADS = 128 * (1 + NE);
 };
 
 constexpr int align1k(int x) { return (x + 1023) / 1024 * 1024; }
@@ -74,23 +88,26 @@ struct TcLayout {
   using Sh = TcShape<K>;
   static constexpr int N2R = (KCH == 1) ? 8 : 16;         // B2 rows stored per K-chunk
   static constexpr int B2ROWS = Sh::KD2 / 8 * N2R;        // 16-byte rows of B2 per tile
-  static constexpr int B2BOX = (B2ROWS <= 256) ? B2ROWS : B2ROWS / 2;
-  static_assert(B2ROWS % B2BOX == 0 && B2BOX <= 256, "B2 box");
   static constexpr int B1_BYTES = Sh::N1 * 16 * KCH;
   static constexpr int B2_BYTES = B2ROWS * 16;
+  static_assert(B1_BYTES % 256 == 0 && B2_BYTES % 256 == 0, "tiles are whole 256-byte TMA rows");
   static constexpr int B1_OFF_IN_STAGE = 0;
   static constexpr int B2_OFF_IN_STAGE = align1k(B1_BYTES);
   static constexpr int STAGE_BYTES = align1k(B2_OFF_IN_STAGE + B2_BYTES);
   static constexpr uint32_t STAGE_TX = B1_BYTES + B2_BYTES;
   static constexpr int A1_BYTES = kTcM * 16 * KCH;
-  static constexpr int A2_BYTES = kTcM * Sh::KD2 * 2;
   static constexpr int ZERO_BYTES = 4096;
+  static constexpr int ACC_BYTES = kTcM * 16 * 8;
+  static constexpr int FIXED = align1k(2 * A1_BYTES) + ZERO_BYTES + ACC_BYTES + 2048;
+  static constexpr int NST_FIT = (200 * 1024 - FIXED) / STAGE_BYTES;
+  static constexpr int NST = NST_FIT < kTcStages ? NST_FIT : kTcStages;
+  static_assert(NST >= 2, "pipeline depth");
   static constexpr int STAGES_OFF = 0;
-  static constexpr int A1_OFF = STAGES_OFF + kTcStages * STAGE_BYTES;
-  static constexpr int A2_OFF = A1_OFF + align1k(2 * A1_BYTES);
-  static constexpr int ZERO_OFF = A2_OFF + align1k(2 * A2_BYTES);
-  static constexpr int BAR_OFF = ZERO_OFF + ZERO_BYTES;
-  static constexpr int NBARS = 2 * kTcStages + 16 + 1;  // stage pairs, 8 double-buffered pairs, drain
+  static constexpr int A1_OFF = STAGES_OFF + NST * STAGE_BYTES;
+  static constexpr int ZERO_OFF = A1_OFF + align1k(2 * A1_BYTES);
+  static constexpr int ACC_OFF = ZERO_OFF + ZERO_BYTES;   // FP32 two-sum partials, 128 x 16 x (hi, lo)
+  static constexpr int BAR_OFF = ACC_OFF + ACC_BYTES;
+  static constexpr int NBARS = 2 * NST + 16 + 2;  // stage pairs, 8 double-buffered pairs, 2 drains
   static constexpr int USED = BAR_OFF + NBARS * 8 + 16;
   // at least 120 KB so that two CTAs never share an SM (each holds all 512
   // TMEM columns)
@@ -126,8 +143,26 @@ __device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t* v) {
   }
 }
 
+template <int W>
+__device__ __forceinline__ void tmem_st_cols(uint32_t taddr, const uint32_t* v) {
+  if constexpr (W == 16) {
+    ptx::tmem_st_x16(taddr, *reinterpret_cast<const uint32_t(*)[16]>(v));
+  } else {
+    static_assert(W == 8, "store width");
+    ptx::tmem_st_x8(taddr, *reinterpret_cast<const uint32_t(*)[8]>(v));
+  }
+}
+
+// One lane of the warp polls the barrier (keeps shared-memory traffic low);
+// the outcome is broadcast to the warp, which is converged afterwards.
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int lane) {
+  int ok = 1;
+  if (lane == 0) ok = ptx::mbar_wait(bar, parity, abort, kWaitLimit) ? 1 : 0;
+  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
 template <int K, int KCH>
-__global__ void __launch_bounds__(128 * (1 + kTcNE), 1)
+__global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
     score_tc_kernel(const __grid_constant__ CUtensorMap tm_vt, const __grid_constant__ CUtensorMap tm_b2,
                     const __grid_constant__ CUtensorMap tm_ct, TcParams prm, double* __restrict__ partial,
                     int32_t* status) {
@@ -137,14 +172,15 @@ __global__ void __launch_bounds__(128 * (1 + kTcNE), 1)
   constexpr int N1 = Sh::N1;
   constexpr int BK = Sh::BK;
   constexpr int G = Sh::G;
-  constexpr int RPE = ROWS / kTcNE;
-  constexpr uint32_t D1_COL0 = 32;  // D2 double buffer occupies columns 0..31
+  constexpr int NE = Sh::NE;
+  constexpr int RPE = Sh::RPE;
+  constexpr int NST = L::NST;
 
   extern __shared__ __align__(1024) uint8_t smem[];
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
   uint64_t* full_b = bars;
-  uint64_t* empty_b = bars + kTcStages;
-  uint64_t* a1_full = bars + 2 * kTcStages;
+  uint64_t* empty_b = bars + NST;
+  uint64_t* a1_full = bars + 2 * NST;
   uint64_t* a1_empty = a1_full + 2;
   uint64_t* d1_full = a1_full + 4;
   uint64_t* d1_empty = a1_full + 6;
@@ -160,7 +196,7 @@ __global__ void __launch_bounds__(128 * (1 + kTcNE), 1)
   const int lane = threadIdx.x & 31;
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < kTcStages; ++s) {
+    for (int s = 0; s < NST; ++s) {
       ptx::mbar_init(&full_b[s], 1);
       ptx::mbar_init(&empty_b[s], 1);
     }
@@ -168,19 +204,22 @@ __global__ void __launch_bounds__(128 * (1 + kTcNE), 1)
       ptx::mbar_init(&a1_full[b], 1);
       ptx::mbar_init(&a1_empty[b], 1);
       ptx::mbar_init(&d1_full[b], 1);
-      ptx::mbar_init(&d1_empty[b], kTcNE * 128);
-      ptx::mbar_init(&a2_full[b], kTcNE * 128);
+      ptx::mbar_init(&d1_empty[b], NE * 4);  // one arrival per epilogue warp
+      ptx::mbar_init(&a2_full[b], NE * 4);
       ptx::mbar_init(&a2_empty[b], 1);
       ptx::mbar_init(&d2_full[b], 1);
-      ptx::mbar_init(&d2_empty[b], 128);
+      ptx::mbar_init(&d2_empty[b], 4);  // the four warps of epilogue warpgroup 0
     }
     ptx::mbar_init(drain_bar, 1);
+    ptx::mbar_init(drain_bar + 1, 1);
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
   {
     uint4* z = reinterpret_cast<uint4*>(smem + L::ZERO_OFF);
     for (int i = threadIdx.x; i < L::ZERO_BYTES / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
+    uint4* acc = reinterpret_cast<uint4*>(smem + L::ACC_OFF);
+    for (int i = threadIdx.x; i < L::ACC_BYTES / 16; i += blockDim.x) acc[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   ptx::fence_proxy_async_smem();
   if (warp == 0 && lane == 0) {
@@ -222,9 +261,8 @@ __global__ void __launch_bounds__(128 * (1 + kTcNE), 1)
           break;
         }
         ptx::mbar_arrive_expect_tx(&a1_full[ab], L::A1_BYTES);
-        for (int ch = 0; ch < KCH; ++ch)
-          ptx::tma_load_2d(smem + L::A1_OFF + ab * L::A1_BYTES + ch * kTcM * 16, &tm_ct, 0,
-                           static_cast<int>((ct * KCH + ch) * kTcM), &a1_full[ab]);
+        ptx::tma_load_2d(smem + L::A1_OFF + ab * L::A1_BYTES, &tm_ct, 0, static_cast<int>(ct * (L::A1_BYTES / 256)),
+                         &a1_full[ab]);
         ++a1_issued;
         for (int64_t t = t0; t < t1; ++t) {
           if (!ptx::mbar_wait(&empty_b[stage], sphase ^ 1u, abort_flag, kWaitLimit)) {
@@ -234,22 +272,20 @@ __global__ void __launch_bounds__(128 * (1 + kTcNE), 1)
           }
           uint8_t* st = smem + L::STAGES_OFF + stage * L::STAGE_BYTES;
           ptx::mbar_arrive_expect_tx(&full_b[stage], L::STAGE_TX);
-          for (int ch = 0; ch < KCH; ++ch)
-            ptx::tma_load_2d(st + L::B1_OFF_IN_STAGE + ch * N1 * 16, &tm_vt, 0,
-                             static_cast<int>((t * KCH + ch) * N1), &full_b[stage]);
-          for (int p = 0; p < L::B2ROWS; p += L::B2BOX)
-            ptx::tma_load_2d(st + L::B2_OFF_IN_STAGE + p * 16, &tm_b2, 0, static_cast<int>(t * L::B2ROWS + p),
-                             &full_b[stage]);
+          ptx::tma_load_2d(st + L::B1_OFF_IN_STAGE, &tm_vt, 0, static_cast<int>(t * (L::B1_BYTES / 256)),
+                           &full_b[stage]);
+          ptx::tma_load_2d(st + L::B2_OFF_IN_STAGE, &tm_b2, 0, static_cast<int>(t * (L::B2_BYTES / 256)),
+                           &full_b[stage]);
           ++issued;
-          if (++stage == kTcStages) {
+          if (++stage == NST) {
             stage = 0;
             sphase ^= 1u;
           }
         }
       }
       // drain: every issued copy must have landed before the CTA exits
-      for (uint32_t s = 0; s < kTcStages && s < issued; ++s) {
-        uint32_t cnt = issued / kTcStages + (s < issued % kTcStages ? 1u : 0u);
+      for (uint32_t s = 0; s < NST && s < issued; ++s) {
+        uint32_t cnt = issued / NST + (s < issued % NST ? 1u : 0u);
         volatile int never = 0;
         ptx::mbar_wait(&full_b[s], (cnt - 1) & 1u, &never, kWaitLimit);
       }
@@ -260,43 +296,15 @@ __global__ void __launch_bounds__(128 * (1 + kTcNE), 1)
       }
     }
   } else if (warp == 1) {
-    // ------------------------------------------------------------ MMA issuer
+    // ------------------------------------------------------------ GEMM1 issuer
     if (lane == 0) {
       constexpr uint32_t idesc1 = ptx::idesc_bf16_f32(kTcM, N1);
-      constexpr uint32_t idesc2 = ptx::idesc_bf16_f32(kTcM, 16);
-      uint32_t stage = 0, sphase = 0, g = 0, pc = 0, a1c = 0;
+      uint32_t stage = 0, sphase = 0, g = 0, a1c = 0;
       bool ok = true;
-      struct Pend {
-        uint32_t stage, g, pc;
-        bool first, last;
-      } pend{0, 0, 0, false, false};
-      bool has_pend = false;
-      auto issue_gemm2 = [&](const Pend& P) -> bool {
-        const uint32_t b = P.g & 1u;
-        if (!ptx::mbar_wait(&a2_full[b], (P.g >> 1) & 1u, abort_flag, kWaitLimit)) return false;
-        const uint32_t db = P.pc & 1u;
-        if (P.first && !ptx::mbar_wait(&d2_empty[db], ((P.pc >> 1) & 1u) ^ 1u, abort_flag, kWaitLimit))
-          return false;
-        ptx::tc_fence_after();
-        const uint32_t a2 = smem_base + L::A2_OFF + b * L::A2_BYTES;
-        const uint32_t b2 = smem_base + L::STAGES_OFF + P.stage * L::STAGE_BYTES + L::B2_OFF_IN_STAGE;
-        constexpr uint32_t lbo_b2 = L::N2R * 16;
-#pragma unroll
-        for (int q = 0; q < Sh::KD2 / 16; ++q) {
-          const uint64_t ad = ptx::smem_desc(a2 + q * 2 * 2048, 2048, 128);
-          const uint32_t bstart = b2 + q * 2 * lbo_b2;
-          const uint32_t sbo_b2 = (KCH == 2) ? 128u : (smem_base + L::ZERO_OFF - bstart);
-          const uint64_t bd = ptx::smem_desc(bstart, lbo_b2, sbo_b2);
-          ptx::mma_bf16_ss(tmem + db * 16, ad, bd, idesc2, (q > 0 || !P.first) ? 1u : 0u);
-        }
-        ptx::mma_commit(&a2_empty[b]);
-        ptx::mma_commit(&empty_b[P.stage]);
-        if (P.last) ptx::mma_commit(&d2_full[db]);
-        return true;
-      };
       for (int64_t item = blockIdx.x; item < prm.num_items && ok; item += gridDim.x) {
         const int64_t chunk = item / c_tiles;
-        const int64_t t0 = chunk * tpc, t1 = min(prm.n_tiles, t0 + tpc);
+        const int64_t t0 = chunk * tpc;
+        const int ntile = static_cast<int>(min(prm.n_tiles, t0 + tpc) - t0);
         const uint32_t ab = a1c & 1u;
         if (!ptx::mbar_wait(&a1_full[ab], (a1c >> 1) & 1u, abort_flag, kWaitLimit)) {
           give_up();
@@ -305,8 +313,7 @@ __global__ void __launch_bounds__(128 * (1 + kTcNE), 1)
         const uint32_t a1 = smem_base + L::A1_OFF + ab * L::A1_BYTES;
         const uint32_t lbo_a1 = (KCH == 2) ? kTcM * 16u : (smem_base + L::ZERO_OFF - a1);
         const uint64_t adesc = ptx::smem_desc(a1, lbo_a1, 128);
-        for (int64_t t = t0; t < t1; ++t) {
-          const int64_t j = t - t0;
+        for (int j = 0; j < ntile; ++j) {
           const uint32_t b = g & 1u;
           if (!ptx::mbar_wait(&full_b[stage], sphase, abort_flag, kWaitLimit) ||
               !ptx::mbar_wait(&d1_empty[b], ((g >> 1) & 1u) ^ 1u, abort_flag, kWaitLimit)) {
@@ -317,33 +324,74 @@ __global__ void __launch_bounds__(128 * (1 + kTcNE), 1)
           ptx::tc_fence_after();
           const uint32_t b1 = smem_base + L::STAGES_OFF + stage * L::STAGE_BYTES + L::B1_OFF_IN_STAGE;
           const uint32_t lbo_b1 = (KCH == 2) ? N1 * 16u : (smem_base + L::ZERO_OFF - b1);
-          const uint64_t bdesc = ptx::smem_desc(b1, lbo_b1, 128);
-          ptx::mma_bf16_ss(tmem + D1_COL0 + b * N1, adesc, bdesc, idesc1, 0u);
+          ptx::mma_bf16_ss(tmem + Sh::D1_COL0 + b * N1, adesc, ptx::smem_desc(b1, lbo_b1, 128), idesc1, 0u);
           ptx::mma_commit(&d1_full[b]);
-          if (t == t1 - 1) ptx::mma_commit(&a1_empty[ab]);
-          if (has_pend && !issue_gemm2(pend)) {
-            give_up();
-            ok = false;
-            break;
-          }
-          const bool first = (j % F) == 0;
-          const bool last = ((j % F) == F - 1) || (t == t1 - 1);
-          pend = Pend{stage, g, pc, first, last};
-          has_pend = true;
-          if (last) ++pc;
+          if (j == ntile - 1) ptx::mma_commit(&a1_empty[ab]);
           ++g;
-          if (++stage == kTcStages) {
+          if (++stage == NST) {
             stage = 0;
             sphase ^= 1u;
           }
         }
         ++a1c;
       }
-      if (ok && has_pend && !issue_gemm2(pend)) give_up();
       // drain: all issued MMAs complete before TMEM is released
       ptx::mma_commit(drain_bar);
       volatile int never = 0;
       ptx::mbar_wait(drain_bar, 0u, &never, kWaitLimit);
+    }
+  } else if (warp == 2) {
+    // ------------------------------------------------------------ GEMM2 issuer
+    // GEMM2(t) starts only after the epilogue has consumed D1(t), i.e. after
+    // GEMM1(t) completed, so releasing the stage from here also covers the
+    // GEMM1 operands of that stage.
+    if (lane == 0) {
+      constexpr uint32_t idesc2 = ptx::idesc_bf16_f32(kTcM, 16);
+      constexpr uint32_t lbo_b2 = L::N2R * 16;
+      uint32_t stage = 0, g = 0, pc = 0;
+      bool ok = true;
+      for (int64_t item = blockIdx.x; item < prm.num_items && ok; item += gridDim.x) {
+        const int64_t chunk = item / c_tiles;
+        const int64_t t0 = chunk * tpc;
+        const int ntile = static_cast<int>(min(prm.n_tiles, t0 + tpc) - t0);
+        int pos = 0;  // tile position within the accumulation period
+        for (int j = 0; j < ntile; ++j) {
+          const uint32_t b = g & 1u;
+          const uint32_t db = pc & 1u;
+          const bool first = pos == 0;
+          const bool last = (pos == F - 1) || (j == ntile - 1);
+          if (!ptx::mbar_wait(&a2_full[b], (g >> 1) & 1u, abort_flag, kWaitLimit) ||
+              (first && !ptx::mbar_wait(&d2_empty[db], ((pc >> 1) & 1u) ^ 1u, abort_flag, kWaitLimit))) {
+            give_up();
+            ok = false;
+            break;
+          }
+          ptx::tc_fence_after();
+          const uint32_t a2 = tmem + Sh::A2_COL0 + b * Sh::A2COLS;
+          const uint32_t b2 = smem_base + L::STAGES_OFF + stage * L::STAGE_BYTES + L::B2_OFF_IN_STAGE;
+#pragma unroll
+          for (int q = 0; q < Sh::KD2 / 16; ++q) {
+            const uint32_t bstart = b2 + q * 2 * lbo_b2;
+            const uint32_t sbo_b2 = (KCH == 2) ? 128u : (smem_base + L::ZERO_OFF - bstart);
+            ptx::mma_bf16_ts(tmem + Sh::D2_COL0 + db * 16, a2 + q * 8, ptx::smem_desc(bstart, lbo_b2, sbo_b2),
+                             idesc2, (q > 0 || !first) ? 1u : 0u);
+          }
+          ptx::mma_commit(&a2_empty[b]);
+          ptx::mma_commit(&empty_b[stage]);
+          if (last) {
+            ptx::mma_commit(&d2_full[db]);
+            ++pc;
+            pos = 0;
+          } else {
+            ++pos;
+          }
+          ++g;
+          if (++stage == NST) stage = 0;
+        }
+      }
+      ptx::mma_commit(drain_bar + 1);
+      volatile int never = 0;
+      ptx::mbar_wait(drain_bar + 1, 0u, &never, kWaitLimit);
     }
   } else if (warp >= 4) {
     // ------------------------------------------------------------ epilogue
@@ -352,17 +400,16 @@ __global__ void __launch_bounds__(128 * (1 + kTcNE), 1)
     const int row = qtr * 32 + lane; // candidate row within the tile
     const uint32_t lane_base = static_cast<uint32_t>(qtr * 32) << 16;
     uint32_t g = 0, pc = 0;
-    float hi[2 * kMaxRank], lo[2 * kMaxRank];
-#pragma unroll
-    for (int jj = 0; jj < 2 * kMaxRank; ++jj) hi[jj] = lo[jj] = 0.f;
+    float2* acc = reinterpret_cast<float2*>(smem + L::ACC_OFF) + row * 16;  // (hi, lo) per component
     bool ok = true;
     for (int64_t item = blockIdx.x; item < prm.num_items && ok; item += gridDim.x) {
       const int64_t chunk = item / c_tiles, ct = item % c_tiles;
-      const int64_t t0 = chunk * tpc, t1 = min(prm.n_tiles, t0 + tpc);
-      for (int64_t t = t0; t < t1; ++t) {
-        const int64_t j = t - t0;
+      const int64_t t0 = chunk * tpc;
+      const int ntile = static_cast<int>(min(prm.n_tiles, t0 + tpc) - t0);
+      int pos = 0;  // tile position within the accumulation period
+      for (int j = 0; j < ntile; ++j) {
         const uint32_t b = g & 1u;
-        if (!__all_sync(0xffffffffu, ptx::mbar_wait(&d1_full[b], (g >> 1) & 1u, abort_flag, kWaitLimit))) {
+        if (!warp_wait(&d1_full[b], (g >> 1) & 1u, abort_flag, lane)) {
           give_up();
           ok = false;
           break;
@@ -371,10 +418,11 @@ __global__ void __launch_bounds__(128 * (1 + kTcNE), 1)
         uint32_t pl[BK][RPE];
 #pragma unroll
         for (int m = 0; m < BK; ++m)
-          tmem_ld_cols<RPE>(tmem + lane_base + D1_COL0 + b * N1 + m * ROWS + e * RPE, pl[m]);
+          tmem_ld_cols<RPE>(tmem + lane_base + Sh::D1_COL0 + b * N1 + m * ROWS + e * RPE, pl[m]);
         ptx::tmem_wait_ld();
         ptx::tc_fence_before();
-        ptx::mbar_arrive(&d1_empty[b]);
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&d1_empty[b]);
         // indicator words: word p holds rows (2p, 2p+1) of this slice
         uint32_t wv[G][RPE / 2];
 #pragma unroll
@@ -390,52 +438,53 @@ __global__ void __launch_bounds__(128 * (1 + kTcNE), 1)
               wv[gc][p] = (nm[gc] & 0x80008000u) | 0x3F803F80u;  // sign(p_m) as +-1
           }
         }
-        if (!__all_sync(0xffffffffu, ptx::mbar_wait(&a2_empty[b], ((g >> 1) & 1u) ^ 1u, abort_flag, kWaitLimit))) {
+        if (!warp_wait(&a2_empty[b], ((g >> 1) & 1u) ^ 1u, abort_flag, lane)) {
           give_up();
           ok = false;
           break;
         }
-        uint8_t* a2 = smem + L::A2_OFF + b * L::A2_BYTES + (row >> 3) * 128 + (row & 7) * 16;
+        ptx::tc_fence_after();
 #pragma unroll
-        for (int gc = 0; gc < G; ++gc) {
-#pragma unroll
-          for (int c = 0; c < RPE / 8; ++c) {
-            const int kchunk = (gc * ROWS + e * RPE) / 8 + c;
-            *reinterpret_cast<uint4*>(a2 + kchunk * 2048) =
-                make_uint4(wv[gc][4 * c], wv[gc][4 * c + 1], wv[gc][4 * c + 2], wv[gc][4 * c + 3]);
-          }
-        }
-        ptx::fence_proxy_async_smem();
-        ptx::mbar_arrive(&a2_full[b]);
-        const bool last = ((j % F) == F - 1) || (t == t1 - 1);
+        for (int gc = 0; gc < G; ++gc)
+          tmem_st_cols<RPE / 2>(tmem + lane_base + Sh::A2_COL0 + b * Sh::A2COLS + (gc * ROWS + e * RPE) / 2,
+                                wv[gc]);
+        ptx::tmem_wait_st();
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&a2_full[b]);
+        const bool last = (pos == F - 1) || (j == ntile - 1);
+        pos = last ? 0 : pos + 1;
         if (e == 0 && last) {
           const uint32_t db = pc & 1u;
-          if (!__all_sync(0xffffffffu, ptx::mbar_wait(&d2_full[db], (pc >> 1) & 1u, abort_flag, kWaitLimit))) {
+          if (!warp_wait(&d2_full[db], (pc >> 1) & 1u, abort_flag, lane)) {
             give_up();
             ok = false;
             break;
           }
           ptx::tc_fence_after();
           uint32_t dv[16];
-          ptx::tmem_ld_x16(tmem + lane_base + db * 16, dv);
+          ptx::tmem_ld_x16(tmem + lane_base + Sh::D2_COL0 + db * 16, dv);
           ptx::tmem_wait_ld();
           ptx::tc_fence_before();
-          ptx::mbar_arrive(&d2_empty[db]);
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&d2_empty[db]);
+          const int r2 = 2 * prm.r;
+          const bool item_end = (j == ntile - 1);
+          double* out = partial + (chunk * prm.S_pad + ct * kTcM + row) * r2;
 #pragma unroll
           for (int jj = 0; jj < 2 * kMaxRank; ++jj) {
-            float s, er;
-            two_sum_f(hi[jj], __uint_as_float(dv[jj]), s, er);
-            hi[jj] = s;
-            lo[jj] += er;
-          }
-          if (t == t1 - 1) {
-            const int r2 = 2 * prm.r;
-            double* out = partial + (chunk * prm.S_pad + ct * kTcM + row) * r2;
-#pragma unroll
-            for (int jj = 0; jj < 2 * kMaxRank; ++jj)
-              if (jj < r2) out[jj] = static_cast<double>(hi[jj]) + static_cast<double>(lo[jj]);
-#pragma unroll
-            for (int jj = 0; jj < 2 * kMaxRank; ++jj) hi[jj] = lo[jj] = 0.f;
+            if (jj < r2) {
+              float2 hl = acc[jj];
+              float s, er;
+              two_sum_f(hl.x, __uint_as_float(dv[jj]), s, er);
+              hl.x = s;
+              hl.y += er;
+              if (item_end) {
+                out[jj] = static_cast<double>(hl.x) + static_cast<double>(hl.y);
+                hl = make_float2(0.f, 0.f);
+              }
+              acc[jj] = hl;
+            }
           }
         }
         if (last) ++pc;
@@ -609,12 +658,18 @@ static EncodeTiledFn get_encode_fn() {
   return fn;
 }
 
-static int make_rows_map(CUtensorMap* map, const void* base, int64_t rows, int box_rows) {
+// Every packed operand tile is a contiguous byte range whose size is a
+// multiple of 256 bytes, so the buffer is viewed as rows of 128 bf16 (256 B)
+// and one box of (tile bytes / 256) rows copies a whole tile.  Wide rows keep
+// the TMA requests at full 32-byte-sector efficiency.
+static int make_rows_map(CUtensorMap* map, const void* base, size_t total_bytes, int tile_bytes) {
   EncodeTiledFn enc = get_encode_fn();
   if (!enc) return fail(LRQ_ECUDA, "cuTensorMapEncodeTiled is unavailable");
-  cuuint64_t dims[2] = {8, static_cast<cuuint64_t>(rows)};
-  cuuint64_t strides[1] = {16};
-  cuuint32_t box[2] = {8, static_cast<cuuint32_t>(box_rows)};
+  if (total_bytes % 256 != 0 || tile_bytes % 256 != 0 || tile_bytes / 256 > 256)
+    return fail(LRQ_EUNSUPPORTED, "packed operand tile is not a whole number of 256-byte rows");
+  cuuint64_t dims[2] = {128, static_cast<cuuint64_t>(total_bytes / 256)};
+  cuuint64_t strides[1] = {256};
+  cuuint32_t box[2] = {128, static_cast<cuuint32_t>(tile_bytes / 256)};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -630,9 +685,9 @@ static int score_impl(const ScorePlan& p, const void* vt, const void* b2, const 
   using L = TcLayout<K, KCH>;
   CUtensorMap m_vt, m_b2, m_ct;
   int e;
-  if ((e = make_rows_map(&m_vt, vt, p.n_tiles * KCH * Sh::N1, Sh::N1))) return e;
-  if ((e = make_rows_map(&m_b2, b2, p.n_tiles * L::B2ROWS, L::B2BOX))) return e;
-  if ((e = make_rows_map(&m_ct, ct, p.c_tiles * KCH * kTcM, kTcM))) return e;
+  if ((e = make_rows_map(&m_vt, vt, static_cast<size_t>(p.n_tiles) * L::B1_BYTES, L::B1_BYTES))) return e;
+  if ((e = make_rows_map(&m_b2, b2, static_cast<size_t>(p.n_tiles) * L::B2_BYTES, L::B2_BYTES))) return e;
+  if ((e = make_rows_map(&m_ct, ct, static_cast<size_t>(p.c_tiles) * L::A1_BYTES, L::A1_BYTES))) return e;
   static std::once_flag attr_once;
   static cudaError_t attr_err = cudaSuccess;
   std::call_once(attr_once, []() {
@@ -648,7 +703,7 @@ static int score_impl(const ScorePlan& p, const void* vt, const void* b2, const 
   prm.r = p.r;
   prm.flush = kTcFlush;
   int grid = static_cast<int>(std::min<int64_t>(prm.num_items, num_sms_current()));
-  score_tc_kernel<K, KCH><<<grid, 128 * (1 + kTcNE), L::TOTAL, st>>>(m_vt, m_b2, m_ct, prm, partial, status);
+  score_tc_kernel<K, KCH><<<grid, Sh::THREADS, L::TOTAL, st>>>(m_vt, m_b2, m_ct, prm, partial, status);
   count_launch();
   return cuda_check(cudaGetLastError(), "score_tc_kernel");
 }

@@ -8,7 +8,7 @@
 
 #include <string>
 
-#include "../../include/lrq.h"
+#include "lrq.h"  // include/ is on the compiler include path
 
 namespace lrq {
 
