@@ -309,7 +309,7 @@ int launch_finalize(const ScorePlan& p, const Alphabet& a, const double* partial
                     float* scores, uint64_t* keys, cudaStream_t st) {
   (void)a;
   int64_t S_pad = p.c_tiles * 128;
-  finalize_kernel<<<static_cast<unsigned>(ceil_div(p.S, 256)), 256, 0, st>>>(partial, p.nsplit, p.S, S_pad, p.r,
+  finalize_kernel<<<static_cast<unsigned>(ceil_div(p.S, 256)), 256, 0, st>>>(partial, p.npart, p.S, S_pad, p.r,
                                                                              T, scores, keys);
   count_launch();
   return cuda_check(cudaGetLastError(), "finalize_kernel");

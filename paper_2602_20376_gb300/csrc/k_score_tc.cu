@@ -51,34 +51,34 @@
 namespace lrq {
 
 constexpr int kTcM = 128;
-constexpr int kTcStages = 12;
+constexpr int kTcStages = 8;
 constexpr int kTcFlush = 64;
 constexpr long long kWaitLimit = 2000000000LL;
 
-// Tile shape per alphabet.  TMEM (512 columns) holds, per CTA:
-//   D2  : 2 x 16 columns       GEMM2 accumulators (double-buffered by period)
-//   A2  : 2 x KD2/2 columns    indicator operand of GEMM2 (bf16 pairs)
-//   D1  : 2 x N1 columns       GEMM1 projections
-// ROWS (coordinates per tile) is the largest size whose buffers fit.  NE
-// epilogue warpgroups each round RPE = ROWS / NE coordinates of a tile.
+// Tile shape per alphabet.  A CTA runs NW independent workers; each worker is
+// one warpgroup (128 threads, one per candidate of the tile) plus a producer
+// thread, and owns a TMEM slice of WCOLS columns:
+//   D1 : N1 = BK * R columns    GEMM1 projections of one tile
+//   A2 : KD2 / 2 columns         GEMM2 indicator operand (bf16 pairs)
+//   D2 : 16 columns              GEMM2 accumulator
+// NW * WCOLS <= 512.  R is the number of coordinates per tile.
 template <int K>
 struct TcShape {
   static constexpr int BK = (K % 2 == 0) ? K / 2 : K;
   static constexpr int G = (K % 2 == 0) ? K / 2 : K - 1;
-  static constexpr int ROWS = K == 2 ? 128 : K == 3 ? 48 : K == 4 ? 64 : K == 5 ? 32 : K == 6 ? 48 : K == 7 ? 16 : 32;
-  static constexpr int NE = (ROWS / 16) < 4 ? (ROWS / 16) : 4;
-  static constexpr int RPE = ROWS / NE;
-  static constexpr int N1 = BK * ROWS;   // GEMM1 N
-  static constexpr int KD2 = G * ROWS;   // GEMM2 reduction length per tile
+  static constexpr int NW = K == 2 ? 4 : K == 3 ? 3 : K == 4 ? 4 : K == 5 ? 2 : K == 6 ? 3 : K == 7 ? 2 : 2;
+  static constexpr int R = K == 2 ? 64 : K == 7 ? 16 : 32;
+  static constexpr int ROWS = R;  // coordinates per tile (packing granularity)
+  static constexpr int N1 = BK * R;    // GEMM1 N
+  static constexpr int KD2 = G * R;    // GEMM2 reduction length per tile
   static constexpr int A2COLS = KD2 / 2;
-  static constexpr int D2_COL0 = 0;
-  static constexpr int A2_COL0 = 32;
-  static constexpr int D1_COL0 = A2_COL0 + 2 * A2COLS;
-  static_assert(D1_COL0 + 2 * N1 <= 512, "TMEM budget");
+  static constexpr int WCOLS = N1 + A2COLS + 16;
+  static constexpr int D1_OFF = 0, A2_OFF = N1, D2_OFF = N1 + A2COLS;
+  static_assert(NW * WCOLS <= 512, "TMEM budget");
   static_assert(N1 % 16 == 0 && N1 <= 256, "GEMM1 N");
   static_assert(KD2 % 16 == 0, "GEMM2 K");
-  static_assert(RPE == 16 || RPE == 32, "epilogue slice");
-  static constexpr int THREADS = 128 * (1 + NE);
+  static_assert(R % 16 == 0, "rows are processed 16 at a time");
+  static constexpr int THREADS = 128 + 128 * NW;
 };
 
 constexpr int align1k(int x) { return (x + 1023) / 1024 * 1024; }
@@ -96,19 +96,20 @@ struct TcLayout {
   static constexpr int STAGE_BYTES = align1k(B2_OFF_IN_STAGE + B2_BYTES);
   static constexpr uint32_t STAGE_TX = B1_BYTES + B2_BYTES;
   static constexpr int A1_BYTES = kTcM * 16 * KCH;
+  static constexpr int ACC_BYTES = kTcM * 16 * 8;         // two-sum partials, 128 x 16 x (hi, lo)
   static constexpr int ZERO_BYTES = 4096;
-  static constexpr int ACC_BYTES = kTcM * 16 * 8;
-  static constexpr int FIXED = align1k(2 * A1_BYTES) + ZERO_BYTES + ACC_BYTES + 2048;
-  static constexpr int NST_FIT = (200 * 1024 - FIXED) / STAGE_BYTES;
-  static constexpr int NST = NST_FIT < kTcStages ? NST_FIT : kTcStages;
-  static_assert(NST >= 2, "pipeline depth");
-  static constexpr int STAGES_OFF = 0;
-  static constexpr int A1_OFF = STAGES_OFF + NST * STAGE_BYTES;
-  static constexpr int ZERO_OFF = A1_OFF + align1k(2 * A1_BYTES);
-  static constexpr int ACC_OFF = ZERO_OFF + ZERO_BYTES;   // FP32 two-sum partials, 128 x 16 x (hi, lo)
-  static constexpr int BAR_OFF = ACC_OFF + ACC_BYTES;
-  static constexpr int NBARS = 2 * NST + 16 + 2;  // stage pairs, 8 double-buffered pairs, 2 drains
-  static constexpr int USED = BAR_OFF + NBARS * 8 + 16;
+  static constexpr int WFIXED = align1k(2 * A1_BYTES) + ACC_BYTES;
+  static constexpr int NST_FIT = (200 * 1024 - ZERO_BYTES - 4096 - Sh::NW * WFIXED) / (Sh::NW * STAGE_BYTES);
+  static constexpr int NST = NST_FIT < kTcStages ? NST_FIT : kTcStages;  // stages per worker
+  static_assert(NST >= 3, "pipeline depth");
+  static constexpr int WSMEM = NST * STAGE_BYTES + WFIXED;  // per worker: stages | A1 x 2 | ACC
+  static constexpr int W_A1 = NST * STAGE_BYTES;
+  static constexpr int W_ACC = W_A1 + align1k(2 * A1_BYTES);
+  static constexpr int ZERO_OFF = Sh::NW * WSMEM;
+  static constexpr int BAR_OFF = ZERO_OFF + ZERO_BYTES;
+  // per worker: full / empty per stage, A1 full / empty pairs, D1-full, D2-ready, 4 drains
+  static constexpr int WBARS = 2 * NST + 4 + 2 + 4;
+  static constexpr int USED = BAR_OFF + Sh::NW * WBARS * 8 + 16;
   // at least 120 KB so that two CTAs never share an SM (each holds all 512
   // TMEM columns)
   static constexpr int TOTAL = USED < 120 * 1024 ? 120 * 1024 : USED;
@@ -132,33 +133,33 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   e = (a - (s - bb)) + (b - bb);
 }
 
-template <int RPE>
-__device__ __forceinline__ void tmem_ld_cols(uint32_t taddr, uint32_t* v) {
-  if constexpr (RPE == 32) {
-    ptx::tmem_ld_x32(taddr, v);
-  } else {
-    static_assert(RPE == 16, "slice width");
-    uint32_t (&vv)[16] = *reinterpret_cast<uint32_t(*)[16]>(v);
-    ptx::tmem_ld_x16(taddr, vv);
-  }
-}
-
-template <int W>
-__device__ __forceinline__ void tmem_st_cols(uint32_t taddr, const uint32_t* v) {
-  if constexpr (W == 16) {
-    ptx::tmem_st_x16(taddr, *reinterpret_cast<const uint32_t(*)[16]>(v));
-  } else {
-    static_assert(W == 8, "store width");
-    ptx::tmem_st_x8(taddr, *reinterpret_cast<const uint32_t(*)[8]>(v));
-  }
-}
-
 // One lane of the warp polls the barrier (keeps shared-memory traffic low);
 // the outcome is broadcast to the warp, which is converged afterwards.
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int lane) {
   int ok = 1;
   if (lane == 0) ok = ptx::mbar_wait(bar, parity, abort, kWaitLimit) ? 1 : 0;
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
+}
+
+// GEMM1 of one tile of a worker: wait for the stage's operands, then
+// D1 = A1[ab] x Vaug(stage)^T and commit to d1_full.  wsm_s is the shared
+// address of the worker's region.
+template <class L>
+__device__ __forceinline__ bool tc_issue_gemm1(uint32_t tw, uint32_t wsm_s, uint32_t smem_base, uint64_t* full_b,
+                                               uint64_t* d1_full, uint32_t stage, uint32_t sphase, uint32_t ab,
+                                               volatile int* abort) {
+  using Sh = typename L::Sh;
+  constexpr bool two_chunks = (L::N2R == 16);
+  if (!ptx::mbar_wait(&full_b[stage], sphase, abort, kWaitLimit)) return false;
+  ptx::tc_fence_after();
+  const uint32_t a1 = wsm_s + L::W_A1 + ab * L::A1_BYTES;
+  const uint32_t lbo_a1 = two_chunks ? kTcM * 16u : (smem_base + L::ZERO_OFF - a1);
+  const uint32_t b1 = wsm_s + stage * L::STAGE_BYTES + L::B1_OFF_IN_STAGE;
+  const uint32_t lbo_b1 = two_chunks ? Sh::N1 * 16u : (smem_base + L::ZERO_OFF - b1);
+  ptx::mma_bf16_ss(tw + Sh::D1_OFF, ptx::smem_desc(a1, lbo_a1, 128), ptx::smem_desc(b1, lbo_b1, 128),
+                   ptx::idesc_bf16_f32(kTcM, Sh::N1), 0u);
+  ptx::mma_commit(d1_full);
+  return true;
 }
 
 template <int K, int KCH>
@@ -168,58 +169,37 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
                     int32_t* status) {
   using Sh = TcShape<K>;
   using L = TcLayout<K, KCH>;
-  constexpr int ROWS = Sh::ROWS;
-  constexpr int N1 = Sh::N1;
+  constexpr int R = Sh::R;
   constexpr int BK = Sh::BK;
   constexpr int G = Sh::G;
-  constexpr int NE = Sh::NE;
-  constexpr int RPE = Sh::RPE;
+  constexpr int NW = Sh::NW;
   constexpr int NST = L::NST;
 
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
-  uint64_t* full_b = bars;
-  uint64_t* empty_b = bars + NST;
-  uint64_t* a1_full = bars + 2 * NST;
-  uint64_t* a1_empty = a1_full + 2;
-  uint64_t* d1_full = a1_full + 4;
-  uint64_t* d1_empty = a1_full + 6;
-  uint64_t* a2_full = a1_full + 8;
-  uint64_t* a2_empty = a1_full + 10;
-  uint64_t* d2_full = a1_full + 12;
-  uint64_t* d2_empty = a1_full + 14;
-  uint64_t* drain_bar = a1_full + 16;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + L::NBARS);
-  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::BAR_OFF + NW * L::WBARS * 8);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   if (threadIdx.x == 0) {
-    for (int s = 0; s < NST; ++s) {
-      ptx::mbar_init(&full_b[s], 1);
-      ptx::mbar_init(&empty_b[s], 1);
+    for (int w = 0; w < NW; ++w) {
+      uint64_t* wb = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF) + w * L::WBARS;
+      for (int s = 0; s < NST; ++s) {
+        ptx::mbar_init(&wb[s], 1);        // stage landed (TMA)
+        ptx::mbar_init(&wb[NST + s], 1);  // stage consumed (GEMM2 commit)
+      }
+      for (int i = 2 * NST; i < L::WBARS; ++i) ptx::mbar_init(&wb[i], 1);
     }
-    for (int b = 0; b < 2; ++b) {
-      ptx::mbar_init(&a1_full[b], 1);
-      ptx::mbar_init(&a1_empty[b], 1);
-      ptx::mbar_init(&d1_full[b], 1);
-      ptx::mbar_init(&d1_empty[b], NE * 4);  // one arrival per epilogue warp
-      ptx::mbar_init(&a2_full[b], NE * 4);
-      ptx::mbar_init(&a2_empty[b], 1);
-      ptx::mbar_init(&d2_full[b], 1);
-      ptx::mbar_init(&d2_empty[b], 4);  // the four warps of epilogue warpgroup 0
-    }
-    ptx::mbar_init(drain_bar, 1);
-    ptx::mbar_init(drain_bar + 1, 1);
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
   {
     uint4* z = reinterpret_cast<uint4*>(smem + L::ZERO_OFF);
     for (int i = threadIdx.x; i < L::ZERO_BYTES / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
-    uint4* acc = reinterpret_cast<uint4*>(smem + L::ACC_OFF);
-    for (int i = threadIdx.x; i < L::ACC_BYTES / 16; i += blockDim.x) acc[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int w = 0; w < NW; ++w) {
+      uint4* acc = reinterpret_cast<uint4*>(smem + w * L::WSMEM + L::W_ACC);
+      for (int i = threadIdx.x; i < L::ACC_BYTES / 16; i += blockDim.x) acc[i] = make_uint4(0u, 0u, 0u, 0u);
+    }
   }
   ptx::fence_proxy_async_smem();
   if (warp == 0 && lane == 0) {
@@ -240,37 +220,48 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
   const int64_t c_tiles = prm.c_tiles;
   const int64_t tpc = prm.tiles_per_chunk;
   const int F = prm.flush;
+  const int64_t workers = static_cast<int64_t>(gridDim.x) * NW;
 
-  auto give_up = [&]() {
-    *abort_flag = 1;
-    dev_fail(status, LRQ_ETIMEOUT);
-  };
+  // worker index within the CTA: producers are warps 0..NW-1, warpgroups follow
+  const int w = (warp < 4) ? warp : (warp - 4) >> 2;
+  const int64_t gw = static_cast<int64_t>(blockIdx.x) * NW + w;  // global worker id
+  uint8_t* wsm = smem + w * L::WSMEM;
+  const uint32_t wsm_s = smem_base + w * L::WSMEM;
+  uint64_t* wb = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF) + w * L::WBARS;
+  uint64_t* full_b = wb;
+  uint64_t* empty_b = wb + NST;
+  uint64_t* a1_full = wb + 2 * NST;
+  uint64_t* a1_empty = a1_full + 2;
+  uint64_t* d1_full = a1_full + 4;
+  uint64_t* d2_ready = a1_full + 5;
+  uint64_t* drain_bar = a1_full + 6;  // [4]
 
-  if (warp == 0) {
-    // ------------------------------------------------------------ producer
+  if (warp < NW) {
+    // ------------------------------------------------------------ producer of worker w
     uint32_t issued = 0, a1_issued = 0;
     if (lane == 0) {
       uint32_t stage = 0, sphase = 0;
       bool ok = true;
-      for (int64_t item = blockIdx.x; item < prm.num_items && ok; item += gridDim.x) {
+      for (int64_t item = gw; item < prm.num_items && ok; item += workers) {
         const int64_t chunk = item / c_tiles, ct = item % c_tiles;
-        const int64_t t0 = chunk * tpc, t1 = min(prm.n_tiles, t0 + tpc);
+        const int64_t t0 = chunk * tpc;
+        const int ntile = static_cast<int>(min(prm.n_tiles, t0 + tpc) - t0);
         const uint32_t ab = a1_issued & 1u;
         if (!ptx::mbar_wait(&a1_empty[ab], ((a1_issued >> 1) & 1u) ^ 1u, abort_flag, kWaitLimit)) {
-          give_up();
+          ok = false;
           break;
         }
         ptx::mbar_arrive_expect_tx(&a1_full[ab], L::A1_BYTES);
-        ptx::tma_load_2d(smem + L::A1_OFF + ab * L::A1_BYTES, &tm_ct, 0, static_cast<int>(ct * (L::A1_BYTES / 256)),
+        ptx::tma_load_2d(wsm + L::W_A1 + ab * L::A1_BYTES, &tm_ct, 0, static_cast<int>(ct * (L::A1_BYTES / 256)),
                          &a1_full[ab]);
         ++a1_issued;
-        for (int64_t t = t0; t < t1; ++t) {
+        for (int j = 0; j < ntile; ++j) {
           if (!ptx::mbar_wait(&empty_b[stage], sphase ^ 1u, abort_flag, kWaitLimit)) {
-            give_up();
             ok = false;
             break;
           }
-          uint8_t* st = smem + L::STAGES_OFF + stage * L::STAGE_BYTES;
+          uint8_t* st = wsm + stage * L::STAGE_BYTES;
+          const int64_t t = t0 + j;
           ptx::mbar_arrive_expect_tx(&full_b[stage], L::STAGE_TX);
           ptx::tma_load_2d(st + L::B1_OFF_IN_STAGE, &tm_vt, 0, static_cast<int>(t * (L::B1_BYTES / 256)),
                            &full_b[stage]);
@@ -283,193 +274,162 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
           }
         }
       }
+      if (!ok) {
+        *abort_flag = 1;
+        dev_fail(status, LRQ_ETIMEOUT);
+      }
       // drain: every issued copy must have landed before the CTA exits
+      volatile int never = 0;
       for (uint32_t s = 0; s < NST && s < issued; ++s) {
         uint32_t cnt = issued / NST + (s < issued % NST ? 1u : 0u);
-        volatile int never = 0;
         ptx::mbar_wait(&full_b[s], (cnt - 1) & 1u, &never, kWaitLimit);
       }
       for (uint32_t b = 0; b < 2 && b < a1_issued; ++b) {
         uint32_t cnt = a1_issued / 2 + (b < a1_issued % 2 ? 1u : 0u);
-        volatile int never = 0;
         ptx::mbar_wait(&a1_full[b], (cnt - 1) & 1u, &never, kWaitLimit);
       }
     }
-  } else if (warp == 1) {
-    // ------------------------------------------------------------ GEMM1 issuer
-    if (lane == 0) {
-      constexpr uint32_t idesc1 = ptx::idesc_bf16_f32(kTcM, N1);
-      uint32_t stage = 0, sphase = 0, g = 0, a1c = 0;
-      bool ok = true;
-      for (int64_t item = blockIdx.x; item < prm.num_items && ok; item += gridDim.x) {
-        const int64_t chunk = item / c_tiles;
-        const int64_t t0 = chunk * tpc;
-        const int ntile = static_cast<int>(min(prm.n_tiles, t0 + tpc) - t0);
-        const uint32_t ab = a1c & 1u;
-        if (!ptx::mbar_wait(&a1_full[ab], (a1c >> 1) & 1u, abort_flag, kWaitLimit)) {
-          give_up();
-          break;
-        }
-        const uint32_t a1 = smem_base + L::A1_OFF + ab * L::A1_BYTES;
-        const uint32_t lbo_a1 = (KCH == 2) ? kTcM * 16u : (smem_base + L::ZERO_OFF - a1);
-        const uint64_t adesc = ptx::smem_desc(a1, lbo_a1, 128);
-        for (int j = 0; j < ntile; ++j) {
-          const uint32_t b = g & 1u;
-          if (!ptx::mbar_wait(&full_b[stage], sphase, abort_flag, kWaitLimit) ||
-              !ptx::mbar_wait(&d1_empty[b], ((g >> 1) & 1u) ^ 1u, abort_flag, kWaitLimit)) {
-            give_up();
-            ok = false;
-            break;
-          }
-          ptx::tc_fence_after();
-          const uint32_t b1 = smem_base + L::STAGES_OFF + stage * L::STAGE_BYTES + L::B1_OFF_IN_STAGE;
-          const uint32_t lbo_b1 = (KCH == 2) ? N1 * 16u : (smem_base + L::ZERO_OFF - b1);
-          ptx::mma_bf16_ss(tmem + Sh::D1_COL0 + b * N1, adesc, ptx::smem_desc(b1, lbo_b1, 128), idesc1, 0u);
-          ptx::mma_commit(&d1_full[b]);
-          if (j == ntile - 1) ptx::mma_commit(&a1_empty[ab]);
-          ++g;
-          if (++stage == NST) {
-            stage = 0;
-            sphase ^= 1u;
-          }
-        }
-        ++a1c;
-      }
-      // drain: all issued MMAs complete before TMEM is released
-      ptx::mma_commit(drain_bar);
-      volatile int never = 0;
-      ptx::mbar_wait(drain_bar, 0u, &never, kWaitLimit);
-    }
-  } else if (warp == 2) {
-    // ------------------------------------------------------------ GEMM2 issuer
-    // GEMM2(t) starts only after the epilogue has consumed D1(t), i.e. after
-    // GEMM1(t) completed, so releasing the stage from here also covers the
-    // GEMM1 operands of that stage.
-    if (lane == 0) {
-      constexpr uint32_t idesc2 = ptx::idesc_bf16_f32(kTcM, 16);
-      constexpr uint32_t lbo_b2 = L::N2R * 16;
-      uint32_t stage = 0, g = 0, pc = 0;
-      bool ok = true;
-      for (int64_t item = blockIdx.x; item < prm.num_items && ok; item += gridDim.x) {
-        const int64_t chunk = item / c_tiles;
-        const int64_t t0 = chunk * tpc;
-        const int ntile = static_cast<int>(min(prm.n_tiles, t0 + tpc) - t0);
-        int pos = 0;  // tile position within the accumulation period
-        for (int j = 0; j < ntile; ++j) {
-          const uint32_t b = g & 1u;
-          const uint32_t db = pc & 1u;
-          const bool first = pos == 0;
-          const bool last = (pos == F - 1) || (j == ntile - 1);
-          if (!ptx::mbar_wait(&a2_full[b], (g >> 1) & 1u, abort_flag, kWaitLimit) ||
-              (first && !ptx::mbar_wait(&d2_empty[db], ((pc >> 1) & 1u) ^ 1u, abort_flag, kWaitLimit))) {
-            give_up();
-            ok = false;
-            break;
-          }
-          ptx::tc_fence_after();
-          const uint32_t a2 = tmem + Sh::A2_COL0 + b * Sh::A2COLS;
-          const uint32_t b2 = smem_base + L::STAGES_OFF + stage * L::STAGE_BYTES + L::B2_OFF_IN_STAGE;
-#pragma unroll
-          for (int q = 0; q < Sh::KD2 / 16; ++q) {
-            const uint32_t bstart = b2 + q * 2 * lbo_b2;
-            const uint32_t sbo_b2 = (KCH == 2) ? 128u : (smem_base + L::ZERO_OFF - bstart);
-            ptx::mma_bf16_ts(tmem + Sh::D2_COL0 + db * 16, a2 + q * 8, ptx::smem_desc(bstart, lbo_b2, sbo_b2),
-                             idesc2, (q > 0 || !first) ? 1u : 0u);
-          }
-          ptx::mma_commit(&a2_empty[b]);
-          ptx::mma_commit(&empty_b[stage]);
-          if (last) {
-            ptx::mma_commit(&d2_full[db]);
-            ++pc;
-            pos = 0;
-          } else {
-            ++pos;
-          }
-          ++g;
-          if (++stage == NST) stage = 0;
-        }
-      }
-      ptx::mma_commit(drain_bar + 1);
-      volatile int never = 0;
-      ptx::mbar_wait(drain_bar + 1, 0u, &never, kWaitLimit);
-    }
   } else if (warp >= 4) {
-    // ------------------------------------------------------------ epilogue
-    const int e = (warp - 4) >> 2;   // warpgroup
-    const int qtr = warp & 3;        // TMEM lane quarter
-    const int row = qtr * 32 + lane; // candidate row within the tile
+    // ------------------------------------------------------------ worker warpgroup w
+    // Thread `row` owns candidate `row` of every tile.  Per tile g:
+    //   wait D1(g) -> round its R coordinates into indicator words -> D1
+    //   consumed (the issuing thread starts GEMM1(g+1) into it) -> store the
+    //   words into A2 once GEMM2(g-1) released it -> GEMM2(g) into D2 ->
+    //   every `flush` tiles fold D2 into the two-sum partials.
+    // The issuing thread rotates over the four warps of the warpgroup.
+    const int qtr = warp & 3;         // TMEM lane quarter
+    const int row = qtr * 32 + lane;  // candidate row within the tile
     const uint32_t lane_base = static_cast<uint32_t>(qtr * 32) << 16;
-    uint32_t g = 0, pc = 0;
-    float2* acc = reinterpret_cast<float2*>(smem + L::ACC_OFF) + row * 16;  // (hi, lo) per component
-    bool ok = true;
-    for (int64_t item = blockIdx.x; item < prm.num_items && ok; item += gridDim.x) {
-      const int64_t chunk = item / c_tiles, ct = item % c_tiles;
-      const int64_t t0 = chunk * tpc;
-      const int ntile = static_cast<int>(min(prm.n_tiles, t0 + tpc) - t0);
-      int pos = 0;  // tile position within the accumulation period
-      for (int j = 0; j < ntile; ++j) {
-        const uint32_t b = g & 1u;
-        if (!warp_wait(&d1_full[b], (g >> 1) & 1u, abort_flag, lane)) {
-          give_up();
-          ok = false;
-          break;
-        }
+    const uint32_t tw = tmem + w * Sh::WCOLS;  // this worker's TMEM slice
+    constexpr uint32_t idesc2 = ptx::idesc_bf16_f32(kTcM, 16);
+    constexpr uint32_t lbo_b2 = L::N2R * 16;
+    float2* acc = reinterpret_cast<float2*>(wsm + L::W_ACC) + row * 16;  // (hi, lo) per component
+
+    // the worker's tile sequence: items gw, gw + workers, ...; tiles in order
+    int64_t item = gw;
+    int ntile = 0, j = 0, next_ntile = 0;  // tiles of the current / next item (0: none)
+    int64_t chunk = 0, ct = 0;
+    auto tiles_of = [&](int64_t it) -> int {
+      if (it >= prm.num_items) return 0;
+      const int64_t t0 = (it / c_tiles) * tpc;
+      return static_cast<int>(min(prm.n_tiles, t0 + tpc) - t0);
+    };
+    if (item < prm.num_items) {
+      chunk = item / c_tiles;
+      ct = item % c_tiles;
+      ntile = tiles_of(item);
+      next_ntile = tiles_of(item + workers);
+      // prologue: GEMM1 of the first tile (a failure reaches every thread
+      // through the abort flag at the first wait)
+      if (qtr == 0 && lane == 0) {
+        if (!ptx::mbar_wait(&a1_full[0], 0u, abort_flag, kWaitLimit) ||
+            !tc_issue_gemm1<L>(tw, wsm_s, smem_base, full_b, d1_full, 0u, 0u, 0u, abort_flag))
+          *abort_flag = 1;
+        else if (ntile == 1)
+          ptx::mma_commit(&a1_empty[0]);
+      }
+    }
+    uint32_t g = 0, pe = 0, stage = 0, sphase = 0, a1c = 0;
+    uint32_t prev_stage = 0, prev_phase = 0;
+    int pos = 0;        // tile position within the accumulation period
+    bool bad = false;   // this thread saw a wait give up (carried to the next barrier)
+    while (item < prm.num_items) {
+      const bool first = pos == 0;
+      const bool last = (pos == F - 1) || (j == ntile - 1);
+      // ---- round the projections of tile g
+      bad = bad || !warp_wait(d1_full, g & 1u, abort_flag, lane);
+      uint32_t wv[G][R / 2];
+      if (!bad) {
         ptx::tc_fence_after();
-        uint32_t pl[BK][RPE];
 #pragma unroll
-        for (int m = 0; m < BK; ++m)
-          tmem_ld_cols<RPE>(tmem + lane_base + Sh::D1_COL0 + b * N1 + m * ROWS + e * RPE, pl[m]);
-        ptx::tmem_wait_ld();
-        ptx::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&d1_empty[b]);
-        // indicator words: word p holds rows (2p, 2p+1) of this slice
-        uint32_t wv[G][RPE / 2];
+        for (int h = 0; h < R / 16; ++h) {
+          uint32_t pl[BK][16];
 #pragma unroll
-        for (int p = 0; p < RPE / 2; ++p) {
-          uint32_t nm[BK];
+          for (int m = 0; m < BK; ++m) ptx::tmem_ld_x16(tw + lane_base + Sh::D1_OFF + m * R + h * 16, pl[m]);
+          ptx::tmem_wait_ld();
 #pragma unroll
-          for (int m = 0; m < BK; ++m) nm[m] = ptx::prmt(pl[m][2 * p], pl[m][2 * p + 1], 0xFFBBu);
+          for (int p = 0; p < 8; ++p) {
+            uint32_t nm[BK];
 #pragma unroll
-          for (int gc = 0; gc < G; ++gc) {
-            if constexpr (K % 2 == 1)
-              wv[gc][p] = ~nm[gc] & nm[gc + 1] & 0x3F803F80u;  // p_{k-1} > 0 and p_k < 0, k = gc+1
-            else
-              wv[gc][p] = (nm[gc] & 0x80008000u) | 0x3F803F80u;  // sign(p_m) as +-1
+            for (int m = 0; m < BK; ++m) nm[m] = ptx::prmt(pl[m][2 * p], pl[m][2 * p + 1], 0xFFBBu);
+#pragma unroll
+            for (int gc = 0; gc < G; ++gc) {
+              if constexpr (K % 2 == 1)
+                wv[gc][h * 8 + p] = ~nm[gc] & nm[gc + 1] & 0x3F803F80u;  // p_{k-1} > 0 and p_k < 0
+              else
+                wv[gc][h * 8 + p] = (nm[gc] & 0x80008000u) | 0x3F803F80u;  // sign(p_m) as +-1
+            }
           }
         }
-        if (!warp_wait(&a2_empty[b], ((g >> 1) & 1u) ^ 1u, abort_flag, lane)) {
-          give_up();
-          ok = false;
-          break;
+      }
+      ptx::tc_fence_before();
+      // D1 consumed by the whole warpgroup; every thread leaves together on failure
+      if (ptx::named_barrier_or(1 + w, 128, bad)) break;
+      // ---- next tile's position in the sequence; GEMM1 of the next tile
+      const uint32_t next_stage = (stage + 1 == NST) ? 0u : stage + 1;
+      const uint32_t next_sphase = (stage + 1 == NST) ? (sphase ^ 1u) : sphase;
+      const bool item_end = (j == ntile - 1);
+      const bool has_next = !item_end || next_ntile > 0;
+      if (qtr == static_cast<int>(g & 3u) && lane == 0 && has_next) {
+        ptx::tc_fence_after();
+        uint32_t nab = a1c & 1u;
+        bool okk = true;
+        if (item_end) {  // the next tile opens the next item: wait for its directions
+          nab ^= 1u;
+          okk = ptx::mbar_wait(&a1_full[nab], ((a1c + 1) >> 1) & 1u, abort_flag, kWaitLimit);
         }
+        okk = okk && tc_issue_gemm1<L>(tw, wsm_s, smem_base, full_b, d1_full, next_stage, next_sphase, nab,
+                                       abort_flag);
+        if (okk) {
+          // the next tile is the last of its item: release that A1 buffer
+          if ((item_end ? 0 : j + 1) == (item_end ? next_ntile : ntile) - 1) ptx::mma_commit(&a1_empty[nab]);
+        } else {
+          *abort_flag = 1;
+        }
+      }
+      // ---- indicators into A2, once GEMM2 of the previous tile released it
+      bad = g > 0 && !warp_wait(&empty_b[prev_stage], prev_phase, abort_flag, lane);
+      if (!bad) {
         ptx::tc_fence_after();
 #pragma unroll
-        for (int gc = 0; gc < G; ++gc)
-          tmem_st_cols<RPE / 2>(tmem + lane_base + Sh::A2_COL0 + b * Sh::A2COLS + (gc * ROWS + e * RPE) / 2,
-                                wv[gc]);
+        for (int gc = 0; gc < G; ++gc) {
+          if constexpr (R == 16)
+            ptx::tmem_st_x8(tw + lane_base + Sh::A2_OFF + gc * (R / 2),
+                            *reinterpret_cast<const uint32_t(*)[8]>(wv[gc]));
+          else
+#pragma unroll
+            for (int c = 0; c < R / 32; ++c)
+              ptx::tmem_st_x16(tw + lane_base + Sh::A2_OFF + gc * (R / 2) + c * 16,
+                               *reinterpret_cast<const uint32_t(*)[16]>(&wv[gc][c * 16]));
+        }
         ptx::tmem_wait_st();
-        ptx::tc_fence_before();
-        __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&a2_full[b]);
-        const bool last = (pos == F - 1) || (j == ntile - 1);
-        pos = last ? 0 : pos + 1;
-        if (e == 0 && last) {
-          const uint32_t db = pc & 1u;
-          if (!warp_wait(&d2_full[db], (pc >> 1) & 1u, abort_flag, lane)) {
-            give_up();
-            ok = false;
-            break;
-          }
+      }
+      ptx::tc_fence_before();
+      if (ptx::named_barrier_or(1 + w, 128, bad)) break;
+      // ---- GEMM2 of tile g
+      if (qtr == static_cast<int>((g + 2) & 3u) && lane == 0) {
+        ptx::tc_fence_after();
+        const uint32_t b2 = wsm_s + stage * L::STAGE_BYTES + L::B2_OFF_IN_STAGE;
+#pragma unroll
+        for (int q = 0; q < Sh::KD2 / 16; ++q) {
+          const uint32_t bstart = b2 + q * 2 * lbo_b2;
+          const uint32_t sbo_b2 = (KCH == 2) ? 128u : (smem_base + L::ZERO_OFF - bstart);
+          ptx::mma_bf16_ts(tw + Sh::D2_OFF, tw + Sh::A2_OFF + q * 8, ptx::smem_desc(bstart, lbo_b2, sbo_b2), idesc2,
+                           (q > 0 || !first) ? 1u : 0u);
+        }
+        ptx::mma_commit(&empty_b[stage]);  // releases the stage and A2
+        if (last) ptx::mma_commit(d2_ready);
+      }
+      // ---- fold the period's accumulator into the two-sum partials
+      if (last) {
+        bad = !warp_wait(d2_ready, pe & 1u, abort_flag, lane);
+        if (!bad) {
           ptx::tc_fence_after();
           uint32_t dv[16];
-          ptx::tmem_ld_x16(tmem + lane_base + Sh::D2_COL0 + db * 16, dv);
+          ptx::tmem_ld_x16(tw + lane_base + Sh::D2_OFF, dv);
           ptx::tmem_wait_ld();
           ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(&d2_empty[db]);
           const int r2 = 2 * prm.r;
-          const bool item_end = (j == ntile - 1);
           double* out = partial + (chunk * prm.S_pad + ct * kTcM + row) * r2;
 #pragma unroll
           for (int jj = 0; jj < 2 * kMaxRank; ++jj) {
@@ -487,9 +447,38 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
             }
           }
         }
-        if (last) ++pc;
-        ++g;
+        ++pe;
       }
+      // ---- advance
+      pos = last ? 0 : pos + 1;
+      prev_stage = stage;
+      prev_phase = sphase;
+      stage = next_stage;
+      sphase = next_sphase;
+      ++g;
+      if (item_end) {
+        ++a1c;
+        item += workers;
+        if (item < prm.num_items) {
+          chunk = item / c_tiles;
+          ct = item % c_tiles;
+          ntile = next_ntile;
+          next_ntile = tiles_of(item + workers);
+        }
+        j = 0;
+      } else {
+        ++j;
+      }
+    }
+    if (bad || *abort_flag) {
+      *abort_flag = 1;
+      dev_fail(status, LRQ_ETIMEOUT);
+    }
+    // drain: the MMAs issued from this warp complete before TMEM is released
+    if (lane == 0) {
+      ptx::mma_commit(&drain_bar[qtr]);
+      volatile int never = 0;
+      ptx::mbar_wait(&drain_bar[qtr], 0u, &never, kWaitLimit);
     }
   }
   // ------------------------------------------------------------ teardown
@@ -702,7 +691,7 @@ static int score_impl(const ScorePlan& p, const void* vt, const void* b2, const 
   prm.S_pad = p.c_tiles * kTcM;
   prm.r = p.r;
   prm.flush = kTcFlush;
-  int grid = static_cast<int>(std::min<int64_t>(prm.num_items, num_sms_current()));
+  int grid = static_cast<int>(std::min<int64_t>(ceil_div(prm.num_items, Sh::NW), num_sms_current()));
   score_tc_kernel<K, KCH><<<grid, Sh::THREADS, L::TOTAL, st>>>(m_vt, m_b2, m_ct, prm, partial, status);
   count_launch();
   return cuda_check(cudaGetLastError(), "score_tc_kernel");
@@ -718,6 +707,19 @@ int tc_rows_per_tile(int K) {
     case 7: return TcShape<7>::ROWS;
     case 8: return TcShape<8>::ROWS;
     default: return 0;
+  }
+}
+
+int tc_workers_per_cta(int K) {
+  switch (K) {
+    case 2: return TcShape<2>::NW;
+    case 3: return TcShape<3>::NW;
+    case 4: return TcShape<4>::NW;
+    case 5: return TcShape<5>::NW;
+    case 6: return TcShape<6>::NW;
+    case 7: return TcShape<7>::NW;
+    case 8: return TcShape<8>::NW;
+    default: return 1;
   }
 }
 

@@ -18,6 +18,7 @@
 namespace lrq {
 
 int tc_rows_per_tile(int K);
+int tc_workers_per_cta(int K);
 size_t tc_bytes_vaug(int K, int r, int64_t n_tiles);
 size_t tc_bytes_b2(int K, int r, int64_t n_tiles);
 size_t tc_bytes_dirs(int r, int64_t c_tiles);
@@ -117,15 +118,17 @@ int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_
   if (mode == LRQ_MODE_BF16_TC) {
     p->rows_per_tile = tc_rows_per_tile(K);
     p->n_tiles = ceil_div(n, p->rows_per_tile);
-    // coordinate chunks: balance (chunk, candidate tile) items over the SMs
+    // coordinate chunks: balance (chunk, candidate tile) items over the
+    // workers (num_sms CTAs x workers per CTA)
+    const int64_t workers = static_cast<int64_t>(num_sms) * tc_workers_per_cta(K);
     int best_ns = 1;
     double best_eff = -1.0;
     for (int ns = 1; ns <= 64 && ns <= p->n_tiles; ++ns) {
       int64_t tpc = ceil_div(p->n_tiles, ns);
       int64_t ns_eff = ceil_div(p->n_tiles, tpc);
       int64_t items = p->c_tiles * ns_eff;
-      int64_t waves = ceil_div(items, num_sms);
-      double eff = static_cast<double>(items) / static_cast<double>(waves * num_sms);
+      int64_t waves = ceil_div(items, workers);
+      double eff = static_cast<double>(items) / static_cast<double>(waves * workers);
       // a longer chunk amortises the pipeline fill of an item
       eff *= static_cast<double>(tpc) / static_cast<double>(tpc + 2);
       if (eff > best_eff + 1e-3) {
@@ -135,6 +138,7 @@ int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_
     }
     p->tiles_per_chunk = ceil_div(p->n_tiles, best_ns);
     p->nsplit = static_cast<int>(ceil_div(p->n_tiles, p->tiles_per_chunk));
+    p->npart = p->nsplit;
   } else {
     p->fp32_block = 256;
     int64_t blocks_x = ceil_div(S, 256);
@@ -143,9 +147,10 @@ int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_
     int64_t rows = align_up(static_cast<size_t>(ceil_div(n, want)), 256);
     p->fp32_rows_per_chunk = std::max<int64_t>(rows, 256);
     p->nsplit = static_cast<int>(ceil_div(n, p->fp32_rows_per_chunk));
+    p->npart = p->nsplit;
   }
   size_t cur = 0;
-  p->sz_partial = static_cast<size_t>(p->nsplit) * S_pad * 2 * r * sizeof(double);
+  p->sz_partial = static_cast<size_t>(p->npart) * S_pad * 2 * r * sizeof(double);
   p->off_partial = take(cur, p->sz_partial);
   p->sz_T = 2 * kMaxRank * sizeof(double);
   p->off_T = take(cur, p->sz_T);

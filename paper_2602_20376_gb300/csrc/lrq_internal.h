@@ -53,13 +53,14 @@ struct ScorePlan {
   int rows_per_tile;       // coordinates per pipeline stage
   int64_t n_tiles;         // ceil(n / rows_per_tile)
   int64_t c_tiles;         // ceil(S / 128)
-  int nsplit;              // coordinate chunks (partial sums)
+  int nsplit;              // coordinate chunks
+  int npart;               // partial-sum slabs (chunks x producers per chunk)
   int64_t tiles_per_chunk;
   // FP32 tiling
   int fp32_block;          // candidates per block
   int64_t fp32_rows_per_chunk;
   // workspace layout
-  size_t off_partial, sz_partial;   // nsplit x S_pad x 2r doubles
+  size_t off_partial, sz_partial;   // npart x S_pad x 2r doubles
   size_t off_T, sz_T;               // 2r doubles (column sums of conj(V), odd K)
   size_t off_Tpart, sz_Tpart;       // per-block partial column sums
   size_t off_vt, sz_vt;             // packed augmented rows (bf16)
