@@ -168,6 +168,105 @@ int lrq_rescore_no_alloc(const void* V, int64_t n, int r, int K, const void* C, 
                          double* best_f_out, int32_t* dev_status, void* stream);
 
 /* --------------------------------------------------------------------------
+ * lrq_truncate -- spectral truncation Q ~= V V^H (Sec. 4.1, Algorithm 3).
+ *
+ * Computes the r largest (algebraic) eigenvalues lambda_1 >= ... >= lambda_r
+ * of a Hermitian operator and their eigenvectors u_j, and returns
+ * V = [sqrt(lambda_1) u_1, ..., sqrt(lambda_r) u_r] with the columns of
+ * non-positive eigenvalues set to zero (a maximisation of z^H Q z gains
+ * nothing from them).  FP64 Lanczos with full reorthogonalisation on the GPU;
+ * converged pairs are locked and further runs from fresh random starts
+ * recover every copy of a repeated eigenvalue among the r largest.
+ *
+ * Operators (lrq_matrix, a HOST struct whose array members are device
+ * pointers):
+ *   LRQ_MATRIX_DENSE_C128   values: n x ld complex128, row-major; the caller
+ *                           guarantees Q = Q^H (only y = Q x is used).
+ *   LRQ_MATRIX_CSR_LAPLACIAN  L = D - A of an undirected graph: rowptr (n+1
+ *                           int32), colidx (nnz int32), weights (nnz double,
+ *                           or NULL for unit weights); each edge stored in
+ *                           both rows; self loops ignored.  This is the Q of
+ *                           Max-K-Cut (Sec. 1).
+ *
+ *   r        : 1 <= r <= min(8, n).
+ *   tol      : residual tolerance ||Q y - theta y|| <= tol ||T|| for every
+ *              wanted Ritz pair (<= 0 selects 1e-10).
+ *   max_iter : Krylov dimension cap per run (0 selects min(500, n); at most
+ *              4096).  Workspace grows as n * (max_iter + 2r + 9) scalars.
+ *   seed     : start vectors are Philox4x32-10 Gaussians keyed by seed.
+ *   V_out    : n x r complex128 (device) or NULL.
+ *   V32_out  : n x r complex64 (device, V rounded to nearest) or NULL; the
+ *              input layout of lrq_sample_score.
+ *   lambda_out : r doubles (device), descending.
+ *   iters_out  : HOST int64, total Lanczos steps over all runs, or NULL.
+ * Errors: invalid CSR (rowptr not monotone, rowptr[0] != 0,
+ * rowptr[n] != nnz, colidx out of range) or non-finite values -> LRQ_EINVAL
+ * (found on the device and returned by this call); no convergence within
+ * max_iter -> LRQ_ENOCONV.
+ * Unlike the other entry points this call is synchronous: it waits on
+ * `stream` at every convergence check (every 2 to 8 Lanczos steps) and
+ * returns after the outputs are written.
+ * ------------------------------------------------------------------------ */
+typedef enum {
+  LRQ_MATRIX_DENSE_C128 = 0,
+  LRQ_MATRIX_CSR_LAPLACIAN = 1
+} lrq_matrix_kind;
+
+typedef struct {
+  int kind;               /* lrq_matrix_kind */
+  int64_t n;
+  const void* values;     /* dense: n x ld complex128 (device) */
+  int64_t ld;
+  const int32_t* rowptr;  /* CSR: n + 1 (device) */
+  const int32_t* colidx;  /* CSR: nnz (device) */
+  const double* weights;  /* CSR: nnz (device) or NULL = unit weights */
+  int64_t nnz;
+} lrq_matrix;
+
+int lrq_truncate_workspace_size(const lrq_matrix* Q, int r, int max_iter, size_t* bytes);
+int lrq_truncate(const lrq_matrix* Q, int r, double tol, int max_iter, uint64_t seed, void* V_out, void* V32_out,
+                 double* lambda_out, int64_t* iters_out, void* ws, size_t ws_bytes, int32_t* dev_status,
+                 void* stream);
+
+/* --------------------------------------------------------------------------
+ * lrq_enumerate -- exact maximiser for rank r by vertex enumeration.
+ *
+ * Sec. 3, Algorithm 2 (with Theorem 3.2: for Q = V V^H of rank r the
+ * enumeration finds a global maximiser of z^H Q z over A_K^n).  Runs the
+ * levels d = r, r-1, ..., 1 on the leading columns V[:, :d].  At each level
+ * the augmented rows (Eq. 6) h_(i,m) = [Im(rho_m V_i), Re(rho_m V_i)],
+ * rho_m = exp(-i pi (2m+1)/K), m < B_K, are the normals of the decision
+ * boundaries in R^{2d}.  Every index set I of 2d-1 rows with at most two rows
+ * per coordinate is solved in FP64 for the null vector of its rows (sets of
+ * lower rank are skipped); both signs of that direction are expanded into
+ * every assignment of the cells touching the vertex (all K codes for a
+ * coordinate with two rows in I, the two codes across a boundary that passes
+ * within 1e-9 rad of w_i, the decision-rule code of Eq. 9 elsewhere), and
+ * each is scored as ||V^H z||^2 on the full V in FP64.  This candidate set
+ * contains the paper's (Algorithm 4 resolves the same ambiguity with one
+ * fixed-angle solve per vertex).
+ *
+ *   V        : n x r complex128 (device), row-major.
+ *   budget   : refuse with LRQ_EUNSUPPORTED when r * n^(2r+1) > budget
+ *              (<= 0 selects 1e12).
+ *   z_out    : n uint8 codes of the best assignment (device), written.
+ *   f_out    : 1 double, ||V^H z||^2 of z_out (device), written.
+ *   n_sets_out : 1 int64, number of full-rank index sets over all levels
+ *              (device, written), or NULL.
+ *   ws       : lrq_enumerate_workspace_size bytes.
+ * Limits: 1 <= n <= 512, 1 <= r <= 4, 2 <= K <= 8.  A vertex touching more
+ * than 12 boundaries at once or giving more than 65536 assignments (a
+ * degenerate V, e.g. many identical rows) makes the call report
+ * LRQ_EUNSUPPORTED in *dev_status instead of an uncertified answer.
+ * Non-finite V -> LRQ_EINVAL in *dev_status.  Zero rows of V get code 0.
+ * Ties between equal objectives go to the first vertex in the order
+ * (level descending, index sets in colexicographic order, + before -).
+ * ------------------------------------------------------------------------ */
+int lrq_enumerate_workspace_size(int64_t n, int r, int K, size_t* bytes);
+int lrq_enumerate(const void* V, int64_t n, int r, int K, double budget, uint8_t* z_out, double* f_out,
+                  int64_t* n_sets_out, void* ws, size_t ws_bytes, int32_t* dev_status, void* stream);
+
+/* --------------------------------------------------------------------------
  * lrq_cut_count -- exact Max-K-Cut value of an assignment on a graph.
  *
  * Sec. 1: for K = 3 and Q the graph Laplacian the problem is Max-3-Cut.

@@ -197,14 +197,19 @@ def laplacian_quadform(rowptr, colidx, K: int, z) -> float:
                                                    len(rowptr) - 1, int(K), _ptr(z)))
 
 
-def laplacian_dense(rowptr, colidx) -> np.ndarray:
-    """Dense L = D - A of a unit-weight symmetric CSR graph."""
+def laplacian_dense(rowptr, colidx, weights=None) -> np.ndarray:
+    """Dense L = D - A of a symmetric CSR graph (unit weights unless given);
+    self loops cancel in D - A."""
     n = len(rowptr) - 1
     L = np.zeros((n, n), dtype=np.float64)
     for i in range(n):
         for e in range(rowptr[i], rowptr[i + 1]):
-            L[i, colidx[e]] -= 1.0
-            L[i, i] += 1.0
+            j = colidx[e]
+            if j == i:
+                continue
+            w = 1.0 if weights is None else float(weights[e])
+            L[i, j] -= w
+            L[i, i] += w
     return L
 
 
@@ -397,13 +402,19 @@ def truncate_dense(Q, r: int):
     return V, lam
 
 
-def truncate_laplacian(rowptr, colidx, r: int, tol: float = 1e-12):
-    """Top-r eigenpairs of the unit-weight graph Laplacian L = D - A via
-    ARPACK (scipy eigsh), the eigen-solver the paper uses (Sec. 5)."""
+def truncate_laplacian(rowptr, colidx, r: int, tol: float = 1e-12, weights=None):
+    """Top-r eigenpairs of the graph Laplacian L = D - A (unit weights unless
+    given; self loops cancel) via ARPACK (scipy eigsh), the eigen-solver the
+    paper uses (Sec. 5)."""
     import scipy.sparse as sp
     import scipy.sparse.linalg as spla
     n = len(rowptr) - 1
-    A = sp.csr_matrix((np.ones(len(colidx)), np.asarray(colidx), np.asarray(rowptr)), shape=(n, n))
+    rowptr = np.asarray(rowptr)
+    colidx = np.asarray(colidx)
+    w = np.ones(len(colidx)) if weights is None else np.asarray(weights, dtype=np.float64)
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    w = np.where(colidx == rows, 0.0, w)
+    A = sp.csr_matrix((w, colidx, rowptr), shape=(n, n))
     deg = np.asarray(A.sum(axis=1)).ravel()
     L = sp.diags(deg) - A
     # ARPACK may skip a copy of a repeated eigenvalue when asked for exactly

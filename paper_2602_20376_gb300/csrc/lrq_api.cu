@@ -327,6 +327,44 @@ int lrq_rescore(const void* V, int64_t n, int r, int K, const void* C, int64_t S
                         st);
 }
 
+int lrq_truncate_workspace_size(const lrq_matrix* Q, int r, int max_iter, size_t* bytes) {
+  if (!bytes) return fail(LRQ_EINVAL, "bytes is NULL");
+  int e = truncate_check(Q, r, max_iter);
+  if (e) return e;
+  *bytes = truncate_workspace_bytes(Q, r, max_iter);
+  return LRQ_OK;
+}
+
+int lrq_truncate(const lrq_matrix* Q, int r, double tol, int max_iter, uint64_t seed, void* V_out, void* V32_out,
+                 double* lambda_out, int64_t* iters_out, void* ws, size_t ws_bytes, int32_t* dev_status,
+                 void* stream) {
+  int e = truncate_check(Q, r, max_iter);
+  if (e) return e;
+  if (!lambda_out || !dev_status) return fail(LRQ_EINVAL, "NULL pointer argument");
+  if (!(tol < 1.0) || tol != tol) return fail(LRQ_EINVAL, "tol must be below 1");
+  if ((e = check_ws(ws, ws_bytes, truncate_workspace_bytes(Q, r, max_iter)))) return e;
+  return launch_truncate(Q, r, tol, max_iter, seed, static_cast<double2*>(V_out), static_cast<float2*>(V32_out),
+                         lambda_out, iters_out, ws, dev_status, static_cast<cudaStream_t>(stream));
+}
+
+int lrq_enumerate_workspace_size(int64_t n, int r, int K, size_t* bytes) {
+  if (!bytes) return fail(LRQ_EINVAL, "bytes is NULL");
+  int e = enumerate_check(n, r, K, 1e300);
+  if (e) return e;
+  *bytes = enum_workspace_bytes(n, r);
+  return LRQ_OK;
+}
+
+int lrq_enumerate(const void* V, int64_t n, int r, int K, double budget, uint8_t* z_out, double* f_out,
+                  int64_t* n_sets_out, void* ws, size_t ws_bytes, int32_t* dev_status, void* stream) {
+  int e = enumerate_check(n, r, K, budget);
+  if (e) return e;
+  if (!V || !z_out || !f_out || !dev_status) return fail(LRQ_EINVAL, "NULL pointer argument");
+  if ((e = check_ws(ws, ws_bytes, enum_workspace_bytes(n, r)))) return e;
+  return launch_enumerate(static_cast<const double2*>(V), n, r, K, z_out, f_out, n_sets_out, ws, dev_status,
+                          static_cast<cudaStream_t>(stream));
+}
+
 int lrq_cut_count(const int32_t* rowptr, const int32_t* colidx, int64_t n, const uint8_t* z, int64_t* cut_out,
                   void* stream) {
   if (n < 0) return fail(LRQ_EINVAL, "n must be >= 0");

@@ -105,6 +105,16 @@ int launch_rescore(const RescorePlan& p, const Alphabet& a, const float2* V, con
                    int64_t* best_out, double* best_f_out, int32_t* status, cudaStream_t st);
 int launch_cut_count(const int32_t* rowptr, const int32_t* colidx, int64_t n, const uint8_t* z,
                      int64_t* cut_out, cudaStream_t st);
+// spectral truncation (FP64 Lanczos)
+int truncate_check(const lrq_matrix* Q, int r, int max_iter);
+size_t truncate_workspace_bytes(const lrq_matrix* Q, int r, int max_iter);
+int launch_truncate(const lrq_matrix* Q, int r, double tol, int max_iter, uint64_t seed, double2* V, float2* V32,
+                    double* lambda_out, int64_t* iters_out, void* ws, int32_t* status, cudaStream_t st);
+// vertex enumeration (FP64)
+int enumerate_check(int64_t n, int r, int K, double budget);
+size_t enum_workspace_bytes(int64_t n, int r);
+int launch_enumerate(const double2* V, int64_t n, int r, int K, uint8_t* z_out, double* f_out, int64_t* n_sets_out,
+                     void* ws, int32_t* status, cudaStream_t st);
 // tensor-core path
 int launch_tc_pack(const ScorePlan& p, const Alphabet& a, const float2* V, const float2* C,
                    void* vt, void* b2, void* ct, cudaStream_t st);

@@ -38,6 +38,34 @@ class LrqError(RuntimeError):
         self.status = status
 
 
+LRQ_MATRIX_DENSE_C128 = 0
+LRQ_MATRIX_CSR_LAPLACIAN = 1
+
+
+class LrqMatrix(ctypes.Structure):
+    """lrq_matrix of include/lrq.h (array members are device pointers)."""
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int64), ("values", ctypes.c_void_p), ("ld", ctypes.c_int64),
+                ("rowptr", ctypes.c_void_p), ("colidx", ctypes.c_void_p), ("weights", ctypes.c_void_p),
+                ("nnz", ctypes.c_int64)]
+
+
+def dense_matrix(Q: torch.Tensor) -> LrqMatrix:
+    assert Q.dtype == torch.complex128 and Q.dim() == 2 and Q.shape[0] == Q.shape[1] and Q.stride(1) == 1
+    return LrqMatrix(LRQ_MATRIX_DENSE_C128, Q.shape[0], _addr(Q), Q.stride(0), None, None, None, 0)
+
+
+def laplacian_matrix(rowptr: torch.Tensor, colidx: torch.Tensor, weights=None) -> LrqMatrix:
+    assert rowptr.dtype == torch.int32 and colidx.dtype == torch.int32
+    assert weights is None or weights.dtype == torch.float64
+    return LrqMatrix(LRQ_MATRIX_CSR_LAPLACIAN, rowptr.numel() - 1, None, 0, _addr(rowptr), _addr(colidx),
+                     _addr(weights), colidx.numel())
+
+
+def _addr(t):
+    p = _ptr(t)
+    return None if p is None else p.value
+
+
 def load() -> ctypes.CDLL:
     """Load liblrq.so from the package directory (built by build.build())."""
     global _lib
@@ -66,6 +94,15 @@ def load() -> ctypes.CDLL:
         lib.lrq_rescore.restype = I
         lib.lrq_rescore_no_alloc.argtypes = [P, I64, I, I, P, I64, P, I, P, P, P, P, P, P]
         lib.lrq_rescore_no_alloc.restype = I
+        lib.lrq_truncate_workspace_size.argtypes = [ctypes.POINTER(LrqMatrix), I, I, ctypes.POINTER(SZ)]
+        lib.lrq_truncate_workspace_size.restype = I
+        lib.lrq_truncate.argtypes = [ctypes.POINTER(LrqMatrix), I, ctypes.c_double, I, U64, P, P, P,
+                                     ctypes.POINTER(I64), P, SZ, P, P]
+        lib.lrq_truncate.restype = I
+        lib.lrq_enumerate_workspace_size.argtypes = [I64, I, I, ctypes.POINTER(SZ)]
+        lib.lrq_enumerate_workspace_size.restype = I
+        lib.lrq_enumerate.argtypes = [P, I64, I, I, ctypes.c_double, P, P, P, P, SZ, P, P]
+        lib.lrq_enumerate.restype = I
         lib.lrq_cut_count.argtypes = [P, P, I64, P, P, P]
         lib.lrq_cut_count.restype = I
         lib.lrq_set_timing_events.argtypes = [P, P]
@@ -80,7 +117,9 @@ def exported_symbols():
     """Names of the entry points include/lrq.h declares."""
     return ["lrq_status_string", "lrq_last_error", "lrq_abi_version", "lrq_sample_directions",
             "lrq_sample_score_workspace_size", "lrq_sample_score", "lrq_rescore_workspace_size",
-            "lrq_rescore", "lrq_rescore_no_alloc", "lrq_cut_count", "lrq_set_timing_events", "lrq_kernel_launches"]
+            "lrq_rescore", "lrq_rescore_no_alloc", "lrq_truncate_workspace_size", "lrq_truncate",
+            "lrq_enumerate_workspace_size", "lrq_enumerate",
+            "lrq_cut_count", "lrq_set_timing_events", "lrq_kernel_launches"]
 
 
 def _check(status: int, where: str):
@@ -177,6 +216,40 @@ def lrq_rescore_no_alloc(V: torch.Tensor, K: int, C: torch.Tensor, idx: torch.Te
            "lrq_rescore_no_alloc")
 
 
+def lrq_truncate_workspace_size(Q: LrqMatrix, r: int, max_iter: int = 0) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().lrq_truncate_workspace_size(ctypes.byref(Q), int(r), int(max_iter), ctypes.byref(out)),
+           "lrq_truncate_workspace_size")
+    return int(out.value)
+
+
+def lrq_truncate(Q: LrqMatrix, r: int, tol: float, max_iter: int, seed: int, V_out, V32_out, lambda_out,
+                 ws: torch.Tensor, dev_status: torch.Tensor, stream=None) -> int:
+    """Returns the total number of Lanczos steps."""
+    iters = ctypes.c_int64(0)
+    _check(load().lrq_truncate(ctypes.byref(Q), int(r), float(tol), int(max_iter), int(seed), _ptr(V_out),
+                               _ptr(V32_out), _ptr(lambda_out), ctypes.byref(iters), _ptr(ws),
+                               ws.numel() * ws.element_size(), _ptr(dev_status), _stream(stream)), "lrq_truncate")
+    return int(iters.value)
+
+
+def lrq_enumerate_workspace_size(n: int, r: int, K: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().lrq_enumerate_workspace_size(int(n), int(r), int(K), ctypes.byref(out)),
+           "lrq_enumerate_workspace_size")
+    return int(out.value)
+
+
+def lrq_enumerate(V: torch.Tensor, K: int, budget: float, z_out: torch.Tensor, f_out: torch.Tensor, n_sets_out,
+                  ws: torch.Tensor, dev_status: torch.Tensor, stream=None):
+    """V: n x r complex128 on the device."""
+    n, r = V.shape
+    assert V.dtype == torch.complex128 and z_out.dtype == torch.uint8 and f_out.dtype == torch.float64
+    _check(load().lrq_enumerate(_ptr(V), n, r, int(K), float(budget), _ptr(z_out), _ptr(f_out), _ptr(n_sets_out),
+                                _ptr(ws), ws.numel() * ws.element_size(), _ptr(dev_status), _stream(stream)),
+           "lrq_enumerate")
+
+
 def lrq_cut_count(rowptr: torch.Tensor, colidx: torch.Tensor, z: torch.Tensor, cut_out: torch.Tensor,
                   stream=None):
     assert rowptr.dtype == torch.int32 and colidx.dtype == torch.int32 and z.dtype == torch.uint8
@@ -248,3 +321,29 @@ def rescore(V, K, C, idx, want_z=False, ws=None, dev_status=None, stream=None):
     best_f = torch.empty(1, dtype=torch.float64, device=dev)
     lrq_rescore(V, K, C, idx, f, z, best, best_f, ws, dev_status, stream)
     return dict(f=f, z=z, best=best, best_f=best_f, dev_status=dev_status, ws=ws)
+
+
+def enumerate(V, K, budget=0.0, stream=None):
+    """Exact maximiser for rank r; allocates outputs and workspace with torch."""
+    dev = V.device
+    n, r = V.shape
+    ws = workspace(lrq_enumerate_workspace_size(n, r, K), dev)
+    dev_status = torch.zeros(1, dtype=torch.int32, device=dev)
+    z = torch.empty(n, dtype=torch.uint8, device=dev)
+    f = torch.empty(1, dtype=torch.float64, device=dev)
+    n_sets = torch.empty(1, dtype=torch.int64, device=dev)
+    lrq_enumerate(V, K, budget, z, f, n_sets, ws, dev_status, stream)
+    return dict(z=z, f=f, n_sets=n_sets, dev_status=dev_status)
+
+
+def truncate(Q: LrqMatrix, r, tol=0.0, max_iter=0, seed=0, want_c128=True, want_c64=True, device="cuda",
+             stream=None):
+    """Top-r spectral truncation; keep the tensors behind Q alive meanwhile."""
+    n = Q.n
+    ws = workspace(lrq_truncate_workspace_size(Q, r, max_iter), device)
+    dev_status = torch.zeros(1, dtype=torch.int32, device=device)
+    V = torch.empty((n, r), dtype=torch.complex128, device=device) if want_c128 else None
+    V32 = torch.empty((n, r), dtype=torch.complex64, device=device) if want_c64 else None
+    lam = torch.empty(r, dtype=torch.float64, device=device)
+    iters = lrq_truncate(Q, r, tol, max_iter, seed, V, V32, lam, ws, dev_status, stream)
+    return dict(V=V, V32=V32, lam=lam, iters=iters)

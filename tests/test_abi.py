@@ -93,3 +93,51 @@ def test_workspace_queries(lib):
     assert lrq.lrq_rescore_workspace_size(1 << 20, 4, 64) > 0
     with pytest.raises(lrq.LrqError):
         lrq.lrq_sample_score_workspace_size(1 << 20, 4, 9, 1 << 16, lrq.LRQ_MODE_BF16_TC, 64)
+
+
+@pytest.mark.parametrize("n,r,K,budget,code", [
+    (0, 2, 3, 0.0, 1), (12, 0, 3, 0.0, 1), (12, 2, 1, 0.0, 1),   # invalid
+    (513, 1, 3, 0.0, 2), (6, 5, 3, 0.0, 2), (12, 2, 9, 0.0, 2),  # beyond the enumerator's limits
+    (12, 2, 3, 1e5, 2),                                           # 2 * 12^5 = 497664 > budget
+    (200, 3, 3, 0.0, 2),                                          # r n^(2r+1) > the default 1e12
+])
+def test_enumerate_rejects_bad_arguments_on_host(lib, n, r, K, budget, code):
+    P = ctypes.c_void_p
+    assert lib.lrq_enumerate(P(256), n, r, K, budget, P(512), P(1024), None, P(4096), 1 << 30, P(8192), None) == code
+    assert len(lib.lrq_last_error()) > 0
+
+
+def test_enumerate_workspace_and_null_checks(lib):
+    from paper_2602_20376_gb300 import lrq
+    assert lrq.lrq_enumerate_workspace_size(12, 2, 3) > 0
+    P = ctypes.c_void_p
+    assert lib.lrq_enumerate(P(256), 12, 2, 3, 0.0, None, P(1024), None, P(4096), 1 << 30, P(8192), None) == 1
+    assert lib.lrq_enumerate(P(256), 12, 2, 3, 0.0, P(512), P(1024), None, P(4096), 16, P(8192), None) == 6
+
+
+def test_truncate_rejects_bad_arguments_on_host(lib):
+    from paper_2602_20376_gb300 import lrq
+    P = ctypes.c_void_p
+    dense = lrq.LrqMatrix(lrq.LRQ_MATRIX_DENSE_C128, 100, 256, 100, None, None, None, 0)
+    csr = lrq.LrqMatrix(lrq.LRQ_MATRIX_CSR_LAPLACIAN, 100, None, 0, 256, 512, None, 600)
+    assert lrq.lrq_truncate_workspace_size(dense, 4) > 100 * 4 * 16
+    assert lrq.lrq_truncate_workspace_size(csr, 3, 50) > 100 * 50 * 8
+    it = ctypes.c_int64(0)
+
+    def call(Q, r=4, tol=0.0, max_iter=0, lam=P(1024), ws_bytes=1 << 30, status=P(8192)):
+        return lib.lrq_truncate(ctypes.byref(Q), r, tol, max_iter, 1, None, None, lam, ctypes.byref(it), P(4096),
+                                ws_bytes, status, None)
+    assert call(dense, r=0) == 1
+    assert call(dense, r=9) == 1
+    assert call(dense, max_iter=5000) == 1
+    assert call(dense, tol=2.0) == 1
+    assert call(dense, lam=None) == 1
+    assert call(dense, status=None) == 1
+    assert call(dense, ws_bytes=64) == 6
+    bad_ld = lrq.LrqMatrix(lrq.LRQ_MATRIX_DENSE_C128, 100, 256, 50, None, None, None, 0)
+    assert call(bad_ld) == 1
+    bad_kind = lrq.LrqMatrix(7, 100, 256, 100, None, None, None, 0)
+    assert call(bad_kind) == 1
+    small = lrq.LrqMatrix(lrq.LRQ_MATRIX_CSR_LAPLACIAN, 3, None, 0, 256, 512, None, 4)
+    assert call(small, r=4) == 1  # r > n
+    assert lib.lrq_truncate(None, 4, 0.0, 0, 1, None, None, P(1024), None, P(4096), 1 << 30, P(8192), None) == 1

@@ -1,0 +1,135 @@
+"""lrq_enumerate (Sec. 3, Algorithm 2) on the GPU against the oracle.
+
+The exact rank-r solver returns the maximum of ||V^H z||^2 over A_K^n
+(Theorem 3.2), so its value is unique while its maximiser is not (every
+global phase omega^j z scores the same).  The tests therefore compare the
+value with the oracle's enumeration and, where K^n is small, with brute force
+over all assignments, within 1e-9 relative (both sides in FP64; the
+difference is rounding order only), and check that the returned codes score
+that value under the oracle's objective.  Integer counts (full-rank index
+sets) must be identical.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2602_20376_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+DEV = "cuda:0"
+
+
+@pytest.fixture(scope="module")
+def lrq():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2602_20376_gb300 import lrq as L
+    L.load()
+    return L
+
+
+def _enum(lrq, V, K, budget=0.0):
+    out = lrq.enumerate(torch.from_numpy(np.ascontiguousarray(V, dtype=np.complex128)).to(DEV), K, budget)
+    torch.cuda.synchronize()
+    return out
+
+
+def _check_value(V, K, out, f_ref):
+    lrq_status = int(out["dev_status"].item())
+    assert lrq_status == 0
+    f = float(out["f"].item())
+    z = out["z"].cpu().numpy()
+    assert z.max() < K
+    assert abs(f - f_ref) <= 1e-9 * f_ref
+    assert abs(oracle.objective(V, K, z) - f) <= 1e-12 * f
+    return f, z
+
+
+def test_exact_small_instance_matches_bruteforce(lrq):
+    # n = 12, r = 2, K = 3, V i.i.d. CN(0, 1), complex128, seed 0
+    V = I.factor(12, 2, seed=0)
+    out = _enum(lrq, V, 3)
+    f_bf, _ = oracle.bruteforce(V, 3)
+    f_en, _, st = oracle.enumerate_vertices(V, 3)
+    assert abs(f_en - f_bf) <= 1e-12 * f_bf
+    _check_value(V, 3, out, f_bf)
+    assert int(out["n_sets"].item()) == st["full_rank"] == 7164
+
+
+@pytest.mark.parametrize("n,r,K,seed", [
+    (8, 3, 3, 1), (6, 3, 4, 2), (10, 2, 8, 3), (5, 4, 2, 4), (9, 2, 5, 5), (7, 1, 7, 6),
+    (12, 1, 3, 7), (16, 2, 2, 8), (5, 4, 3, 9), (11, 2, 6, 10), (4, 2, 4, 11), (1, 1, 3, 12), (2, 2, 5, 13),
+])
+def test_enumeration_matches_oracle(lrq, n, r, K, seed):
+    V = I.factor(n, r, seed=seed, scales=np.linspace(1.5, 0.5, r))
+    out = _enum(lrq, V, K)
+    f_en, _, st = oracle.enumerate_vertices(V, K)
+    _check_value(V, K, out, f_en)
+    assert int(out["n_sets"].item()) == st["full_rank"]
+    if K ** n <= 2_000_000:
+        f_bf, _ = oracle.bruteforce(V, K)
+        assert abs(f_bf - f_en) <= 1e-12 * f_bf
+
+
+def test_rank_one_matches_sweep(lrq):
+    # r = 1: Algorithm 1's angular sweep is exact
+    q = I.complex_gaussian((200, 1), seed=21)
+    out = _enum(lrq, q, 5)
+    f_sw, _ = oracle.rank1_sweep(q[:, 0], 5)
+    _check_value(q, 5, out, f_sw)
+
+
+def test_zero_rows_get_code_zero(lrq):
+    V = I.factor(10, 2, seed=22)
+    V[3] = 0
+    V[7] = 0
+    out = _enum(lrq, V, 3)
+    f_bf, _ = oracle.bruteforce(V, 3)
+    _, z = _check_value(V, 3, out, f_bf)
+    assert z[3] == 0 and z[7] == 0
+
+
+def test_identical_rows_within_branch_budget(lrq):
+    # every vertex puts all 8 equal coordinates on a boundary at once (2^8 assignments)
+    row = I.complex_gaussian((1, 2), seed=23)
+    V = np.repeat(row, 8, axis=0)
+    out = _enum(lrq, V, 3)
+    f_bf, _ = oracle.bruteforce(V, 3)
+    _check_value(V, 3, out, f_bf)
+
+
+def test_identical_rows_beyond_branch_budget_is_reported(lrq):
+    V = np.repeat(I.complex_gaussian((1, 1), seed=24), 20, axis=0)
+    out = _enum(lrq, V, 3)
+    assert int(out["dev_status"].item()) == lrq.LRQ_EUNSUPPORTED
+
+
+def test_non_finite_input_is_reported(lrq):
+    V = I.factor(6, 2, seed=25)
+    V[2, 1] = np.nan
+    out = _enum(lrq, V, 3)
+    assert int(out["dev_status"].item()) == lrq.LRQ_EINVAL
+
+
+def test_larger_instance_bounds_and_determinism(lrq):
+    # n = 64 is beyond the oracle's enumeration in seconds: check the value
+    # against the best of 20000 sampled directions (a lower bound, Sec. 4.2)
+    # and n * lambda_max(V V^H) (an upper bound), and that two runs agree.
+    V = I.factor(64, 2, seed=26, scales=(2.0, 1.0))
+    a = _enum(lrq, V, 3)
+    b = _enum(lrq, V, 3)
+    assert int(a["dev_status"].item()) == 0
+    f = float(a["f"].item())
+    z = a["z"].cpu().numpy()
+    assert torch.equal(a["z"], b["z"]) and float(b["f"].item()) == f
+    assert abs(oracle.objective(V, 3, z) - f) <= 1e-12 * f
+    C = I.directions(20000, 2, seed=27, dtype=np.complex128)
+    sampled = oracle.score(V, 3, C)
+    assert f >= sampled.max() * (1 - 1e-12)
+    lam = np.linalg.eigvalsh(V.conj().T @ V).max()
+    assert f <= 64 * lam * (1 + 1e-12)
+    # N = 192 boundary rows, |I| = 3: C(192, 3) sets, none with three rows of a group
+    from math import comb
+    assert int(a["n_sets"].item()) == comb(192, 3) - 64 * comb(3, 3) + 192

@@ -371,3 +371,43 @@ def test_truncate_laplacian_even_torus():
     checker = ((a + b) % 2 * 2 - 1).ravel() / np.sqrt(k1 * k2)
     u1 = V[:, 0] / np.sqrt(lam[0])
     assert abs(abs(np.vdot(checker, u1)) - 1.0) < 1e-9
+
+
+def test_truncate_laplacian_uniform_weights_scale_the_spectrum():
+    # L(c w) = c L(w): a uniform edge weight c multiplies every eigenvalue by c
+    k1, k2 = 6, 8
+    rowptr, colidx = I.torus_graph(k1, k2)
+    _, lam1 = O.truncate_laplacian(rowptr, colidx, 3)
+    _, lam25 = O.truncate_laplacian(rowptr, colidx, 3, weights=np.full(len(colidx), 2.5))
+    assert np.allclose(lam25, 2.5 * lam1, atol=1e-9)
+    assert np.isclose(lam1[0], 8.0, atol=1e-9)
+
+
+def test_weighted_laplacian_quadratic_form_and_self_loops():
+    # x^T L x = sum over undirected edges of w_ij (x_i - x_j)^2; rows sum to 0;
+    # a self loop contributes nothing to D - A
+    g = I.rng(5)
+    n = 9
+    src, dst = np.triu_indices(n, 1)
+    keep = g.random(src.size) < 0.4
+    src, dst = src[keep], dst[keep]
+    wu = g.uniform(0.5, 2.0, src.size)
+    rowptr, colidx = I._csr_from_edges(n, src, dst)
+    wmap = {}
+    for a, b, w in zip(src, dst, wu):
+        wmap[(a, b)] = wmap[(b, a)] = w
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    weights = np.array([wmap[(i, j)] for i, j in zip(rows, colidx)])
+    L = O.laplacian_dense(rowptr, colidx, weights)
+    assert np.allclose(L.sum(axis=1), 0, atol=1e-14)
+    x = g.standard_normal(n)
+    assert np.isclose(x @ L @ x, sum(w * (x[a] - x[b]) ** 2 for a, b, w in zip(src, dst, wu)))
+    # the same graph with a weighted self loop on every vertex
+    rp2 = rowptr + np.arange(n + 1, dtype=np.int32)
+    ci2 = np.concatenate([np.concatenate([colidx[rowptr[i]:rowptr[i + 1]], [i]]) for i in range(n)]).astype(np.int32)
+    w2 = np.concatenate([np.concatenate([weights[rowptr[i]:rowptr[i + 1]], [7.0]]) for i in range(n)])
+    assert np.allclose(O.laplacian_dense(rp2, ci2, w2), L)
+    _, lam_a = O.truncate_laplacian(rowptr, colidx, 3, weights=weights)
+    _, lam_b = O.truncate_laplacian(rp2, ci2, 3, weights=w2)
+    assert np.allclose(lam_a, lam_b, atol=1e-10)
+    assert np.allclose(lam_a, np.sort(np.linalg.eigvalsh(L))[::-1][:3], atol=1e-10)
