@@ -168,6 +168,67 @@ int lrq_rescore_no_alloc(const void* V, int64_t n, int r, int K, const void* C, 
                          double* best_f_out, int32_t* dev_status, void* stream);
 
 /* --------------------------------------------------------------------------
+ * Batched scoring: many independent instances in one persistent launch.
+ *
+ * Each problem p is the sampling method of Sec. 4.2 on its own V_p (n_p x r_p
+ * complex64) and alphabet K_p: S_p directions (the caller's, or drawn on the
+ * device as in lrq_sample_directions with seed_p + call index), FP32
+ * scoring, then the top_m candidates by FP32 score are re-scored in FP64
+ * (decisions and sums in FP64) and the best is returned.  All problems'
+ * (problem, candidate tile) work items run in one persistent kernel, longest
+ * first; the candidate tile per (r, K, floor(log2 n)) class comes from the
+ * library's autotuner (lrq_batched_autotune) or its cache, else 128.
+ *
+ * Life cycle (all host calls; plan is a HOST object):
+ *   lrq_batched_plan_create(problems, P, top_m, &plan)  validates, no launch
+ *   lrq_batched_workspace_size(plan, &bytes)
+ *   lrq_batched_prepare(plan, ws, ws_bytes, stream)      uploads descriptors
+ *       into ws and resets the call index; synchronous
+ *   lrq_batched_autotune(plan, ws, ws_bytes, dev_status, stream)  optional,
+ *       synchronous: times tiles 64/128/256 per class on the plan's own
+ *       problems, keeps the fastest in the plan and a process-wide cache
+ *   lrq_sample_score_batched(plan, ws, ...)              asynchronous; only
+ *       kernel launches and a memset, so it can be captured in a CUDA graph
+ *   lrq_batched_graph_create(...) captures exactly that into a graph
+ *       (stream must not be the legacy default stream); replay with
+ *       lrq_graph_launch, free with lrq_graph_destroy.  Replays advance the
+ *       call index, so drawn directions differ between replays.
+ *   lrq_batched_plan_destroy(plan)
+ *
+ *   problems : P problem descriptors (HOST array; V and C device pointers,
+ *              which must stay valid while the plan is used).
+ *   best_f_out : P doubles (device), FP64 objective of each problem's winner.
+ *   best_idx_out : P int64 (device), the winner's candidate index.
+ * Limits: 1 <= r_p <= 8, 2 <= K_p <= 64, 1 <= S_p <= 8192, 1 <= n_p < 2^31,
+ * 1 <= top_m <= min(16, S_p), P <= 65535.  Non-finite V or C -> LRQ_EINVAL
+ * in *dev_status.
+ * ------------------------------------------------------------------------ */
+typedef struct {
+  const void* V;   /* n x r complex64 (device) */
+  int64_t n;
+  int r;
+  int K;
+  const void* C;   /* S x r complex64 (device), or NULL: drawn on the device */
+  int64_t S;
+  uint64_t seed;
+} lrq_problem;
+
+typedef struct lrq_batched_plan lrq_batched_plan;
+
+int lrq_batched_plan_create(const lrq_problem* problems, int P, int top_m, lrq_batched_plan** plan_out);
+void lrq_batched_plan_destroy(lrq_batched_plan* plan);
+int lrq_batched_workspace_size(const lrq_batched_plan* plan, size_t* bytes);
+int lrq_batched_prepare(lrq_batched_plan* plan, void* ws, size_t ws_bytes, void* stream);
+int lrq_batched_autotune(lrq_batched_plan* plan, void* ws, size_t ws_bytes, int32_t* dev_status, void* stream);
+int lrq_batched_tile(const lrq_batched_plan* plan, int p); /* the candidate tile of problem p, or -1 */
+int lrq_sample_score_batched(const lrq_batched_plan* plan, void* ws, size_t ws_bytes, double* best_f_out,
+                             int64_t* best_idx_out, int32_t* dev_status, void* stream);
+int lrq_batched_graph_create(const lrq_batched_plan* plan, void* ws, size_t ws_bytes, double* best_f_out,
+                             int64_t* best_idx_out, int32_t* dev_status, void* stream, void** graph_exec_out);
+int lrq_graph_launch(void* graph_exec, void* stream);
+int lrq_graph_destroy(void* graph_exec);
+
+/* --------------------------------------------------------------------------
  * lrq_truncate -- spectral truncation Q ~= V V^H (Sec. 4.1, Algorithm 3).
  *
  * Computes the r largest (algebraic) eigenvalues lambda_1 >= ... >= lambda_r

@@ -14,24 +14,7 @@
 
 namespace lrq {
 
-// ---------------------------------------------------------------------------
-// Uniform directions on the complex unit sphere (Sec. 4.2; App. E, Lemma
-// "innerIsBeta": c = Z/||Z||, Z ~ CN(0, I_r)).  One thread per candidate; the
-// Philox counter of component j of candidate s is (lo32 s, hi32 s, j, 0).
-// ---------------------------------------------------------------------------
-__device__ __forceinline__ void sphere_component(uint64_t seed, int64_t s, int j, double* zr, double* zi) {
-  PhiloxOut o = philox4x32_10(static_cast<uint32_t>(s), static_cast<uint32_t>(static_cast<uint64_t>(s) >> 32),
-                              static_cast<uint32_t>(j), 0u, static_cast<uint32_t>(seed),
-                              static_cast<uint32_t>(seed >> 32));
-  double u1 = uniform53(o.w[0], o.w[1]);
-  double u2 = uniform53(o.w[2], o.w[3]);
-  double rad = sqrt(-log(u1));
-  double sn, cs;
-  sincospi(2.0 * u2, &sn, &cs);
-  *zr = rad * cs;
-  *zi = rad * sn;
-}
-
+// Uniform directions on the complex unit sphere: sphere_component (lrq_device.cuh).
 __global__ void sample_directions_kernel(uint64_t seed, int64_t S, int r, float2* __restrict__ C) {
   int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (s >= S) return;

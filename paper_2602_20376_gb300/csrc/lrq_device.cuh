@@ -54,6 +54,24 @@ __device__ __forceinline__ double uniform53(uint32_t hi, uint32_t lo) {
 }
 
 // ---------------------------------------------------------------------------
+// Uniform directions on the complex unit sphere (Sec. 4.2; App. E, Lemma
+// "innerIsBeta": c = Z/||Z||, Z ~ CN(0, I_r)).  One thread per candidate; the
+// Philox counter of component j of candidate s is (lo32 s, hi32 s, j, 0).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void sphere_component(uint64_t seed, int64_t s, int j, double* zr, double* zi) {
+  PhiloxOut o = philox4x32_10(static_cast<uint32_t>(s), static_cast<uint32_t>(static_cast<uint64_t>(s) >> 32),
+                              static_cast<uint32_t>(j), 0u, static_cast<uint32_t>(seed),
+                              static_cast<uint32_t>(seed >> 32));
+  double u1 = uniform53(o.w[0], o.w[1]);
+  double u2 = uniform53(o.w[2], o.w[3]);
+  double rad = sqrt(-log(u1));
+  double sn, cs;
+  sincospi(2.0 * u2, &sn, &cs);
+  *zr = rad * cs;
+  *zi = rad * sn;
+}
+
+// ---------------------------------------------------------------------------
 // Decision rule (Sec. 3, Eq. 9) from boundary-line signs.
 // s_m = [p_m > 0] with p_m = Im(exp(-i theta_m) w), theta_m = pi(2m+1)/K.
 //   even K (B_K = K/2 lines): c = #{m : s_m}, k = s_0 ? c : (K - c) mod K;

@@ -66,6 +66,12 @@ def _addr(t):
     return None if p is None else p.value
 
 
+class LrqProblem(ctypes.Structure):
+    """lrq_problem of include/lrq.h (V and C are device pointers)."""
+    _fields_ = [("V", ctypes.c_void_p), ("n", ctypes.c_int64), ("r", ctypes.c_int), ("K", ctypes.c_int),
+                ("C", ctypes.c_void_p), ("S", ctypes.c_int64), ("seed", ctypes.c_uint64)]
+
+
 def load() -> ctypes.CDLL:
     """Load liblrq.so from the package directory (built by build.build())."""
     global _lib
@@ -94,6 +100,27 @@ def load() -> ctypes.CDLL:
         lib.lrq_rescore.restype = I
         lib.lrq_rescore_no_alloc.argtypes = [P, I64, I, I, P, I64, P, I, P, P, P, P, P, P]
         lib.lrq_rescore_no_alloc.restype = I
+        PP = ctypes.c_void_p
+        lib.lrq_batched_plan_create.argtypes = [ctypes.POINTER(LrqProblem), I, I, ctypes.POINTER(PP)]
+        lib.lrq_batched_plan_create.restype = I
+        lib.lrq_batched_plan_destroy.argtypes = [PP]
+        lib.lrq_batched_plan_destroy.restype = None
+        lib.lrq_batched_workspace_size.argtypes = [PP, ctypes.POINTER(SZ)]
+        lib.lrq_batched_workspace_size.restype = I
+        lib.lrq_batched_prepare.argtypes = [PP, P, SZ, P]
+        lib.lrq_batched_prepare.restype = I
+        lib.lrq_batched_autotune.argtypes = [PP, P, SZ, P, P]
+        lib.lrq_batched_autotune.restype = I
+        lib.lrq_batched_tile.argtypes = [PP, I]
+        lib.lrq_batched_tile.restype = I
+        lib.lrq_sample_score_batched.argtypes = [PP, P, SZ, P, P, P, P]
+        lib.lrq_sample_score_batched.restype = I
+        lib.lrq_batched_graph_create.argtypes = [PP, P, SZ, P, P, P, P, ctypes.POINTER(PP)]
+        lib.lrq_batched_graph_create.restype = I
+        lib.lrq_graph_launch.argtypes = [PP, P]
+        lib.lrq_graph_launch.restype = I
+        lib.lrq_graph_destroy.argtypes = [PP]
+        lib.lrq_graph_destroy.restype = I
         lib.lrq_truncate_workspace_size.argtypes = [ctypes.POINTER(LrqMatrix), I, I, ctypes.POINTER(SZ)]
         lib.lrq_truncate_workspace_size.restype = I
         lib.lrq_truncate.argtypes = [ctypes.POINTER(LrqMatrix), I, ctypes.c_double, I, U64, P, P, P,
@@ -118,7 +145,9 @@ def exported_symbols():
     return ["lrq_status_string", "lrq_last_error", "lrq_abi_version", "lrq_sample_directions",
             "lrq_sample_score_workspace_size", "lrq_sample_score", "lrq_rescore_workspace_size",
             "lrq_rescore", "lrq_rescore_no_alloc", "lrq_truncate_workspace_size", "lrq_truncate",
-            "lrq_enumerate_workspace_size", "lrq_enumerate",
+            "lrq_enumerate_workspace_size", "lrq_enumerate", "lrq_batched_plan_create", "lrq_batched_plan_destroy",
+            "lrq_batched_workspace_size", "lrq_batched_prepare", "lrq_batched_autotune", "lrq_batched_tile",
+            "lrq_sample_score_batched", "lrq_batched_graph_create", "lrq_graph_launch", "lrq_graph_destroy",
             "lrq_cut_count", "lrq_set_timing_events", "lrq_kernel_launches"]
 
 
@@ -323,7 +352,7 @@ def rescore(V, K, C, idx, want_z=False, ws=None, dev_status=None, stream=None):
     return dict(f=f, z=z, best=best, best_f=best_f, dev_status=dev_status, ws=ws)
 
 
-def enumerate(V, K, budget=0.0, stream=None):
+def enumerate_exact(V, K, budget=0.0, stream=None):
     """Exact maximiser for rank r; allocates outputs and workspace with torch."""
     dev = V.device
     n, r = V.shape
@@ -347,3 +376,72 @@ def truncate(Q: LrqMatrix, r, tol=0.0, max_iter=0, seed=0, want_c128=True, want_
     lam = torch.empty(r, dtype=torch.float64, device=device)
     iters = lrq_truncate(Q, r, tol, max_iter, seed, V, V32, lam, ws, dev_status, stream)
     return dict(V=V, V32=V32, lam=lam, iters=iters)
+
+
+class BatchedPlan:
+    """Owns an lrq_batched_plan, its workspace and outputs; keeps the problem
+    tensors alive.  problems: list of dicts with V (n x r complex64, device),
+    K, and either C (S x r complex64, device) or S and seed."""
+
+    def __init__(self, problems, top_m=4, device="cuda", stream=None):
+        self.keep = []
+        arr = (LrqProblem * len(problems))()
+        for i, q in enumerate(problems):
+            V = q["V"]
+            C = q.get("C")
+            self.keep += [V, C]
+            S = C.shape[0] if C is not None else int(q["S"])
+            arr[i] = LrqProblem(_addr(V), V.shape[0], V.shape[1], int(q["K"]), _addr(C), S, int(q.get("seed", 0)))
+        h = ctypes.c_void_p()
+        _check(load().lrq_batched_plan_create(arr, len(problems), int(top_m), ctypes.byref(h)),
+               "lrq_batched_plan_create")
+        self.h = h
+        self.P = len(problems)
+        self.stream = stream
+        nb = ctypes.c_size_t(0)
+        _check(load().lrq_batched_workspace_size(self.h, ctypes.byref(nb)), "lrq_batched_workspace_size")
+        self.ws = workspace(nb.value, device)
+        self.status = torch.zeros(1, dtype=torch.int32, device=device)
+        self.best_f = torch.empty(self.P, dtype=torch.float64, device=device)
+        self.best_idx = torch.empty(self.P, dtype=torch.int64, device=device)
+        self.graph = None
+        _check(load().lrq_batched_prepare(self.h, _ptr(self.ws), self._wsb(), _stream(stream)), "lrq_batched_prepare")
+
+    def _wsb(self):
+        return self.ws.numel() * self.ws.element_size()
+
+    def autotune(self):
+        _check(load().lrq_batched_autotune(self.h, _ptr(self.ws), self._wsb(), _ptr(self.status),
+                                           _stream(self.stream)), "lrq_batched_autotune")
+
+    def tile(self, p):
+        return int(load().lrq_batched_tile(self.h, int(p)))
+
+    def run(self):
+        _check(load().lrq_sample_score_batched(self.h, _ptr(self.ws), self._wsb(), _ptr(self.best_f),
+                                               _ptr(self.best_idx), _ptr(self.status), _stream(self.stream)),
+               "lrq_sample_score_batched")
+
+    def capture(self):
+        g = ctypes.c_void_p()
+        _check(load().lrq_batched_graph_create(self.h, _ptr(self.ws), self._wsb(), _ptr(self.best_f),
+                                               _ptr(self.best_idx), _ptr(self.status), _stream(self.stream),
+                                               ctypes.byref(g)), "lrq_batched_graph_create")
+        self.graph = g
+
+    def replay(self):
+        _check(load().lrq_graph_launch(self.graph, _stream(self.stream)), "lrq_graph_launch")
+
+    def close(self):
+        if self.graph is not None:
+            load().lrq_graph_destroy(self.graph)
+            self.graph = None
+        if self.h:
+            load().lrq_batched_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -141,3 +141,23 @@ def test_truncate_rejects_bad_arguments_on_host(lib):
     small = lrq.LrqMatrix(lrq.LRQ_MATRIX_CSR_LAPLACIAN, 3, None, 0, 256, 512, None, 4)
     assert call(small, r=4) == 1  # r > n
     assert lib.lrq_truncate(None, 4, 0.0, 0, 1, None, None, P(1024), None, P(4096), 1 << 30, P(8192), None) == 1
+
+
+def test_batched_plan_rejects_bad_problems_on_host(lib):
+    from paper_2602_20376_gb300 import lrq
+    P = ctypes.c_void_p
+
+    def create(probs, top_m=1):
+        arr = (lrq.LrqProblem * len(probs))(*probs)
+        h = ctypes.c_void_p()
+        return lib.lrq_batched_plan_create(arr, len(probs), top_m, ctypes.byref(h))
+    ok = lrq.LrqProblem(256, 100, 4, 3, None, 1000, 1)
+    for bad in (lrq.LrqProblem(None, 100, 4, 3, None, 1000, 1), lrq.LrqProblem(256, 0, 4, 3, None, 1000, 1),
+                lrq.LrqProblem(256, 100, 9, 3, None, 1000, 1), lrq.LrqProblem(256, 100, 4, 1, None, 1000, 1),
+                lrq.LrqProblem(256, 100, 4, 3, None, 8193, 1), lrq.LrqProblem(256, 100, 4, 3, None, 0, 1)):
+        assert create([ok, bad]) == 1
+    assert create([ok], top_m=17) == 1
+    assert create([ok], top_m=0) == 1
+    assert lib.lrq_batched_plan_create(None, 1, 1, ctypes.byref(ctypes.c_void_p())) == 1
+    assert lib.lrq_graph_launch(None, None) == 1
+    assert lib.lrq_sample_score_batched(None, P(256), 1, P(512), P(1024), P(2048), None) == 1

@@ -31,7 +31,7 @@ def lrq():
 
 
 def _enum(lrq, V, K, budget=0.0):
-    out = lrq.enumerate(torch.from_numpy(np.ascontiguousarray(V, dtype=np.complex128)).to(DEV), K, budget)
+    out = lrq.enumerate_exact(torch.from_numpy(np.ascontiguousarray(V, dtype=np.complex128)).to(DEV), K, budget)
     torch.cuda.synchronize()
     return out
 
