@@ -21,9 +21,16 @@ Pieces and the passages they follow:
   (Sec. 4.1, Algorithm 3) through LAPACK ``eigh`` and ARPACK ``eigsh``
   (the paper's own eigen-solver, Sec. 5).
 
+* ``learned.py`` (numpy FP64): the learned proposal, which the paper does
+  not have: spectral features with a phase gauge, the 3-layer MLP forward
+  and backward, the von Mises-Fisher mixture head on S^7 with its negative
+  log-likelihood and gradient, Wood's vMF sampler, the canonical window of
+  the K-fold equivalence (Sec. 2.1, 2.3) and Adam.
+
 Parity pins for every function live in ``tests/test_oracle_*.py``.  Parity
-unpinned: none of the functions above; the learned-proposal gain (no passage
-of the paper defines it) is not part of the oracle.
+unpinned: none of the functions above; the learned-proposal gain over uniform
+sampling (an empirical claim no passage of the paper defines) is measured,
+not pinned.
 """
 from __future__ import annotations
 

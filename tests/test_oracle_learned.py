@@ -1,0 +1,142 @@
+"""Pins for the learned-proposal oracle against independent facts: library
+Bessel functions, limits of the vMF normaliser, central finite differences of
+every gradient, the vMF mean resultant length of Wood's sampler, invariances
+of the features and the one-step closed form of Adam."""
+import math
+
+import numpy as np
+import pytest
+from scipy import special
+
+from oracle import learned as L
+from paper_2602_20376_gb300 import inputs as I
+
+
+@pytest.mark.parametrize("nu", [3, 4])
+def test_log_bessel_matches_scipy(nu):
+    for k in [1e-3, 0.1, 1.0, 5.0, 17.0, 29.9, 30.1, 45.0, 200.0, 3000.0]:
+        ref = math.log(special.ive(nu, k)) + k
+        assert abs(L.log_bessel_i(nu, k) - ref) <= 1e-11 * max(1.0, abs(ref)), (nu, k)
+
+
+def test_vmf_normaliser_limits():
+    # kappa -> 0: the uniform density on S^7, whose area is 2 pi^4 / 3! = pi^4 / 3
+    assert abs(L.log_c8(1e-7) + math.log(math.pi ** 4 / 3)) < 1e-10
+    # A_8(kappa) ~ kappa / 8 for small kappa, 1 - 7 / (2 kappa) for large kappa
+    assert abs(L.a8(1e-4) - 1e-4 / 8) < 1e-10
+    k = 1e4
+    assert abs(L.a8(k) - (1 - 7 / (2 * k))) < 1e-6
+
+
+def test_dlogc8_is_minus_a8():
+    for k in [0.3, 2.0, 12.0, 29.0, 31.0, 150.0]:
+        h = 1e-5 * max(1.0, k)
+        fd = (L.log_c8(k + h) - L.log_c8(k - h)) / (2 * h)
+        assert abs(fd + L.a8(k)) < 1e-7, k
+
+
+def test_single_flat_component_gives_uniform_nll():
+    # one component with kappa -> 0 and the rest with -inf logits: density 3 / pi^4
+    O = np.zeros((1, L.N_OUT))
+    O = O.reshape(1, L.N_COMP, L.HEAD)
+    O[0, :, :8] = 1.0
+    O[0, :, 8] = -40.0            # softplus ~ 4e-18
+    O[0, 1:, 9] = -1e3
+    x = I.rng(1).standard_normal((1, 5, 8))
+    x /= np.linalg.norm(x, axis=2, keepdims=True)
+    assert abs(L.nll(O.reshape(1, -1), x) - math.log(math.pi ** 4 / 3)) < 1e-9
+
+
+def _random_head(B, seed):
+    g = I.rng(seed)
+    O = g.standard_normal((B, L.N_OUT))
+    O = O.reshape(B, L.N_COMP, L.HEAD)
+    O[:, :, 8] = g.uniform(-1, 4, (B, L.N_COMP))
+    return O.reshape(B, L.N_OUT)
+
+
+def test_nll_gradient_matches_finite_differences():
+    B, T = 2, 7
+    O = _random_head(B, 2)
+    x = I.rng(3).standard_normal((B, T, 8))
+    x /= np.linalg.norm(x, axis=2, keepdims=True)
+    G = L.nll_grad(O, x)
+    idx = I.rng(4).choice(O.size, 60, replace=False)
+    for flat in idx:
+        b, j = divmod(int(flat), L.N_OUT)
+        h = 1e-6
+        Op, Om = O.copy(), O.copy()
+        Op[b, j] += h
+        Om[b, j] -= h
+        fd = (L.nll(Op, x) - L.nll(Om, x)) / (2 * h)
+        assert abs(fd - G[b, j]) <= 1e-6 * max(1e-3, abs(fd)) + 1e-9, (b, j, fd, G[b, j])
+
+
+def test_mlp_backward_matches_finite_differences():
+    F, B = 24, 3
+    g = I.rng(5)
+    params = g.standard_normal(L.n_params(F)) * 0.1
+    X = g.standard_normal((B, F))
+    R = g.standard_normal((B, L.N_OUT))  # loss = sum(O * R)
+    O, cache = L.mlp_forward(params, X)
+    grad = L.mlp_backward(params, cache, R)
+    for k in g.choice(params.size, 80, replace=False):
+        h = 1e-6
+        p1, p2 = params.copy(), params.copy()
+        p1[k] += h
+        p2[k] -= h
+        fd = ((L.mlp_forward(p1, X)[0] - L.mlp_forward(p2, X)[0]) * R).sum() / (2 * h)
+        assert abs(fd - grad[k]) <= 1e-6 * max(1.0, abs(fd)), k
+
+
+def test_wood_sampler_mean_resultant_length():
+    rng = np.random.default_rng(6)
+    mu = rng.standard_normal(8)
+    mu /= np.linalg.norm(mu)
+    for kappa in [0.5, 5.0, 60.0]:
+        X = L.wood_sample(mu, kappa, 20000, rng)
+        assert np.allclose(np.linalg.norm(X, axis=1), 1.0, atol=1e-12)
+        t = X @ mu
+        se = t.std() / math.sqrt(len(t))
+        assert abs(t.mean() - L.a8(kappa)) < 5 * se, kappa
+        # the part orthogonal to mu has no preferred direction
+        perp = X - t[:, None] * mu[None, :]
+        assert np.abs(perp.mean(axis=0)).max() < 5 * perp.std() / math.sqrt(len(t))
+
+
+def test_features_invariances():
+    V = I.factor(300, 4, seed=7, scales=(3.0, 2.0, 1.0, 0.5))
+    lam = np.array([9.0, 4.0, 1.0, 0.25])
+    f = L.features(V, lam)
+    assert f.size == 24
+    # moduli only: any column phase leaves them unchanged, and the gauge
+    # fixes the phases to the same V
+    ph = np.exp(1j * I.rng(8).uniform(0, 2 * np.pi, 4))
+    assert np.allclose(L.features(V * ph[None, :], lam), f, atol=1e-12)
+    assert np.allclose(L.gauge_fix(V * ph[None, :]), L.gauge_fix(V), atol=1e-12)
+    G = L.gauge_fix(V)
+    i = np.argmax(np.abs(G), axis=0)
+    assert np.all(np.abs(G[i, np.arange(4)].imag) < 1e-15) and np.all(G[i, np.arange(4)].real > 0)
+    # scaling V and lambda together changes no feature; the normalised means are 1
+    assert np.allclose(L.features(2.0 * V, 4.0 * lam), f, atol=1e-12)
+    assert np.allclose(f[4], (np.abs(V) ** 2).sum() * 300 / lam.sum() / 300)
+
+
+def test_canonical_window_and_equivalence():
+    K = 8
+    C = I.directions(500, 4, seed=9, dtype=np.complex128)
+    Cc = L.canonicalize(C, K)
+    a = np.angle(Cc[:, 0])
+    assert np.all(a > -np.pi / K - 1e-12) and np.all(a <= np.pi / K + 1e-12)
+    # each row differs from the original by a K-th root of unity
+    ratio = Cc[:, 0] / C[:, 0]
+    k = np.round(np.angle(ratio) * K / (2 * np.pi))
+    assert np.allclose(ratio, np.exp(2j * np.pi * k / K))
+
+
+def test_adam_first_step_closed_form():
+    g = I.rng(10)
+    p = g.standard_normal(50)
+    gr = g.standard_normal(50)
+    out, m, v = L.adam_step(p, gr, np.zeros(50), np.zeros(50), 1, lr=0.01, eps=0.0)
+    assert np.allclose(out, p - 0.01 * np.sign(gr), atol=1e-15)
