@@ -328,6 +328,57 @@ int lrq_enumerate(const void* V, int64_t n, int r, int K, double budget, uint8_t
                   int64_t* n_sets_out, void* ws, size_t ws_bytes, int32_t* dev_status, void* stream);
 
 /* --------------------------------------------------------------------------
+ * Learned proposal (the paper has no counterpart: it samples directions
+ * uniformly, Sec. 4.2).  A small network maps spectral features of V to a
+ * mixture of 16 von Mises-Fisher densities on the unit sphere S^7 of
+ * C^4 = R^8 (r = 4), from which directions are drawn instead.  Directions c
+ * and omega^k c score the same (Sec. 2.3), so targets are kept in the
+ * window arg c_1 in (-pi/K, pi/K] and samples get a random omega^k.
+ *
+ * lrq_proposal_features: for B instances (V: B x n x r complex64, lambda:
+ *   B x r doubles, both device), writes the gauge-fixed V (each column times
+ *   |a| / a, a its entry of largest modulus, lowest row on ties) to Vg_out
+ *   (B x n x r complex64) and F = 5 r + 4 features per instance to feat_out
+ *   (B x F floats): lambda_j / sum lambda, then mean, variance, skewness and
+ *   excess kurtosis of ||V_i||^2 n / sum lambda and of |V_ij|^2 n / lambda_j
+ *   for each column j (FP64 inside).  sum lambda <= 0 -> LRQ_EINVAL on the
+ *   device.
+ * lrq_mlp_forward / lrq_mlp_backward: the network F -> 256 -> 256 -> 160,
+ *   ReLU after the hidden layers.  params (lrq_proposal_num_params(F)
+ *   floats): W1 (F x 256), b1, W2 (256 x 256), b2, W3 (256 x 160), b3, each W
+ *   row-major (in x out).  X: B x F; H1, H2: B x 256 (written by forward,
+ *   read by backward); O: B x 160.  backward: dO (B x 160) -> grads (same
+ *   layout as params), scratch: 2 B x 256 floats.  bf16 != 0 rounds every
+ *   GEMM operand to bfloat16 (products accumulate in FP32).
+ * lrq_vmf_nll: O (B x 160): per component m, outputs 10m..10m+7 give
+ *   mu_m = u / ||u||, 10m+8 gives kappa_m = softplus, 10m+9 the mixture
+ *   logit.  targets: B x T x 8 unit vectors.  loss_out (1 double, device):
+ *   mean over the B T targets of -log sum_m pi_m C_8(kappa_m)
+ *   exp(kappa_m mu_m . x), C_8(kappa) = kappa^3 / ((2 pi)^4 I_3(kappa));
+ *   dO (B x 160 floats): its gradient.  FP64 inside.
+ * lrq_vmf_sample: S draws per instance from the mixture of O (component by
+ *   weight, Wood's rejection method for the cosine to mu, a uniform
+ *   direction orthogonal to mu), each multiplied by omega^k with k uniform
+ *   in [0, K); C_out: B x S x 4 complex64.  Philox4x32-10 keyed by seed with
+ *   counter (s, b, draw, 0x564D46).  A rejection loop that failed 1000 times
+ *   (never observed) reports LRQ_ETIMEOUT.
+ * lrq_adam_step: Adam with bias correction for step t >= 1 on count floats.
+ * ------------------------------------------------------------------------ */
+int lrq_proposal_num_features(int r);
+int64_t lrq_proposal_num_params(int F);
+int lrq_proposal_features(const void* V, int B, int64_t n, int r, const double* lambda, void* Vg_out,
+                          float* feat_out, int32_t* dev_status, void* stream);
+int lrq_mlp_forward(const float* params, int F, int B, const float* X, float* H1, float* H2, float* O, int bf16,
+                    void* stream);
+int lrq_mlp_backward(const float* params, int F, int B, const float* X, const float* H1, const float* H2,
+                     const float* dO, float* grads, float* scratch, int bf16, void* stream);
+int lrq_vmf_nll(const float* O, int B, const float* targets, int T, double* loss_out, float* dO, void* stream);
+int lrq_vmf_sample(const float* O, int B, int S, int K, uint64_t seed, void* C_out, int32_t* dev_status,
+                   void* stream);
+int lrq_adam_step(float* params, const float* grads, float* m, float* v, int64_t count, int t, float lr,
+                  float beta1, float beta2, float eps, void* stream);
+
+/* --------------------------------------------------------------------------
  * lrq_cut_count -- exact Max-K-Cut value of an assignment on a graph.
  *
  * Sec. 1: for K = 3 and Q the graph Laplacian the problem is Max-3-Cut.

@@ -347,6 +347,56 @@ int lrq_truncate(const lrq_matrix* Q, int r, double tol, int max_iter, uint64_t 
                          lambda_out, iters_out, ws, dev_status, static_cast<cudaStream_t>(stream));
 }
 
+int lrq_proposal_num_features(int r) { return (r >= 1 && r <= kMaxRank) ? 5 * r + 4 : -1; }
+
+int64_t lrq_proposal_num_params(int F) { return F >= 1 ? proposal_num_params(F) : -1; }
+
+int lrq_proposal_features(const void* V, int B, int64_t n, int r, const double* lambda, void* Vg_out,
+                          float* feat_out, int32_t* dev_status, void* stream) {
+  if (B < 1 || n < 1 || r < 1 || r > kMaxRank) return fail(LRQ_EINVAL, "bad sizes");
+  if (!V || !lambda || !Vg_out || !feat_out || !dev_status) return fail(LRQ_EINVAL, "NULL pointer argument");
+  return launch_features(static_cast<const float2*>(V), B, n, r, lambda, static_cast<float2*>(Vg_out), feat_out,
+                         dev_status, static_cast<cudaStream_t>(stream));
+}
+
+int lrq_mlp_forward(const float* params, int F, int B, const float* X, float* H1, float* H2, float* O, int bf16,
+                    void* stream) {
+  if (F < 1 || B < 1) return fail(LRQ_EINVAL, "bad sizes");
+  if (!params || !X || !H1 || !H2 || !O) return fail(LRQ_EINVAL, "NULL pointer argument");
+  return launch_mlp_forward(params, F, B, X, H1, H2, O, bf16 ? 1 : 0, static_cast<cudaStream_t>(stream));
+}
+
+int lrq_mlp_backward(const float* params, int F, int B, const float* X, const float* H1, const float* H2,
+                     const float* dO, float* grads, float* scratch, int bf16, void* stream) {
+  if (F < 1 || B < 1) return fail(LRQ_EINVAL, "bad sizes");
+  if (!params || !X || !H1 || !H2 || !dO || !grads || !scratch) return fail(LRQ_EINVAL, "NULL pointer argument");
+  return launch_mlp_backward(params, F, B, X, H1, H2, dO, grads, scratch, bf16 ? 1 : 0,
+                             static_cast<cudaStream_t>(stream));
+}
+
+int lrq_vmf_nll(const float* O, int B, const float* targets, int T, double* loss_out, float* dO, void* stream) {
+  if (B < 1 || T < 1) return fail(LRQ_EINVAL, "bad sizes");
+  if (!O || !targets || !loss_out || !dO) return fail(LRQ_EINVAL, "NULL pointer argument");
+  return launch_vmf_nll(O, B, targets, T, loss_out, dO, static_cast<cudaStream_t>(stream));
+}
+
+int lrq_vmf_sample(const float* O, int B, int S, int K, uint64_t seed, void* C_out, int32_t* dev_status,
+                   void* stream) {
+  if (B < 1 || S < 1 || B > 65535) return fail(LRQ_EINVAL, "bad sizes");
+  if (K < 1 || K > kMaxK) return fail(LRQ_EINVAL, "K must be in [1, 64]");
+  if (!O || !C_out || !dev_status) return fail(LRQ_EINVAL, "NULL pointer argument");
+  return launch_vmf_sample(O, B, S, K, seed, static_cast<float2*>(C_out), dev_status,
+                           static_cast<cudaStream_t>(stream));
+}
+
+int lrq_adam_step(float* params, const float* grads, float* m, float* v, int64_t count, int t, float lr,
+                  float beta1, float beta2, float eps, void* stream) {
+  if (count < 0 || t < 1) return fail(LRQ_EINVAL, "count must be >= 0 and t >= 1");
+  if (count > 0 && (!params || !grads || !m || !v)) return fail(LRQ_EINVAL, "NULL pointer argument");
+  if (count == 0) return LRQ_OK;
+  return launch_adam(params, grads, m, v, count, t, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream));
+}
+
 int lrq_enumerate_workspace_size(int64_t n, int r, int K, size_t* bytes) {
   if (!bytes) return fail(LRQ_EINVAL, "bytes is NULL");
   int e = enumerate_check(n, r, K, 1e300);

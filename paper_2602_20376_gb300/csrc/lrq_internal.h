@@ -110,6 +110,19 @@ int truncate_check(const lrq_matrix* Q, int r, int max_iter);
 size_t truncate_workspace_bytes(const lrq_matrix* Q, int r, int max_iter);
 int launch_truncate(const lrq_matrix* Q, int r, double tol, int max_iter, uint64_t seed, double2* V, float2* V32,
                     double* lambda_out, int64_t* iters_out, void* ws, int32_t* status, cudaStream_t st);
+// learned proposal
+int64_t proposal_num_params(int F);
+int launch_features(const float2* V, int B, int64_t n, int r, const double* lambda, float2* Vg, float* feat,
+                    int32_t* status, cudaStream_t st);
+int launch_mlp_forward(const float* params, int F, int B, const float* X, float* H1, float* H2, float* O, int bf16,
+                       cudaStream_t st);
+int launch_mlp_backward(const float* params, int F, int B, const float* X, const float* H1, const float* H2,
+                        const float* dO, float* grads, float* scratch, int bf16, cudaStream_t st);
+int launch_vmf_nll(const float* O, int B, const float* X, int T, double* loss, float* dO, cudaStream_t st);
+int launch_vmf_sample(const float* O, int B, int S, int K, uint64_t seed, float2* C, int32_t* status,
+                      cudaStream_t st);
+int launch_adam(float* p, const float* g, float* m, float* v, int64_t count, int t, float lr, float b1, float b2,
+                float eps, cudaStream_t st);
 // vertex enumeration (FP64)
 int enumerate_check(int64_t n, int r, int K, double budget);
 size_t enum_workspace_bytes(int64_t n, int r);

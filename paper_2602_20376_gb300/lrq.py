@@ -121,6 +121,23 @@ def load() -> ctypes.CDLL:
         lib.lrq_graph_launch.restype = I
         lib.lrq_graph_destroy.argtypes = [PP]
         lib.lrq_graph_destroy.restype = I
+        F32 = ctypes.c_float
+        lib.lrq_proposal_num_features.argtypes = [I]
+        lib.lrq_proposal_num_features.restype = I
+        lib.lrq_proposal_num_params.argtypes = [I]
+        lib.lrq_proposal_num_params.restype = I64
+        lib.lrq_proposal_features.argtypes = [P, I, I64, I, P, P, P, P, P]
+        lib.lrq_proposal_features.restype = I
+        lib.lrq_mlp_forward.argtypes = [P, I, I, P, P, P, P, I, P]
+        lib.lrq_mlp_forward.restype = I
+        lib.lrq_mlp_backward.argtypes = [P, I, I, P, P, P, P, P, P, I, P]
+        lib.lrq_mlp_backward.restype = I
+        lib.lrq_vmf_nll.argtypes = [P, I, P, I, P, P, P]
+        lib.lrq_vmf_nll.restype = I
+        lib.lrq_vmf_sample.argtypes = [P, I, I, I, U64, P, P, P]
+        lib.lrq_vmf_sample.restype = I
+        lib.lrq_adam_step.argtypes = [P, P, P, P, I64, I, F32, F32, F32, F32, P]
+        lib.lrq_adam_step.restype = I
         lib.lrq_truncate_workspace_size.argtypes = [ctypes.POINTER(LrqMatrix), I, I, ctypes.POINTER(SZ)]
         lib.lrq_truncate_workspace_size.restype = I
         lib.lrq_truncate.argtypes = [ctypes.POINTER(LrqMatrix), I, ctypes.c_double, I, U64, P, P, P,
@@ -148,6 +165,8 @@ def exported_symbols():
             "lrq_enumerate_workspace_size", "lrq_enumerate", "lrq_batched_plan_create", "lrq_batched_plan_destroy",
             "lrq_batched_workspace_size", "lrq_batched_prepare", "lrq_batched_autotune", "lrq_batched_tile",
             "lrq_sample_score_batched", "lrq_batched_graph_create", "lrq_graph_launch", "lrq_graph_destroy",
+            "lrq_proposal_num_features", "lrq_proposal_num_params", "lrq_proposal_features", "lrq_mlp_forward",
+            "lrq_mlp_backward", "lrq_vmf_nll", "lrq_vmf_sample", "lrq_adam_step",
             "lrq_cut_count", "lrq_set_timing_events", "lrq_kernel_launches"]
 
 
@@ -243,6 +262,50 @@ def lrq_rescore_no_alloc(V: torch.Tensor, K: int, C: torch.Tensor, idx: torch.Te
     _check(load().lrq_rescore_no_alloc(_ptr(V), n, r, int(K), _ptr(C), S, _ptr(idx), m, _ptr(f_out), _ptr(z_out),
                                        _ptr(best_out), _ptr(best_f_out), _ptr(dev_status), _stream(stream)),
            "lrq_rescore_no_alloc")
+
+
+def lrq_proposal_num_features(r: int) -> int:
+    return int(load().lrq_proposal_num_features(int(r)))
+
+
+def lrq_proposal_num_params(F: int) -> int:
+    return int(load().lrq_proposal_num_params(int(F)))
+
+
+def lrq_proposal_features(V, lam, Vg_out, feat_out, dev_status, stream=None):
+    """V: B x n x r complex64; lam: B x r float64; Vg_out like V; feat_out: B x F float32."""
+    B, n, r = V.shape
+    _check(load().lrq_proposal_features(_ptr(V), B, n, r, _ptr(lam), _ptr(Vg_out), _ptr(feat_out),
+                                        _ptr(dev_status), _stream(stream)), "lrq_proposal_features")
+
+
+def lrq_mlp_forward(params, X, H1, H2, O, bf16=False, stream=None):
+    B, F = X.shape
+    _check(load().lrq_mlp_forward(_ptr(params), F, B, _ptr(X), _ptr(H1), _ptr(H2), _ptr(O), int(bool(bf16)),
+                                  _stream(stream)), "lrq_mlp_forward")
+
+
+def lrq_mlp_backward(params, X, H1, H2, dO, grads, scratch, bf16=False, stream=None):
+    B, F = X.shape
+    _check(load().lrq_mlp_backward(_ptr(params), F, B, _ptr(X), _ptr(H1), _ptr(H2), _ptr(dO), _ptr(grads),
+                                   _ptr(scratch), int(bool(bf16)), _stream(stream)), "lrq_mlp_backward")
+
+
+def lrq_vmf_nll(O, targets, loss_out, dO, stream=None):
+    B, T, _ = targets.shape
+    _check(load().lrq_vmf_nll(_ptr(O), B, _ptr(targets), T, _ptr(loss_out), _ptr(dO), _stream(stream)),
+           "lrq_vmf_nll")
+
+
+def lrq_vmf_sample(O, S, K, seed, C_out, dev_status, stream=None):
+    B = O.shape[0]
+    _check(load().lrq_vmf_sample(_ptr(O), B, int(S), int(K), int(seed), _ptr(C_out), _ptr(dev_status),
+                                 _stream(stream)), "lrq_vmf_sample")
+
+
+def lrq_adam_step(params, grads, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
+    _check(load().lrq_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), params.numel(), int(t), float(lr),
+                                float(beta1), float(beta2), float(eps), _stream(stream)), "lrq_adam_step")
 
 
 def lrq_truncate_workspace_size(Q: LrqMatrix, r: int, max_iter: int = 0) -> int:
