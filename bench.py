@@ -11,9 +11,21 @@ direction seed 1 + s * world + g.  Metric: candidate*n evaluations per
 second (S * n per step), whole job.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--mode bf16|fp32]
+                  [--workload scale|exact|maxcut|batched|learned]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (same metric, unit and config).
+
+The default line (workload "scale") also carries "samples_to_best": the
+learned proposal's median S_u / S_l on held-out angular-synchronisation
+instances (n = 4096, K = 8, r = 4), trained on the GPU in the same run.
+The other workloads print one line each for the remaining paths:
+  exact    n = 12, r = 2, K = 3: vertex enumeration + 4096 sampled directions
+  maxcut   planted 3-partition SBM, n = 10^6: Laplacian truncation (r = 3),
+           2^17 BF16 candidates, FP64 rescore, exact cut count
+  batched  512 instances, n log-uniform in [64, 8192], r in 2..6,
+           K in {2, 3, 4, 8}: one graph-captured persistent launch
+  learned  the learned proposal at a larger training set
 """
 from __future__ import annotations
 
@@ -266,6 +278,9 @@ def run_ours(args):
         "clocks": clk.summary(),
         "samples_to_best": None,
     }
+    if world == 1 and not args.no_learned:
+        line["samples_to_best"] = learned_gain(dev, args.learned_n, args.learned_train, args.learned_eval,
+                                               args.learned_steps)
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(1, args.cpu_sample)
         cb.pop("seconds")
@@ -274,6 +289,252 @@ def run_ours(args):
     if world > 1:
         dist.destroy_process_group()
 
+
+
+# ---------------------------------------------------------------------------
+# the other workloads (one GPU; one JSON line each)
+# ---------------------------------------------------------------------------
+def _events(torch, k):
+    return [torch.cuda.Event(enable_timing=True) for _ in range(k)]
+
+
+def _line(metric, value, unit, args, ms, config, **extra):
+    out = {"metric": metric, "value": value, "unit": unit, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+           "data": "synthetic", "config": config}
+    out.update(extra)
+    print(json.dumps(out), flush=True)
+
+
+def learned_gain(dev, n, ntrain, neval, steps):
+    """Median S_u / S_l of the learned proposal (trained here on the GPU)."""
+    import torch
+
+    from paper_2602_20376_gb300 import proposal as P
+    t0 = time.perf_counter()
+    V, lam = P.truncate_instances(n, range(10 ** 6, 10 ** 6 + ntrain + neval), device=dev)
+    Vg, feat = P.features(V, lam)
+    targets = P.training_targets(Vg[:ntrain], P.K_ANGSYNC, 1 << 14, 555)
+    model = P.Proposal(feat.shape[1], seed=0, device=dev)
+    model.fit_standardizer(feat[:ntrain])
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    losses = P.train(model, feat[:ntrain], targets, steps, 64, 1e-3)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    rows = P.evaluate(model, Vg[ntrain:], feat[ntrain:], P.K_ANGSYNC, 1 << 16, 777)
+    su = sorted(r[1] for r in rows)
+    sl = sorted(r[2] for r in rows)
+    fin = lambda x: x if x != float("inf") else None  # noqa: E731
+    return {"median_ratio": P.median_gain(rows), "median_S_uniform": fin(su[len(su) // 2]),
+            "median_S_learned": fin(sl[len(sl) // 2]), "level": 0.999, "S_max": 1 << 16,
+            "reached": sum(1 for r in rows if r[2] != float("inf")), "instances": len(rows),
+            "workload": "angular synchronisation Q = x x^H + sigma W, x on A_8^n, sigma ~ U[0.5, 2], n=%d, "
+                        "rank-4 truncation, K=8; %d training instances (top 1%% of 2^14 uniform directions "
+                        "each), %d held-out" % (n, ntrain, neval),
+            "train_steps": steps, "loss_first10": float(losses[:10].mean()), "loss_last10": float(losses[-10:].mean()),
+            "data_s": t1 - t0, "train_s": t2 - t1, "kernels": "BF16 MLP fwd/bwd, vMF NLL, Adam, vMF sampler"}
+
+
+def run_learned(args):
+    import torch
+    torch.cuda.set_device(0)
+    from paper_2602_20376_gb300 import lrq
+    lrq.load()
+    res = learned_gain(torch.device("cuda", 0), args.learned_n, max(args.learned_train, 512), args.learned_eval * 2,
+                       max(args.learned_steps, 800))
+    _line("median S_u/S_l to 0.999*best (learned vs uniform proposals)", res["median_ratio"], "x", args, None,
+          {"workload": res["workload"]}, dtype="bf16", samples_to_best=res)
+
+
+def run_exact(args):
+    import torch
+
+    from paper_2602_20376_gb300 import inputs, lrq
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    lrq.load()
+    V64 = torch.from_numpy(inputs.factor(12, 2, seed=0)).to(dev)
+    V32 = V64.to(torch.complex64)
+    SS = 4096
+
+    def step(i):
+        out = lrq.enumerate_exact(V64, 3)
+        smp = lrq.sample_score(V32, 3, S=SS, seed=1 + i, mode=lrq.LRQ_MODE_FP32, top_m=4)
+        rs = lrq.rescore(V32, 3, smp["C"], smp["top_idx"])
+        return out, rs
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    a, b = _events(torch, args.steps), _events(torch, args.steps)
+    l0 = lrq.lrq_kernel_launches()
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            a[i].record()
+            out, rs = step(args.warmup + i)
+            b[i].record()
+        torch.cuda.synchronize()
+    ms = sum(x.elapsed_time(y) for x, y in zip(a, b)) / args.steps
+    f_exact = float(out["f"].item())
+    f_samp = float(rs["best_f"].item())
+    # enumeration throughput on a larger arrangement: n = 64, r = 2, K = 3
+    Vb = torch.from_numpy(inputs.factor(64, 2, seed=26, scales=(2.0, 1.0))).to(dev)
+    lrq.enumerate_exact(Vb, 3)
+    torch.cuda.synchronize()
+    e0, e1 = _events(torch, 2)
+    e0.record()
+    big = lrq.enumerate_exact(Vb, 3)
+    e1.record()
+    torch.cuda.synchronize()
+    big_ms = e0.elapsed_time(e1)
+    sets = int(big["n_sets"].item())
+    _line("exact rank-2 solves/s (n=12, r=2, K=3: vertex enumeration + 4096 sampled directions)", 1e3 / ms,
+          "solves/s", args, ms, {"workload": "exact small instance: n=12, r=2, K=3, V ~ CN(0,1) complex128 seed 0; "
+                                 "7164 index sets; S=4096 FP32 samples + top-4 FP64 rescore"},
+          dtype="f64", gpu_launches=int(lrq.lrq_kernel_launches() - l0), clocks=clk.summary(),
+          exact={"f_enumeration": f_exact, "f_best_of_4096": f_samp, "ratio": f_samp / f_exact,
+                 "index_sets": int(out["n_sets"].item())},
+          enumerate_n64={"index_sets": sets, "ms": big_ms, "sets_per_s": sets / (big_ms * 1e-3)})
+
+
+def run_maxcut(args):
+    import torch
+
+    from paper_2602_20376_gb300 import inputs, lrq
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    lrq.load()
+    n, SS, m = 1_000_000, 1 << 17, 64
+    rowptr, colidx, labels = inputs.sbm_graph(n, 4.0, 8.0, seed=1)
+    rp = torch.from_numpy(rowptr).to(dev)
+    ci = torch.from_numpy(colidx).to(dev)
+    Q = lrq.laplacian_matrix(rp, ci)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    tr = lrq.truncate(Q, 3, max_iter=1000, seed=0, want_c128=False)
+    t1.record()
+    torch.cuda.synchronize()
+    trunc_ms = t0.elapsed_time(t1)
+    V = tr["V32"]
+    lam = tr["lam"].cpu().numpy().tolist()
+    cut = torch.zeros(1, dtype=torch.int64, device=dev)
+    planted = torch.from_numpy(np.asarray(labels, dtype=np.uint8)).to(dev)
+    lrq.lrq_cut_count(rp, ci, planted, cut)
+    torch.cuda.synchronize()
+    planted_cut = int(cut.item())
+    ws = lrq.workspace(lrq.lrq_sample_score_workspace_size(n, 3, 3, SS, lrq.LRQ_MODE_BF16_TC, m), dev)
+    wsr = lrq.workspace(lrq.lrq_rescore_workspace_size(n, 3, m), dev)
+
+    def step(i):
+        out = lrq.sample_score(V, 3, C=None, S=SS, seed=1 + i, mode=lrq.LRQ_MODE_BF16_TC, top_m=m, ws=ws)
+        rs = lrq.rescore(V, 3, out["C"], out["top_idx"], want_z=True, ws=wsr)
+        row = torch.nonzero(out["top_idx"] == rs["best"]).flatten()[0]  # z rows follow top_idx
+        lrq.lrq_cut_count(rp, ci, rs["z"][row], cut)
+        return rs
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    a, b = _events(torch, args.steps), _events(torch, args.steps)
+    l0 = lrq.lrq_kernel_launches()
+    with ClockSampler(0) as clk:
+        for i in range(args.steps):
+            a[i].record()
+            rs = step(args.warmup + i)
+            b[i].record()
+        torch.cuda.synchronize()
+    ms = sum(x.elapsed_time(y) for x, y in zip(a, b)) / args.steps
+    edges = int(rowptr[-1]) // 2
+    _line("Max-3-Cut candidate*n evals/s (SBM n=10^6, S=2^17, r=3)", SS * n / (ms * 1e-3), UNIT, args, ms,
+          {"workload": "planted 3-partition SBM n=10^6, p_in n=4, p_out n=8 (seed 1), unit weights, CSR int32; "
+                       "rank-3 FP64 Lanczos truncation of L; S=2^17 BF16 candidates, top-64 FP64 rescore, exact "
+                       "cut of the winner", "edges": edges},
+          dtype="bf16", gpu_launches=int(lrq.lrq_kernel_launches() - l0), clocks=clk.summary(),
+          maxcut={"cut": int(cut.item()), "planted_cut": planted_cut, "edges": edges,
+                  "cut_fraction": int(cut.item()) / edges, "best_f": float(rs["best_f"].item()),
+                  "lambda": lam, "truncate_ms": trunc_ms, "lanczos_steps": tr["iters"]})
+
+
+def run_batched(args):
+    import torch
+
+    from paper_2602_20376_gb300 import inputs, lrq
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    lrq.load()
+    g = inputs.rng(4)
+    P, SS = 512, 8192
+    probs, evals = [], 0
+    tg = torch.Generator(device=dev)
+    t_prep = time.perf_counter()
+    for p in range(P):
+        n = int(np.exp(g.uniform(np.log(64), np.log(8192))))
+        r = int(g.integers(2, 7))
+        Kp = int(g.choice([2, 3, 4, 8]))
+        tg.manual_seed(1000 + p)
+        V0 = torch.randn((n, r), generator=tg, device=dev, dtype=torch.complex128)
+        Q = V0 @ V0.conj().T
+        nrm = torch.linalg.eigvalsh(V0.conj().T @ V0)[-1].item()  # ||V V^H||_2
+        G = torch.randn((n, n), generator=tg, device=dev, dtype=torch.complex128)
+        H = 0.5 * (G + G.conj().T)
+        hn = 2.0 * np.sqrt(n) * np.sqrt(0.5)  # semicircle edge of H: ||H||_2 ~ 2 sqrt(n / 2)
+        Q += (0.05 * nrm / hn) * H
+        del G, H
+        tr = lrq.truncate(lrq.dense_matrix(Q), r, tol=1e-8, seed=p, want_c128=False)
+        del Q
+        probs.append(dict(V=tr["V32"], K=Kp, S=SS, seed=77 + p))
+        evals += n * SS
+    torch.cuda.synchronize()
+    t_prep = time.perf_counter() - t_prep
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plan = lrq.BatchedPlan(probs, top_m=4, stream=stream)
+        t_at = time.perf_counter()
+        plan.autotune()
+        t_at = time.perf_counter() - t_at
+        plan.capture()
+        for _ in range(args.warmup):
+            plan.replay()
+        stream.synchronize()
+        a, b = _events(torch, args.steps), _events(torch, args.steps)
+        ka, kb = _events(torch, args.steps), _events(torch, args.steps)
+        l0 = lrq.lrq_kernel_launches()
+        with ClockSampler(0) as clk:
+            for i in range(args.steps):
+                a[i].record(stream)
+                plan.replay()
+                b[i].record(stream)
+            stream.synchronize()
+        launches = lrq.lrq_kernel_launches() - l0
+        # the persistent kernel alone (timing hook), outside the graph
+        for i in range(args.steps):
+            lrq.lrq_set_timing_events(ka[i], kb[i])
+            plan.run()
+            lrq.lrq_set_timing_events(None, None)
+        stream.synchronize()
+        lrq.check_status(plan.status, "batched")
+    ms = sum(x.elapsed_time(y) for x, y in zip(a, b)) / args.steps
+    kms = sum(x.elapsed_time(y) for x, y in zip(ka, kb)) / args.steps
+    tiles = {}
+    for p in range(P):
+        tiles[plan.tile(p)] = tiles.get(plan.tile(p), 0) + 1
+    flops = 16.0 * sum(q["V"].shape[0] * q["V"].shape[1] * SS for q in probs)
+    peak_alu = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA lanes x 2 flops x max SM clock
+    _line("batched candidate*n evals/s (512 instances, one graph-captured persistent launch)", evals / (ms * 1e-3),
+          UNIT, args, ms,
+          {"workload": "512 instances: n = floor(exp(U[ln 64, ln 8192])), r ~ U{2..6}, K ~ U{2,3,4,8}, "
+                       "Q = V V^H + sigma H (sigma = 0.05 ||V V^H||_2, H GUE-like scaled to ||H||_2 ~ 1), "
+                       "FP64 Lanczos truncation to r; S=8192 drawn directions each, FP32 scoring, top-4 FP64 "
+                       "rescore", "total_evals": evals},
+          dtype="f32", gpu_launches=int(launches), clocks=clk.summary(),
+          roofline={"bound": "alu", "achieved": flops / (kms * 1e-3) / 1e12, "peak": peak_alu, "unit": "TFLOP/s",
+                    "frac": flops / (kms * 1e-3) / 1e12 / peak_alu, "traffic": None,
+                    "kernel": "batched_score_kernel", "kernel_ms": kms,
+                    "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"},
+          batched={"prep_s": t_prep, "autotune_s": t_at, "tiles": tiles})
+    plan.close()
 
 def main():
     ap = argparse.ArgumentParser()
@@ -289,11 +550,19 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the scoring kernel from an ncu capture")
+    ap.add_argument("--workload", choices=["scale", "exact", "maxcut", "batched", "learned"], default="scale")
+    ap.add_argument("--no-learned", action="store_true", help="leave samples_to_best out of the default line")
+    ap.add_argument("--learned-n", type=int, default=4096)
+    ap.add_argument("--learned-train", type=int, default=128)
+    ap.add_argument("--learned-eval", type=int, default=32)
+    ap.add_argument("--learned-steps", type=int, default=400)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    else:
+    elif args.workload == "scale":
         run_ours(args)
+    else:
+        {"exact": run_exact, "maxcut": run_maxcut, "batched": run_batched, "learned": run_learned}[args.workload](args)
 
 
 if __name__ == "__main__":

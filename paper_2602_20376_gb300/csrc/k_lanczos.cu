@@ -39,7 +39,7 @@
 namespace lrq {
 
 constexpr int kLzThreads = 256;
-constexpr int kLzChunk = 4096;     // rows per block in the projection kernels
+constexpr int kLzChunkMax = 4096;  // rows per block in the projection kernels (at most)
 constexpr int kLzGroup = 8;        // basis vectors per block in the projection kernels
 constexpr int kLzWant = kMaxRank;  // at most 8 wanted pairs per run
 constexpr int kLzMaxIter = 4096;
@@ -182,13 +182,13 @@ __global__ void __launch_bounds__(kLzThreads) lz_matvec_dense(const double2* __r
 template <typename T>
 __global__ void __launch_bounds__(kLzThreads) lz_dots(const T* __restrict__ U, int64_t n, int nc,
                                                       const T* __restrict__ w, T* __restrict__ partial, int nch,
-                                                      const LzState* st) {
+                                                      int chunk_rows, const LzState* st) {
   if (st->stop) return;
   __shared__ T red[kLzGroup][kLzThreads / 32];
   const int chunk = blockIdx.x;
   const int cg = blockIdx.y * kLzGroup;
-  const int64_t i0 = static_cast<int64_t>(chunk) * kLzChunk;
-  const int64_t i1 = min(n, i0 + kLzChunk);
+  const int64_t i0 = static_cast<int64_t>(chunk) * chunk_rows;
+  const int64_t i1 = min(n, i0 + chunk_rows);
   T acc[kLzGroup];
 #pragma unroll
   for (int q = 0; q < kLzGroup; ++q) acc[q] = lz_zero<T>();
@@ -226,36 +226,51 @@ __global__ void lz_reduce(const T* __restrict__ partial, int nc, int nch, T* __r
   if (lane == 0) h[c] = s;
 }
 
-// w -= sum_c U_c h[c]  (a thread per row).
+// w -= sum_c U_c h[c]: a block takes 32 rows, its 8 warps take every 8th
+// basis vector (coalesced 32-row loads), and the 8 partial sums of a row are
+// added in warp order (deterministic).
 template <typename T>
 __global__ void __launch_bounds__(kLzThreads) lz_update(const T* __restrict__ U, int64_t n, int nc,
                                                         const T* __restrict__ h, T* __restrict__ w,
                                                         const LzState* st) {
   if (st->stop) return;
-  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
-  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+  __shared__ T part[kLzThreads / 32][32];
+  const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+  constexpr int NS = kLzThreads / 32;
+  for (int64_t r0 = static_cast<int64_t>(blockIdx.x) * 32; r0 < n; r0 += static_cast<int64_t>(gridDim.x) * 32) {
+    const int64_t i = r0 + lane;
     T s0 = lz_zero<T>(), s1 = lz_zero<T>();
-    int c = 0;
-    for (; c + 1 < nc; c += 2) {
-      lz_add(s0, lz_mul(U[static_cast<int64_t>(c) * n + i], h[c]));
-      lz_add(s1, lz_mul(U[static_cast<int64_t>(c + 1) * n + i], h[c + 1]));
+    if (i < n) {
+      int c = slice;
+      for (; c + NS < nc; c += 2 * NS) {
+        lz_add(s0, lz_mul(U[static_cast<int64_t>(c) * n + i], h[c]));
+        lz_add(s1, lz_mul(U[static_cast<int64_t>(c + NS) * n + i], h[c + NS]));
+      }
+      if (c < nc) lz_add(s0, lz_mul(U[static_cast<int64_t>(c) * n + i], h[c]));
     }
-    if (c < nc) lz_add(s0, lz_mul(U[static_cast<int64_t>(c) * n + i], h[c]));
     lz_add(s0, s1);
-    T v = w[i];
-    lz_sub(v, s0);
-    w[i] = v;
+    part[slice][lane] = s0;
+    __syncthreads();
+    if (slice == 0 && i < n) {
+      T t = part[0][lane];
+      for (int k = 1; k < NS; ++k) lz_add(t, part[k][lane]);
+      T v = w[i];
+      lz_sub(v, t);
+      w[i] = v;
+    }
+    __syncthreads();
   }
 }
 
 // npart[chunk] = sum over the chunk of |w_i|^2
 template <typename T>
 __global__ void __launch_bounds__(kLzThreads) lz_norm_partial(const T* __restrict__ w, int64_t n,
-                                                              double* __restrict__ npart, const LzState* st) {
+                                                              double* __restrict__ npart, int chunk_rows,
+                                                              const LzState* st) {
   if (st->stop) return;
   __shared__ double red[kLzThreads / 32];
-  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * kLzChunk;
-  const int64_t i1 = min(n, i0 + kLzChunk);
+  const int64_t i0 = static_cast<int64_t>(blockIdx.x) * chunk_rows;
+  const int64_t i1 = min(n, i0 + chunk_rows);
   double s = 0.0;
   for (int64_t i = i0 + threadIdx.x; i < i1; i += blockDim.x) s += lz_abs2(w[i]);
   s = lz_warp_sum(s);
@@ -604,7 +619,7 @@ namespace {
 
 struct LzPlan {
   int64_t n;
-  int r, maxit, lmax, cap, nch, ldx;
+  int r, maxit, lmax, cap, nch, chunk, ldx;
   size_t esz;
   size_t off_U, off_w, off_Y, off_part, off_h1, off_h2, off_npart, off_alpha, off_beta, off_state, off_check, off_X,
       off_work, total;
@@ -622,7 +637,10 @@ void lz_plan(int64_t n, int r, int maxit, bool cplx, LzPlan* p) {
   p->maxit = maxit;
   p->lmax = 2 * r + 8;                    // locked vectors (repeated eigenvalues need extra slots)
   p->cap = p->lmax + maxit + 1;           // basis columns
-  p->nch = static_cast<int>(ceil_div(n, kLzChunk));
+  // about two row chunks per SM, 256 to 4096 rows each
+  p->chunk = static_cast<int>(std::min<int64_t>(
+      kLzChunkMax, std::max<int64_t>(256, static_cast<int64_t>(align_up(ceil_div(n, 2 * 152), 256)))));
+  p->nch = static_cast<int>(ceil_div(n, p->chunk));
   p->ldx = maxit + 1;
   p->esz = cplx ? sizeof(double2) : sizeof(double);
   size_t cur = 0;
@@ -684,15 +702,16 @@ struct LzRun {
   void project(int nc, T* h) const {
     if (nc <= 0) return;
     dim3 g(p.nch, static_cast<unsigned>(ceil_div(nc, kLzGroup)));
-    lz_dots<T><<<g, kLzThreads, 0, st>>>(U(), n, nc, w(), part(), p.nch, state());
+    lz_dots<T><<<g, kLzThreads, 0, st>>>(U(), n, nc, w(), part(), p.nch, p.chunk, state());
     lz_reduce<T><<<static_cast<unsigned>(ceil_div(static_cast<int64_t>(nc) * 32, 256)), 256, 0, st>>>(
         part(), nc, p.nch, h, state());
-    lz_update<T><<<lz_rows_grid(n), kLzThreads, 0, st>>>(U(), n, nc, h, w(), state());
+    lz_update<T><<<static_cast<unsigned>(std::min<int64_t>(ceil_div(n, 32), 152 * 16)), kLzThreads, 0, st>>>(
+        U(), n, nc, h, w(), state());
     count_launch(3);
   }
   // normalise w into column c; mode 0 closes Lanczos step j (column c - 1)
   void close(int c, int j, int mode) const {
-    lz_norm_partial<T><<<p.nch, kLzThreads, 0, st>>>(w(), n, npart(), state());
+    lz_norm_partial<T><<<p.nch, kLzThreads, 0, st>>>(w(), n, npart(), p.chunk, state());
     lz_finish<T><<<1, 32, 0, st>>>(npart(), p.nch, h1(), h2(), c - 1, j, mode, alpha(), beta(), state());
     lz_scale_into<T><<<lz_rows_grid(n), kLzThreads, 0, st>>>(w(), n, col(c), state());
     count_launch(3);

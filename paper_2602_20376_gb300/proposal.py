@@ -51,7 +51,8 @@ def truncate_instances(n: int, seeds, device="cuda"):
     Vs, lams = [], []
     for s in seeds:
         Q, _, _ = make_instance(n, s, device)
-        out = lrq.truncate(lrq.dense_matrix(Q), R, seed=int(s), want_c128=False, want_c64=True, device=device)
+        out = lrq.truncate(lrq.dense_matrix(Q), R, tol=1e-8, seed=int(s), want_c128=False, want_c64=True,
+                           device=device)
         Vs.append(out["V32"])
         lams.append(out["lam"])
         del Q

@@ -218,3 +218,22 @@ def test_adam_step_matches_oracle(lrq):
     assert np.abs(P.cpu().numpy() - p_ref).max() <= 1e-6
     assert np.abs(M.cpu().numpy() - m_ref).max() <= 1e-6
     assert np.abs(Vv.cpu().numpy() - v_ref).max() <= 1e-6
+
+
+@pytest.mark.slow
+def test_trained_proposal_beats_uniform_sampling(lrq):
+    # angular synchronisation at n = 1024 (K = 8, rank-4 truncation): train on
+    # the top 1% of 2^14 uniform directions of 96 instances, then on 16
+    # held-out instances count the samples each stream needs to reach 0.999 of
+    # the best of 2^16 uniform samples
+    from paper_2602_20376_gb300 import proposal as P
+    n, ntrain, neval = 1024, 96, 16
+    V, lam = P.truncate_instances(n, range(10 ** 6, 10 ** 6 + ntrain + neval))
+    Vg, feat = P.features(V, lam)
+    targets = P.training_targets(Vg[:ntrain], 8, 1 << 14, 555)
+    model = P.Proposal(feat.shape[1], seed=0)
+    model.fit_standardizer(feat[:ntrain])
+    losses = P.train(model, feat[:ntrain], targets, 300, 64, 1e-3)
+    assert float(losses[-10:].mean()) < float(losses[:10].mean()) - 1.0
+    rows = P.evaluate(model, Vg[ntrain:], feat[ntrain:], 8, 1 << 16, 777)
+    assert P.median_gain(rows) >= 4.0
