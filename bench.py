@@ -167,7 +167,7 @@ def run_ours(args):
     import torch
     import torch.distributed as dist
 
-    from paper_2602_20376_gb300 import inputs, lrq
+    from paper_2602_20376_gb300 import inputs, lrq, multi
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -194,7 +194,7 @@ def run_ours(args):
     stream = torch.cuda.current_stream(dev)
 
     def step(s):
-        seed = 1 + s * world + rank
+        seed = multi.direction_seed(s, world, rank)
         lrq.lrq_sample_score(V, K, C, True, seed, mode, TOP_M, None, top_idx, top_f, ws, status, stream)
         lrq.lrq_rescore(V, K, C, top_idx, f64, None, best, best_f, ws_r, status, stream)
 
@@ -226,10 +226,9 @@ def run_ours(args):
     lrq.check_status(status, "timed steps")
     step_ms = float(sum(a.elapsed_time(b) for a, b in zip(s_start, s_stop)))
     kern_ms = float(sum(a.elapsed_time(b) for a, b in zip(k_start, k_stop)))
-    t_max = torch.tensor([step_ms], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    step_ms = float(t_max.item())
+    step_ms = multi.max_over_ranks(step_ms, device=dev)
+    # the only exchange of the path: each rank's winner of its last step
+    win_f, win_rank, win_idx = multi.merge_best(float(best_f.item()), int(best.item()), device=dev)
     evals = float(world) * args.steps * S * N
     value = evals / (step_ms * 1e-3)
 
@@ -277,6 +276,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "clocks": clk.summary(),
         "samples_to_best": None,
+        "winner": {"f": win_f, "rank": win_rank, "candidate": win_idx},
     }
     if world == 1 and not args.no_learned:
         line["samples_to_best"] = learned_gain(dev, args.learned_n, args.learned_train, args.learned_eval,
