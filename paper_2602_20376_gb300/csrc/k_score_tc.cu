@@ -27,14 +27,13 @@
 // registers (error-free) and written as FP64 partials per coordinate chunk.
 //
 // Pipeline (one CTA per SM, persistent over (chunk, candidate tile) items):
-//   warp 0  : TMA producer (augmented rows + B2 rows per coordinate tile,
-//             directions per item), ring of kStages shared-memory stages;
-//   warp 1  : TMEM allocation and MMA issue (one elected thread);
-//   warps 4+: NE epilogue warpgroups; each reads its slice of the D1 tile
-//             from TMEM, builds indicator words, stores them to shared memory
-//             as GEMM2's A operand; warpgroup 0 also folds the D2 partials.
-// D1 and the indicator buffers are double-buffered so GEMM1 of tile t+1 and
-// GEMM2 of tile t-1 run on the tensor core while tile t is being rounded.
+// NW independent workers per CTA, each a warpgroup (one thread per
+// candidate of the 128-candidate tile) with its own TMA producer thread
+// (warps 0..NW-1), stage ring and TMEM slice (D1 projections, A2 indicator
+// words, D2 accumulator).  Per tile the worker reads D1 from TMEM, rounds it
+// into indicator words written back to TMEM (tcgen05.st) as GEMM2's A
+// operand, and one fixed thread of the worker issues GEMM2 of this tile and
+// GEMM1 of the next; the workers of a CTA interleave on the tensor core.
 // Every wait is bounded; on expiry the kernel records LRQ_ETIMEOUT, drains
 // its in-flight copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
@@ -65,11 +64,15 @@ constexpr long long kWaitLimit = 2000000000LL;
 template <int K>
 struct TcShape {
   static constexpr int BK = (K % 2 == 0) ? K / 2 : K;
+  // boundary lines projected by GEMM1: all B_K, except K = 3 where the three
+  // lines' directions sum to zero, so p_1 = -(p_0 + p_2) is formed on the
+  // CUDA cores
+  static constexpr int BKG = (K == 3) ? 2 : BK;
   static constexpr int G = (K % 2 == 0) ? K / 2 : K - 1;
-  static constexpr int NW = K == 2 ? 4 : K == 3 ? 3 : K == 4 ? 4 : K == 5 ? 2 : K == 6 ? 3 : K == 7 ? 2 : 2;
+  static constexpr int NW = K == 2 ? 4 : K == 3 ? 4 : K == 4 ? 4 : K == 5 ? 2 : K == 6 ? 3 : K == 7 ? 2 : 2;
   static constexpr int R = K == 2 ? 64 : K == 7 ? 16 : 32;
   static constexpr int ROWS = R;  // coordinates per tile (packing granularity)
-  static constexpr int N1 = BK * R;    // GEMM1 N
+  static constexpr int N1 = BKG * R;   // GEMM1 N
   static constexpr int KD2 = G * R;    // GEMM2 reduction length per tile
   static constexpr int A2COLS = KD2 / 2;
   static constexpr int WCOLS = N1 + A2COLS + 16;
@@ -79,6 +82,8 @@ struct TcShape {
   static_assert(KD2 % 16 == 0, "GEMM2 K");
   static_assert(R % 16 == 0, "rows are processed 16 at a time");
   static constexpr int THREADS = 128 + 128 * NW;
+  // boundary line whose projections fill GEMM1 row block b
+  static constexpr __host__ __device__ int line(int b) { return (K == 3 && b == 1) ? 2 : b; }
 };
 
 constexpr int align1k(int x) { return (x + 1023) / 1024 * 1024; }
@@ -141,16 +146,16 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-// GEMM1 of one tile of a worker: wait for the stage's operands, then
-// D1 = A1[ab] x Vaug(stage)^T and commit to d1_full.  wsm_s is the shared
+// GEMM1 of one tile of a worker: wait for the stage's operands (unless the
+// caller already did), then D1 = A1[ab] x Vaug(stage)^T and commit to d1_full.  wsm_s is the shared
 // address of the worker's region.
 template <class L>
 __device__ __forceinline__ bool tc_issue_gemm1(uint32_t tw, uint32_t wsm_s, uint32_t smem_base, uint64_t* full_b,
                                                uint64_t* d1_full, uint32_t stage, uint32_t sphase, uint32_t ab,
-                                               volatile int* abort) {
+                                               volatile int* abort, bool wait_stage = true) {
   using Sh = typename L::Sh;
   constexpr bool two_chunks = (L::N2R == 16);
-  if (!ptx::mbar_wait(&full_b[stage], sphase, abort, kWaitLimit)) return false;
+  if (wait_stage && !ptx::mbar_wait(&full_b[stage], sphase, abort, kWaitLimit)) return false;
   ptx::tc_fence_after();
   const uint32_t a1 = wsm_s + L::W_A1 + ab * L::A1_BYTES;
   const uint32_t lbo_a1 = two_chunks ? kTcM * 16u : (smem_base + L::ZERO_OFF - a1);
@@ -292,17 +297,23 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
   } else if (warp >= 4) {
     // ------------------------------------------------------------ worker warpgroup w
     // Thread `row` owns candidate `row` of every tile.  Per tile g:
-    //   wait D1(g) -> round its R coordinates into indicator words -> D1
-    //   consumed (the issuing thread starts GEMM1(g+1) into it) -> store the
-    //   words into A2 once GEMM2(g-1) released it -> GEMM2(g) into D2 ->
-    //   every `flush` tiles fold D2 into the two-sum partials.
-    // The issuing thread rotates over the four warps of the warpgroup.
+    //   wait D1(g) -> round its R coordinates into indicator words -> store
+    //   them into A2 -> one warpgroup rendezvous -> the issuing thread issues
+    //   GEMM2(g) and then GEMM1(g+1), both committed behind one d1_full
+    //   arrival, so seeing D1(g+1) also certifies that GEMM2(g) has released
+    //   A2 (tcgen05.commit tracks every earlier MMA of the committing thread)
+    //   -> every `flush` tiles fold D2 into the two-sum partials.
+    // One fixed thread issues every MMA of the worker (needed for the
+    // ordering argument); it also waits for the TMA stage of tile g+2 while
+    // the tensor core runs, so that GEMM1(g+1) never waits on a copy.
     const int qtr = warp & 3;         // TMEM lane quarter
     const int row = qtr * 32 + lane;  // candidate row within the tile
+    const bool issuer = (qtr == 0 && lane == 0);
     const uint32_t lane_base = static_cast<uint32_t>(qtr * 32) << 16;
     const uint32_t tw = tmem + w * Sh::WCOLS;  // this worker's TMEM slice
     constexpr uint32_t idesc2 = ptx::idesc_bf16_f32(kTcM, 16);
     constexpr uint32_t lbo_b2 = L::N2R * 16;
+    constexpr int BKG = Sh::BKG;
     float2* acc = reinterpret_cast<float2*>(wsm + L::W_ACC) + row * 16;  // (hi, lo) per component
 
     // the worker's tile sequence: items gw, gw + workers, ...; tiles in order
@@ -314,44 +325,64 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
       const int64_t t0 = (it / c_tiles) * tpc;
       return static_cast<int>(min(prm.n_tiles, t0 + tpc) - t0);
     };
+    auto stage_next = [](uint32_t& s, uint32_t& ph) {
+      if (++s == NST) {
+        s = 0;
+        ph ^= 1u;
+      }
+    };
+    uint32_t g = 0, pe = 0, stage = 0, sphase = 0, a1c = 0;
+    int pos = 0;       // tile position within the accumulation period
+    bool bad = false;  // this thread saw a wait give up (carried to the next barrier)
     if (item < prm.num_items) {
       chunk = item / c_tiles;
       ct = item % c_tiles;
       ntile = tiles_of(item);
       next_ntile = tiles_of(item + workers);
-      // prologue: GEMM1 of the first tile (a failure reaches every thread
-      // through the abort flag at the first wait)
-      if (qtr == 0 && lane == 0) {
-        if (!ptx::mbar_wait(&a1_full[0], 0u, abort_flag, kWaitLimit) ||
-            !tc_issue_gemm1<L>(tw, wsm_s, smem_base, full_b, d1_full, 0u, 0u, 0u, abort_flag))
-          *abort_flag = 1;
-        else if (ntile == 1)
-          ptx::mma_commit(&a1_empty[0]);
+      // prologue: GEMM1 of the first tile, then the stage of the second
+      // (a failure reaches every thread through the abort flag)
+      if (issuer) {
+        bool ok = ptx::mbar_wait(&a1_full[0], 0u, abort_flag, kWaitLimit) &&
+                  tc_issue_gemm1<L>(tw, wsm_s, smem_base, full_b, d1_full, 0u, 0u, 0u, abort_flag);
+        if (ok && ntile == 1) ptx::mma_commit(&a1_empty[0]);
+        if (ok && (ntile > 1 || next_ntile > 0)) {
+          uint32_t s1 = 0, p1 = 0;
+          stage_next(s1, p1);
+          ok = ptx::mbar_wait(&full_b[s1], p1, abort_flag, kWaitLimit);
+        }
+        if (!ok) *abort_flag = 1;
       }
     }
-    uint32_t g = 0, pe = 0, stage = 0, sphase = 0, a1c = 0;
-    uint32_t prev_stage = 0, prev_phase = 0;
-    int pos = 0;        // tile position within the accumulation period
-    bool bad = false;   // this thread saw a wait give up (carried to the next barrier)
     while (item < prm.num_items) {
       const bool first = pos == 0;
       const bool last = (pos == F - 1) || (j == ntile - 1);
-      // ---- round the projections of tile g
+      const bool item_end = (j == ntile - 1);
+      const bool has_next = !item_end || next_ntile > 0;
+      // ---- round the projections of tile g into indicator words in A2
       bad = bad || !warp_wait(d1_full, g & 1u, abort_flag, lane);
-      uint32_t wv[G][R / 2];
       if (!bad) {
         ptx::tc_fence_after();
+        uint32_t wv[G][R / 2];
 #pragma unroll
         for (int h = 0; h < R / 16; ++h) {
-          uint32_t pl[BK][16];
+          uint32_t pl[BKG][16];
 #pragma unroll
-          for (int m = 0; m < BK; ++m) ptx::tmem_ld_x16(tw + lane_base + Sh::D1_OFF + m * R + h * 16, pl[m]);
+          for (int b = 0; b < BKG; ++b) ptx::tmem_ld_x16(tw + lane_base + Sh::D1_OFF + b * R + h * 16, pl[b]);
           ptx::tmem_wait_ld();
 #pragma unroll
           for (int p = 0; p < 8; ++p) {
             uint32_t nm[BK];
+            if constexpr (K == 3) {
+              // p_1 = -(p_0 + p_2): the three boundary directions sum to zero
+              const float q0 = -(__uint_as_float(pl[0][2 * p]) + __uint_as_float(pl[1][2 * p]));
+              const float q1 = -(__uint_as_float(pl[0][2 * p + 1]) + __uint_as_float(pl[1][2 * p + 1]));
+              nm[0] = ptx::prmt(pl[0][2 * p], pl[0][2 * p + 1], 0xFFBBu);
+              nm[1] = ptx::prmt(__float_as_uint(q0), __float_as_uint(q1), 0xFFBBu);
+              nm[2] = ptx::prmt(pl[1][2 * p], pl[1][2 * p + 1], 0xFFBBu);
+            } else {
 #pragma unroll
-            for (int m = 0; m < BK; ++m) nm[m] = ptx::prmt(pl[m][2 * p], pl[m][2 * p + 1], 0xFFBBu);
+              for (int m = 0; m < BK; ++m) nm[m] = ptx::prmt(pl[m][2 * p], pl[m][2 * p + 1], 0xFFBBu);
+            }
 #pragma unroll
             for (int gc = 0; gc < G; ++gc) {
               if constexpr (K % 2 == 1)
@@ -361,36 +392,6 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
             }
           }
         }
-      }
-      ptx::tc_fence_before();
-      // D1 consumed by the whole warpgroup; every thread leaves together on failure
-      if (ptx::named_barrier_or(1 + w, 128, bad)) break;
-      // ---- next tile's position in the sequence; GEMM1 of the next tile
-      const uint32_t next_stage = (stage + 1 == NST) ? 0u : stage + 1;
-      const uint32_t next_sphase = (stage + 1 == NST) ? (sphase ^ 1u) : sphase;
-      const bool item_end = (j == ntile - 1);
-      const bool has_next = !item_end || next_ntile > 0;
-      if (qtr == static_cast<int>(g & 3u) && lane == 0 && has_next) {
-        ptx::tc_fence_after();
-        uint32_t nab = a1c & 1u;
-        bool okk = true;
-        if (item_end) {  // the next tile opens the next item: wait for its directions
-          nab ^= 1u;
-          okk = ptx::mbar_wait(&a1_full[nab], ((a1c + 1) >> 1) & 1u, abort_flag, kWaitLimit);
-        }
-        okk = okk && tc_issue_gemm1<L>(tw, wsm_s, smem_base, full_b, d1_full, next_stage, next_sphase, nab,
-                                       abort_flag);
-        if (okk) {
-          // the next tile is the last of its item: release that A1 buffer
-          if ((item_end ? 0 : j + 1) == (item_end ? next_ntile : ntile) - 1) ptx::mma_commit(&a1_empty[nab]);
-        } else {
-          *abort_flag = 1;
-        }
-      }
-      // ---- indicators into A2, once GEMM2 of the previous tile released it
-      bad = g > 0 && !warp_wait(&empty_b[prev_stage], prev_phase, abort_flag, lane);
-      if (!bad) {
-        ptx::tc_fence_after();
 #pragma unroll
         for (int gc = 0; gc < G; ++gc) {
           if constexpr (R == 16)
@@ -405,9 +406,12 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
         ptx::tmem_wait_st();
       }
       ptx::tc_fence_before();
+      // D1 read and A2 written by the whole warpgroup; all leave together on failure
       if (ptx::named_barrier_or(1 + w, 128, bad)) break;
-      // ---- GEMM2 of tile g
-      if (qtr == static_cast<int>((g + 2) & 3u) && lane == 0) {
+      // ---- the issuing thread: GEMM2(g), then GEMM1(g+1), then the stage of g+2
+      uint32_t s1 = stage, p1 = sphase;
+      stage_next(s1, p1);  // stage of tile g+1
+      if (issuer) {
         ptx::tc_fence_after();
         const uint32_t b2 = wsm_s + stage * L::STAGE_BYTES + L::B2_OFF_IN_STAGE;
 #pragma unroll
@@ -417,8 +421,31 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
           ptx::mma_bf16_ts(tw + Sh::D2_OFF, tw + Sh::A2_OFF + q * 8, ptx::smem_desc(bstart, lbo_b2, sbo_b2), idesc2,
                            (q > 0 || !first) ? 1u : 0u);
         }
-        ptx::mma_commit(&empty_b[stage]);  // releases the stage and A2
+        ptx::mma_commit(&empty_b[stage]);  // releases the stage (GEMM1(g) and GEMM2(g) read it)
         if (last) ptx::mma_commit(d2_ready);
+        bool ok = true;
+        if (has_next) {
+          uint32_t nab = a1c & 1u;
+          if (item_end) {  // the next tile opens the next item: wait for its directions
+            nab ^= 1u;
+            ok = ptx::mbar_wait(&a1_full[nab], ((a1c + 1) >> 1) & 1u, abort_flag, kWaitLimit);
+          }
+          // stage s1 was waited for one tile ago (or in the prologue): p1 is complete
+          ok = ok && tc_issue_gemm1<L>(tw, wsm_s, smem_base, full_b, d1_full, s1, p1, nab, abort_flag, false);
+          if (ok && (item_end ? 0 : j + 1) == (item_end ? next_ntile : ntile) - 1) ptx::mma_commit(&a1_empty[nab]);
+          // does a tile g+2 exist?  (then wait for its stage while the MMAs run)
+          bool has_next2;
+          if (!item_end)
+            has_next2 = (j + 2 < ntile) || next_ntile > 0;
+          else
+            has_next2 = next_ntile > 1 || tiles_of(item + 2 * workers) > 0;
+          if (ok && has_next2) {
+            uint32_t s2 = s1, p2 = p1;
+            stage_next(s2, p2);
+            ok = ptx::mbar_wait(&full_b[s2], p2, abort_flag, kWaitLimit);
+          }
+        }
+        if (!ok) *abort_flag = 1;
       }
       // ---- fold the period's accumulator into the two-sum partials
       if (last) {
@@ -451,10 +478,8 @@ __global__ void __launch_bounds__(TcShape<K>::THREADS, 1)
       }
       // ---- advance
       pos = last ? 0 : pos + 1;
-      prev_stage = stage;
-      prev_phase = sphase;
-      stage = next_stage;
-      sphase = next_sphase;
+      stage = s1;
+      sphase = p1;
       ++g;
       if (item_end) {
         ++a1c;
@@ -500,7 +525,8 @@ struct PackTables {
   float beta_r[8], beta_i[8];  // per-indicator coefficients
 };
 
-// augmented rows: tile t, chunk ch, row (m*ROWS + i), 8 slots
+// augmented rows: tile t, chunk ch, row (b*ROWS + i) for boundary line
+// line(b), 8 slots
 template <int K, int KCH>
 __global__ void pack_vaug_kernel(const float2* __restrict__ V, int64_t n, int r, int64_t n_tiles, PackTables tb,
                                  __nv_bfloat16* __restrict__ vt) {
@@ -510,7 +536,7 @@ __global__ void pack_vaug_kernel(const float2* __restrict__ V, int64_t n, int r,
   if (q >= total) return;
   const int64_t t = q / Sh::N1;
   const int rowin = static_cast<int>(q % Sh::N1);
-  const int m = rowin / Sh::ROWS, i = rowin % Sh::ROWS;
+  const int m = Sh::line(rowin / Sh::ROWS), i = rowin % Sh::ROWS;
   const int64_t ig = t * Sh::ROWS + i;
   float slot[16];
 #pragma unroll
@@ -725,8 +751,18 @@ int tc_workers_per_cta(int K) {
 
 size_t tc_bytes_vaug(int K, int r, int64_t n_tiles) {
   int kch = r <= 4 ? 1 : 2;
-  int bk = (K % 2 == 0) ? K / 2 : K;
-  return static_cast<size_t>(n_tiles) * kch * bk * tc_rows_per_tile(K) * 16;
+  int n1 = 0;
+  switch (K) {
+    case 2: n1 = TcShape<2>::N1; break;
+    case 3: n1 = TcShape<3>::N1; break;
+    case 4: n1 = TcShape<4>::N1; break;
+    case 5: n1 = TcShape<5>::N1; break;
+    case 6: n1 = TcShape<6>::N1; break;
+    case 7: n1 = TcShape<7>::N1; break;
+    case 8: n1 = TcShape<8>::N1; break;
+    default: return 0;
+  }
+  return static_cast<size_t>(n_tiles) * kch * n1 * 16;
 }
 
 size_t tc_bytes_b2(int K, int r, int64_t n_tiles) {
