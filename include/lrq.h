@@ -290,6 +290,38 @@ int lrq_truncate(const lrq_matrix* Q, int r, double tol, int max_iter, uint64_t 
                  void* stream);
 
 /* --------------------------------------------------------------------------
+ * lrq_rank1_sweep -- exact maximiser for rank 1 by an angular sweep
+ * (Sec. 2.5, Algorithm 1), optionally scored on a graph's exact cut.
+ *
+ * For Q = q q^H and c = exp(i phi), every code of z(c) advances once as phi
+ * runs over one period 2 pi / K; the optimum of |q^H z|^2 is one of the
+ * n + 1 states met on the way.  Convention: t_i = K arg(q_i) / (2 pi); state
+ * 0 has codes floor(t_i) mod K; coordinate i advances at
+ * phi_i = (2 pi / K)(1/2 + floor(t_i) - t_i); state s has advanced the s
+ * coordinates first in the order (phi_i, i).  All states are evaluated in
+ * FP64 (sort, prefix sums); ties go to the earliest state.
+ *
+ *   q        : n complex128 (device), e.g. sqrt(lambda_1) u_1 from
+ *              lrq_truncate with r = 1.
+ *   z_out    : n uint8 codes of the best state (device), f_out: 1 double,
+ *              its |q^H z|^2 (device).
+ *   rowptr, colidx, nnz : optional undirected graph, symmetric CSR int32
+ *              (each edge in both rows, self loops ignored); NULL to skip.
+ *              Then cut_out (1 int64) and zcut_out (n uint8) receive the
+ *              state with the largest exact cut #{edges with k_i != k_j}
+ *              and its codes: the sweep path of the rank-1 relaxation scored
+ *              on the true Max-K-Cut objective (Sec. 1), all n + 1 states at
+ *              once through a per-edge difference array.
+ *   ws       : lrq_rank1_workspace_size(n) bytes.
+ * Limits: 1 <= n < 2^31, 2 <= K <= 64.  Non-finite q -> LRQ_EINVAL in
+ * *dev_status.  CSR reads are bounds-guarded by nnz.
+ * ------------------------------------------------------------------------ */
+int lrq_rank1_workspace_size(int64_t n, size_t* bytes);
+int lrq_rank1_sweep(const void* q, int64_t n, int K, uint8_t* z_out, double* f_out, const int32_t* rowptr,
+                    const int32_t* colidx, int64_t nnz, int64_t* cut_out, uint8_t* zcut_out, void* ws,
+                    size_t ws_bytes, int32_t* dev_status, void* stream);
+
+/* --------------------------------------------------------------------------
  * lrq_enumerate -- exact maximiser for rank r by vertex enumeration.
  *
  * Sec. 3, Algorithm 2 (with Theorem 3.2: for Q = V V^H of rank r the

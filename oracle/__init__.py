@@ -249,6 +249,37 @@ def rank1_sweep(q, K: int):
     return float(f), z
 
 
+def rank1_sweep_states(q, K: int):
+    """The n + 1 states of the rank-1 angular sweep (Sec. 2.5, Algorithm 1):
+    state 0 has codes floor(t_i) mod K, t_i = K arg(q_i) / (2 pi); coordinate
+    i advances at phi_i = (2 pi / K)(1/2 + floor(t_i) - t_i); state s has
+    advanced the first s coordinates in the order (phi_i, i).  Returns
+    (codes of state 0, the advancing order)."""
+    q = _c128(q).ravel()
+    t = K * np.arctan2(q.imag, q.real) / (2 * np.pi)
+    fl = np.floor(t)
+    phi = (2 * np.pi / K) * (0.5 + fl - t)
+    order = np.lexsort((np.arange(q.size), phi))
+    return (np.mod(fl, K)).astype(np.uint8), order
+
+
+def rank1_sweep_cut(q, K: int, rowptr, colidx):
+    """Every state of the rank-1 sweep scored on the graph's exact cut
+    (Max-K-Cut, Sec. 1); returns (best cut, its codes, all n + 1 cuts), ties
+    to the earliest state."""
+    z, order = rank1_sweep_states(q, K)
+    z = z.copy()
+    cuts = [cut_count(rowptr, colidx, z)]
+    best, best_z = cuts[0], z.copy()
+    for i in order:
+        z[i] = (z[i] + 1) % K
+        c = cut_count(rowptr, colidx, z)
+        cuts.append(c)
+        if c > best:
+            best, best_z = c, z.copy()
+    return best, best_z, np.array(cuts)
+
+
 # --------------------------------------------------------------------------
 # Exact rank-r vertex enumeration (Sec. 3, Algorithm 2)
 # --------------------------------------------------------------------------

@@ -397,6 +397,26 @@ int lrq_adam_step(float* params, const float* grads, float* m, float* v, int64_t
   return launch_adam(params, grads, m, v, count, t, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream));
 }
 
+int lrq_rank1_workspace_size(int64_t n, size_t* bytes) {
+  if (!bytes) return fail(LRQ_EINVAL, "bytes is NULL");
+  if (n < 1 || n >= (int64_t(1) << 31)) return fail(LRQ_EINVAL, "n must be in [1, 2^31)");
+  *bytes = rank1_workspace_bytes(n);
+  return LRQ_OK;
+}
+
+int lrq_rank1_sweep(const void* q, int64_t n, int K, uint8_t* z_out, double* f_out, const int32_t* rowptr,
+                    const int32_t* colidx, int64_t nnz, int64_t* cut_out, uint8_t* zcut_out, void* ws,
+                    size_t ws_bytes, int32_t* dev_status, void* stream) {
+  if (n < 1 || n >= (int64_t(1) << 31)) return fail(LRQ_EINVAL, "n must be in [1, 2^31)");
+  if (K < 2 || K > kMaxK) return fail(LRQ_EINVAL, "K must be in [2, 64]");
+  if (!q || !z_out || !f_out || !dev_status) return fail(LRQ_EINVAL, "NULL pointer argument");
+  if (rowptr && (!colidx || !cut_out || !zcut_out || nnz < 0)) return fail(LRQ_EINVAL, "incomplete graph arguments");
+  int e = check_ws(ws, ws_bytes, rank1_workspace_bytes(n));
+  if (e) return e;
+  return launch_rank1(static_cast<const double2*>(q), n, K, z_out, f_out, rowptr, colidx, nnz, cut_out, zcut_out,
+                      ws, dev_status, static_cast<cudaStream_t>(stream));
+}
+
 int lrq_enumerate_workspace_size(int64_t n, int r, int K, size_t* bytes) {
   if (!bytes) return fail(LRQ_EINVAL, "bytes is NULL");
   int e = enumerate_check(n, r, K, 1e300);

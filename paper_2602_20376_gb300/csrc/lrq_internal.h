@@ -123,6 +123,11 @@ int launch_vmf_sample(const float* O, int B, int S, int K, uint64_t seed, float2
                       cudaStream_t st);
 int launch_adam(float* p, const float* g, float* m, float* v, int64_t count, int t, float lr, float b1, float b2,
                 float eps, cudaStream_t st);
+// exact rank-1 sweep (FP64)
+size_t rank1_workspace_bytes(int64_t n);
+int launch_rank1(const double2* q, int64_t n, int K, uint8_t* z_out, double* f_out, const int32_t* rowptr,
+                 const int32_t* colidx, int64_t nnz, int64_t* cut_out, uint8_t* zcut_out, void* ws, int32_t* status,
+                 cudaStream_t st);
 // vertex enumeration (FP64)
 int enumerate_check(int64_t n, int r, int K, double budget);
 size_t enum_workspace_bytes(int64_t n, int r);

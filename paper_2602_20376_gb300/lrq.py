@@ -143,6 +143,10 @@ def load() -> ctypes.CDLL:
         lib.lrq_truncate.argtypes = [ctypes.POINTER(LrqMatrix), I, ctypes.c_double, I, U64, P, P, P,
                                      ctypes.POINTER(I64), P, SZ, P, P]
         lib.lrq_truncate.restype = I
+        lib.lrq_rank1_workspace_size.argtypes = [I64, ctypes.POINTER(SZ)]
+        lib.lrq_rank1_workspace_size.restype = I
+        lib.lrq_rank1_sweep.argtypes = [P, I64, I, P, P, P, P, I64, P, P, P, SZ, P, P]
+        lib.lrq_rank1_sweep.restype = I
         lib.lrq_enumerate_workspace_size.argtypes = [I64, I, I, ctypes.POINTER(SZ)]
         lib.lrq_enumerate_workspace_size.restype = I
         lib.lrq_enumerate.argtypes = [P, I64, I, I, ctypes.c_double, P, P, P, P, SZ, P, P]
@@ -162,7 +166,7 @@ def exported_symbols():
     return ["lrq_status_string", "lrq_last_error", "lrq_abi_version", "lrq_sample_directions",
             "lrq_sample_score_workspace_size", "lrq_sample_score", "lrq_rescore_workspace_size",
             "lrq_rescore", "lrq_rescore_no_alloc", "lrq_truncate_workspace_size", "lrq_truncate",
-            "lrq_enumerate_workspace_size", "lrq_enumerate", "lrq_batched_plan_create", "lrq_batched_plan_destroy",
+            "lrq_rank1_workspace_size", "lrq_rank1_sweep", "lrq_enumerate_workspace_size", "lrq_enumerate", "lrq_batched_plan_create", "lrq_batched_plan_destroy",
             "lrq_batched_workspace_size", "lrq_batched_prepare", "lrq_batched_autotune", "lrq_batched_tile",
             "lrq_sample_score_batched", "lrq_batched_graph_create", "lrq_graph_launch", "lrq_graph_destroy",
             "lrq_proposal_num_features", "lrq_proposal_num_params", "lrq_proposal_features", "lrq_mlp_forward",
@@ -323,6 +327,21 @@ def lrq_truncate(Q: LrqMatrix, r: int, tol: float, max_iter: int, seed: int, V_o
                                _ptr(V32_out), _ptr(lambda_out), ctypes.byref(iters), _ptr(ws),
                                ws.numel() * ws.element_size(), _ptr(dev_status), _stream(stream)), "lrq_truncate")
     return int(iters.value)
+
+
+def lrq_rank1_workspace_size(n: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().lrq_rank1_workspace_size(int(n), ctypes.byref(out)), "lrq_rank1_workspace_size")
+    return int(out.value)
+
+
+def lrq_rank1_sweep(q, K, z_out, f_out, rowptr, colidx, cut_out, zcut_out, ws, dev_status, stream=None):
+    """q: n complex128 (device); rowptr/colidx: int32 CSR or None."""
+    n = q.numel()
+    nnz = 0 if colidx is None else colidx.numel()
+    _check(load().lrq_rank1_sweep(_ptr(q), n, int(K), _ptr(z_out), _ptr(f_out), _ptr(rowptr), _ptr(colidx), nnz,
+                                  _ptr(cut_out), _ptr(zcut_out), _ptr(ws), ws.numel() * ws.element_size(),
+                                  _ptr(dev_status), _stream(stream)), "lrq_rank1_sweep")
 
 
 def lrq_enumerate_workspace_size(n: int, r: int, K: int) -> int:
@@ -508,3 +527,17 @@ class BatchedPlan:
             self.close()
         except Exception:
             pass
+
+
+def rank1_sweep(q, K, rowptr=None, colidx=None, stream=None):
+    """Exact rank-1 optimum (and, with a graph, the best-cut state of the sweep)."""
+    dev = q.device
+    n = q.numel()
+    ws = workspace(lrq_rank1_workspace_size(n), dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    z = torch.empty(n, dtype=torch.uint8, device=dev)
+    f = torch.empty(1, dtype=torch.float64, device=dev)
+    cut = torch.zeros(1, dtype=torch.int64, device=dev) if rowptr is not None else None
+    zc = torch.empty(n, dtype=torch.uint8, device=dev) if rowptr is not None else None
+    lrq_rank1_sweep(q, K, z, f, rowptr, colidx, cut, zc, ws, st, stream)
+    return dict(z=z, f=f, cut=cut, zcut=zc, dev_status=st)

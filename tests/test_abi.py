@@ -161,3 +161,21 @@ def test_batched_plan_rejects_bad_problems_on_host(lib):
     assert lib.lrq_batched_plan_create(None, 1, 1, ctypes.byref(ctypes.c_void_p())) == 1
     assert lib.lrq_graph_launch(None, None) == 1
     assert lib.lrq_sample_score_batched(None, P(256), 1, P(512), P(1024), P(2048), None) == 1
+
+
+def test_rank1_rejects_bad_arguments_on_host(lib):
+    P = ctypes.c_void_p
+    args = dict(q=P(256), n=100, K=3, z=P(512), f=P(1024), rp=None, ci=None, nnz=0, cut=None, zc=None, ws=P(4096),
+                wsb=1 << 30, st=P(8192))
+
+    def call(**kw):
+        a = dict(args)
+        a.update(kw)
+        return lib.lrq_rank1_sweep(a["q"], a["n"], a["K"], a["z"], a["f"], a["rp"], a["ci"], a["nnz"], a["cut"],
+                                   a["zc"], a["ws"], a["wsb"], a["st"], None)
+    assert call(n=0) == 1
+    assert call(K=1) == 1
+    assert call(K=65) == 1
+    assert call(q=None) == 1
+    assert call(rp=P(300)) == 1          # graph without colidx / outputs
+    assert call(wsb=8) == 6

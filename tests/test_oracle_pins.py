@@ -411,3 +411,30 @@ def test_weighted_laplacian_quadratic_form_and_self_loops():
     _, lam_b = O.truncate_laplacian(rp2, ci2, 3, weights=w2)
     assert np.allclose(lam_a, lam_b, atol=1e-10)
     assert np.allclose(lam_a, np.sort(np.linalg.eigvalsh(L))[::-1][:3], atol=1e-10)
+
+
+# ----------------------------------------------------------------------------
+# The rank-1 sweep scored on a graph's cut
+# ----------------------------------------------------------------------------
+def test_rank1_sweep_cut_invariants():
+    rowptr, colidx, _ = I.sbm_graph(400, 4.0, 8.0, seed=3)
+    q = I.complex_gaussian((400,), seed=4)
+    for K in (2, 3, 5):
+        best, z, cuts = O.rank1_sweep_cut(q, K, rowptr, colidx)
+        assert cuts[0] == cuts[-1]  # the last state is the first rotated by omega
+        assert best == cuts.max() and O.cut_count(rowptr, colidx, z) == best
+        # the rank-1 optimum (Algorithm 1) is one of the states
+        _, z1 = O.rank1_sweep(q, K)
+        assert best >= O.cut_count(rowptr, colidx, z1)
+
+
+def test_rank1_sweep_cut_bipartite_closed_form():
+    # even torus, K = 2, q = the checkerboard (top Laplacian eigenvector):
+    # some state cuts every edge
+    k1, k2 = 8, 10
+    rowptr, colidx = I.torus_graph(k1, k2)
+    a = np.arange(k1)[:, None]
+    b = np.arange(k2)[None, :]
+    q = ((a + b) % 2 * 2 - 1).ravel().astype(np.complex128)
+    best, z, _ = O.rank1_sweep_cut(q, 2, rowptr, colidx)
+    assert best == len(colidx) // 2
