@@ -539,7 +539,10 @@ def run_batched(args):
     plan.close()
 
 
-def run_rank1(args):
+def run_rank1(args, hybrid=False):
+    """Rank-1 Max-3-Cut at n = 10^6: rank-2 truncation, the two-eigenvector
+    rounding vector, the exact sweep with every state's cut; with hybrid,
+    greedy local search from the sweep's best-cut state."""
     import torch
 
     from paper_2602_20376_gb300 import inputs, lrq
@@ -552,39 +555,54 @@ def run_rank1(args):
     ci = torch.from_numpy(colidx).to(dev)
     Q = lrq.laplacian_matrix(rp, ci)
 
-    def step():
-        tr = lrq.truncate(Q, 1, max_iter=1000, seed=0, want_c64=False)
-        out = lrq.rank1_sweep(tr["V"][:, 0].contiguous(), 3, rp, ci)
-        return tr, out
+    def step(ev=None):
+        if ev:
+            ev[0].record()
+        tr = lrq.truncate(Q, 2, max_iter=1000, seed=0, want_c64=False)
+        if ev:
+            ev[1].record()
+        q = lrq.two_eigvec_q(tr["V"], tr["lam"])
+        out = lrq.rank1_sweep(q, 3, rp, ci)
+        if ev:
+            ev[2].record()
+        gr = lrq.greedy_cut(rp, ci, 3, out["zcut"]) if hybrid else None
+        if ev:
+            ev[3].record()
+        return tr, out, gr
 
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
-    a, b = _events(torch, args.steps), _events(torch, args.steps)
-    sa, sb = _events(torch, args.steps), _events(torch, args.steps)
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(args.steps)]
     l0 = lrq.lrq_kernel_launches()
     with ClockSampler(0) as clk:
         for i in range(args.steps):
-            a[i].record()
-            tr = lrq.truncate(Q, 1, max_iter=1000, seed=0, want_c64=False)
-            sa[i].record()
-            out = lrq.rank1_sweep(tr["V"][:, 0].contiguous(), 3, rp, ci)
-            sb[i].record()
-            b[i].record()
+            tr, out, gr = step(evs[i])
         torch.cuda.synchronize()
-    ms = sum(x.elapsed_time(y) for x, y in zip(a, b)) / args.steps
-    sweep_ms = sum(x.elapsed_time(y) for x, y in zip(sa, sb)) / args.steps
+    phase = lambda a, b: sum(e[a].elapsed_time(e[b]) for e in evs) / args.steps
+    ms, trunc_ms, sweep_ms = phase(0, 3), phase(0, 1), phase(1, 2)
     edges = int(rowptr[-1]) // 2
-    _line("rank-1 Max-3-Cut solves/s (SBM n=10^6: truncation + exact sweep + best cut along it)", 1e3 / ms,
-          "solves/s", args, ms,
-          {"workload": "planted 3-partition SBM n=10^6, p_in n=4, p_out n=8 (seed 1); rank-1 FP64 Lanczos "
-                       "truncation of L, exact rank-1 sweep (K=3), every sweep state's exact cut", "edges": edges},
+    cut = int(out["cut"].item())
+    info = {"f": float(out["f"].item()), "best_cut_along_sweep": cut, "edges": edges, "cut_fraction": cut / edges,
+            "lambda": [float(x) for x in tr["lam"].cpu()], "truncate_ms": trunc_ms, "sweep_ms": sweep_ms,
+            "lanczos_steps": tr["iters"],
+            "paper_context": "the paper's rank-1 solver (ARPACK eigensolve + sweep with incremental scoring) takes "
+                             "about 70 min on one CPU at n = 10^6 on a 5-regular graph (App., rank-1 at scale)"}
+    what = "rank-2 FP64 Lanczos truncation of L, two-eigenvector rounding vector q = u1 + i u2, exact rank-1 " \
+           "sweep (K=3), every sweep state's exact cut"
+    if hybrid:
+        hc = int(gr["cut"].item())
+        info.update(hybrid_cut=hc, hybrid_cut_fraction=hc / edges, greedy_ms=phase(2, 3), greedy_rounds=gr["rounds"],
+                    greedy_moves=gr["moves"], greedy_converged=gr["converged"])
+        metric = "hybrid Max-3-Cut solves/s (SBM n=10^6: truncation + rank-1 sweep + greedy from its best cut)"
+        what += ", then greedy local search to a local optimum"
+    else:
+        metric = "rank-1 Max-3-Cut solves/s (SBM n=10^6: truncation + exact sweep + best cut along it)"
+    _line(metric, 1e3 / ms, "solves/s", args, ms,
+          {"workload": "planted 3-partition SBM n=10^6, p_in n=4, p_out n=8 (seed 1); " + what, "edges": edges},
           dtype="f64", gpu_launches=int(lrq.lrq_kernel_launches() - l0), clocks=clk.summary(),
-          rank1={"f": float(out["f"].item()), "best_cut_along_sweep": int(out["cut"].item()), "edges": edges,
-                 "cut_fraction": int(out["cut"].item()) / edges, "lambda1": float(tr["lam"][0].item()),
-                 "sweep_ms": sweep_ms, "truncate_ms": ms - sweep_ms, "lanczos_steps": tr["iters"],
-                 "paper_context": "the paper's rank-1 hybrid (ARPACK eigensolve + sweep + greedy) takes about 70 min "
-                                  "on one CPU at n = 10^6 on a 5-regular graph (App., rank-1 at scale)"})
+          **{"hybrid" if hybrid else "rank1": info})
+
 
 def main():
     ap = argparse.ArgumentParser()
@@ -600,7 +618,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per launch of the scoring kernel from an ncu capture")
-    ap.add_argument("--workload", choices=["scale", "exact", "maxcut", "batched", "learned", "rank1"],
+    ap.add_argument("--workload", choices=["scale", "exact", "maxcut", "batched", "learned", "rank1", "hybrid"],
                     default="scale")
     ap.add_argument("--no-learned", action="store_true", help="leave samples_to_best out of the default line")
     ap.add_argument("--learned-n", type=int, default=4096)
@@ -614,7 +632,7 @@ def main():
         run_ours(args)
     else:
         {"exact": run_exact, "maxcut": run_maxcut, "batched": run_batched, "learned": run_learned,
-         "rank1": run_rank1}[args.workload](args)
+         "rank1": run_rank1, "hybrid": lambda a: run_rank1(a, hybrid=True)}[args.workload](args)
 
 
 if __name__ == "__main__":

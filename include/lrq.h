@@ -322,6 +322,26 @@ int lrq_rank1_sweep(const void* q, int64_t n, int K, uint8_t* z_out, double* f_o
                     size_t ws_bytes, int32_t* dev_status, void* stream);
 
 /* --------------------------------------------------------------------------
+ * lrq_two_eigvec_q -- the rank-1 input of two-eigenvector complex rounding
+ * (App. "Two-Eigenvector Complex Rounding", Eq. 12).
+ *
+ * A real symmetric Q (a graph Laplacian) has real eigenvectors, whose phases
+ * are 0 or pi: a rank-1 sweep on one of them reaches only two of the K = 3
+ * sectors.  The fix combines the top two, q_i = u_1(i) + i u_2(i), so that
+ * arg(q_i) covers the whole circle.
+ *
+ *   V      : n x r complex128, row-major (device), r >= 2: the V of
+ *            lrq_truncate, columns sqrt(lambda_j) u_j with u_j real (the
+ *            CSR Laplacian path computes in real arithmetic); only the real
+ *            parts of columns 0 and 1 are read.
+ *   lambda : r doubles (device), the eigenvalues lrq_truncate returned;
+ *            u_j = V_j / sqrt(lambda_j), and a column with lambda_j <= 0
+ *            contributes 0.
+ *   q_out  : n complex128 (device), written; the q of lrq_rank1_sweep.
+ * ------------------------------------------------------------------------ */
+int lrq_two_eigvec_q(const void* V, int64_t n, int r, const double* lambda, void* q_out, void* stream);
+
+/* --------------------------------------------------------------------------
  * lrq_enumerate -- exact maximiser for rank r by vertex enumeration.
  *
  * Sec. 3, Algorithm 2 (with Theorem 3.2: for Q = V V^H of rank r the
@@ -424,6 +444,42 @@ int lrq_adam_step(float* params, const float* grads, float* m, float* v, int64_t
  * ------------------------------------------------------------------------ */
 int lrq_cut_count(const int32_t* rowptr, const int32_t* colidx, int64_t n, const uint8_t* z,
                   int64_t* cut_out, void* stream);
+
+/* --------------------------------------------------------------------------
+ * lrq_greedy_cut -- greedy local search for Max-K-Cut, in place (the
+ * refinement step of the hybrid solver, App. "Hybrid Warm-Start": greedy
+ * hill-climbing started from the rank-1 partition, e.g. zcut_out of
+ * lrq_rank1_sweep).
+ *
+ * Vertex i with neighbour counts n_i(c) = #{j in N(i), j != i : k_j = c}
+ * gains g_i = n_i(k_i) - min_{c != k_i} n_i(c) by moving to that label (ties
+ * to the smallest label).  Every round moves, simultaneously, each vertex
+ * with g_i > 0 that no neighbour with positive gain outranks in the order
+ * (larger gain, then smaller index).  The moved vertices are pairwise
+ * non-adjacent, so the cut rises by exactly the sum of their gains, and the
+ * steepest single move is always among them.  Rounds repeat until one moves
+ * nothing (a state no single move improves) or max_rounds have run.  The
+ * result is deterministic.
+ *
+ *   rowptr, colidx, nnz : undirected graph, symmetric CSR int32 (device),
+ *              each edge in both rows, self loops ignored, parallel edges
+ *              counted with their multiplicity.
+ *   z        : n uint8 labels in [0, K) (device), read and overwritten.
+ *   max_rounds : >= 0.
+ *   cut_out  : 1 int64 (device) receives the final cut, or NULL.
+ *   rounds_out, moves_out : host int64, rounds that moved and vertices
+ *              moved in total, or NULL.  converged_out : host int32, 1 when
+ *              a round found no move, 0 when max_rounds stopped the search
+ *              first, or NULL.
+ *   ws       : lrq_greedy_workspace_size(n) bytes.
+ * Limits: 1 <= n < 2^31, 2 <= K <= 8.  Synchronises `stream` once per 8
+ * rounds.  A label >= K, a column index outside [0, n) or a row range
+ * outside [0, nnz] -> LRQ_EINVAL (returned; *dev_status holds it too).
+ * ------------------------------------------------------------------------ */
+int lrq_greedy_workspace_size(int64_t n, size_t* bytes);
+int lrq_greedy_cut(const int32_t* rowptr, const int32_t* colidx, int64_t n, int64_t nnz, int K, uint8_t* z,
+                   int64_t max_rounds, int64_t* cut_out, int64_t* rounds_out, int64_t* moves_out,
+                   int32_t* converged_out, void* ws, size_t ws_bytes, int32_t* dev_status, void* stream);
 
 /* --------------------------------------------------------------------------
  * Measurement hooks (no counterpart in the paper).

@@ -17,6 +17,10 @@ Pieces and the passages they follow:
   arrangement (Sec. 3, Algorithm 2, with the augmented matrix of Eq. 6), in
   the superset reading described in its docstring; SVD is the library step
   that yields each null vector.
+* ``rank1_sweep_states`` / ``rank1_sweep_cut`` (numpy): the n + 1 states of
+  the rank-1 sweep and their exact cuts; ``greedy_cut`` (numpy): greedy
+  local search on the cut from a given partition (the hybrid warm start,
+  App. "Hybrid Warm-Start"), in the round reading given in its docstring.
 * ``truncate_dense`` / ``truncate_laplacian``: spectral truncation
   (Sec. 4.1, Algorithm 3) through LAPACK ``eigh`` and ARPACK ``eigsh``
   (the paper's own eigen-solver, Sec. 5).
@@ -263,6 +267,15 @@ def rank1_sweep_states(q, K: int):
     return (np.mod(fl, K)).astype(np.uint8), order
 
 
+def two_eigvec_q(V, lam):
+    """Two-eigenvector complex rounding (App. "Two-Eigenvector Complex
+    Rounding", Eq. 12): q = u_1 + i u_2 with u_j the real unit eigenvectors,
+    here recovered from V = [sqrt(lambda_j) u_j] (0 where lambda_j <= 0)."""
+    V = np.asarray(V)
+    u = [V[:, j].real / np.sqrt(lam[j]) if lam[j] > 0 else np.zeros(V.shape[0]) for j in (0, 1)]
+    return u[0] + 1j * u[1]
+
+
 def rank1_sweep_cut(q, K: int, rowptr, colidx):
     """Every state of the rank-1 sweep scored on the graph's exact cut
     (Max-K-Cut, Sec. 1); returns (best cut, its codes, all n + 1 cuts), ties
@@ -278,6 +291,53 @@ def rank1_sweep_cut(q, K: int, rowptr, colidx):
         if c > best:
             best, best_z = c, z.copy()
     return best, best_z, np.array(cuts)
+
+
+# --------------------------------------------------------------------------
+# Greedy local search for Max-K-Cut (hybrid warm start, App. "Hybrid
+# Warm-Start")
+# --------------------------------------------------------------------------
+def greedy_cut(rowptr, colidx, K: int, z, max_rounds=None):
+    """Greedy hill-climbing on the exact cut from labels z (Sec. 1 objective;
+    the hybrid solver runs it from the rank-1 partition).
+
+    Reading of "steepest ascent" for a data-parallel round: with neighbour
+    counts n_i(c) (self loops ignored, parallel edges with multiplicity),
+    vertex i gains g_i = n_i(z_i) - min_{c != z_i} n_i(c) by moving to the
+    smallest label attaining that minimum.  A round moves every vertex with
+    g_i > 0 that has no neighbour j with g_j > g_i, or g_j = g_i and j < i.
+    Rounds repeat until one moves nothing or max_rounds have run.
+    Returns (labels uint8, rounds that moved, vertices moved, converged)."""
+    rowptr = np.asarray(rowptr, dtype=np.int64)
+    colidx = np.asarray(colidx, dtype=np.int64)
+    n = len(rowptr) - 1
+    rows = np.repeat(np.arange(n), np.diff(rowptr))
+    keep = colidx != rows
+    src, dst = rows[keep], colidx[keep]
+    z = np.asarray(z, dtype=np.int64).copy()
+    ar = np.arange(n)
+    rounds = moves = ran = 0
+    converged = False
+    while max_rounds is None or ran < max_rounds:
+        ran += 1
+        cnt = np.zeros((n, K), dtype=np.int64)
+        np.add.at(cnt, (src, z[dst]), 1)
+        same = cnt[ar, z]
+        other = cnt.copy()
+        other[ar, z] = np.iinfo(np.int64).max
+        best = np.argmin(other, axis=1)          # first minimum: smallest label
+        gain = np.maximum(same - other[ar, best], 0)
+        gi, gj = gain[src], gain[dst]
+        outranked = (gj > gi) | ((gj == gi) & (dst < src))
+        blocked = np.bincount(src, weights=outranked, minlength=n) > 0
+        mv = (gain > 0) & ~blocked
+        if not mv.any():
+            converged = True
+            break
+        z[mv] = best[mv]
+        rounds += 1
+        moves += int(mv.sum())
+    return z.astype(np.uint8), rounds, moves, converged
 
 
 # --------------------------------------------------------------------------

@@ -414,6 +414,25 @@ void r1_scan(T* x, int64_t n, T* sums, int64_t nb, cudaStream_t st) {
 
 }  // namespace
 
+// two-eigenvector complex rounding vector (App. "Two-Eigenvector Complex
+// Rounding", Eq. 12): q_i = u_1(i) + i u_2(i) from the real eigenvectors of
+// a real symmetric Q, u_j = V_j / sqrt(lambda_j) (a column with
+// lambda_j <= 0 contributes 0)
+__global__ void r1_pair_kernel(const double2* __restrict__ V, int64_t n, int r, const double* __restrict__ lambda,
+                               double2* __restrict__ q) {
+  const int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double l0 = lambda[0], l1 = lambda[1];
+  const double s0 = l0 > 0.0 ? 1.0 / sqrt(l0) : 0.0, s1 = l1 > 0.0 ? 1.0 / sqrt(l1) : 0.0;
+  q[i] = make_double2(V[i * r].x * s0, V[i * r + 1].x * s1);
+}
+
+int launch_two_eigvec_q(const double2* V, int64_t n, int r, const double* lambda, double2* q, cudaStream_t st) {
+  r1_pair_kernel<<<static_cast<unsigned>(ceil_div(n, kR1Threads)), kR1Threads, 0, st>>>(V, n, r, lambda, q);
+  count_launch();
+  return cuda_check(cudaGetLastError(), "r1_pair_kernel");
+}
+
 size_t rank1_workspace_bytes(int64_t n) { return r1_layout(n).total; }
 
 int launch_rank1(const double2* q, int64_t n, int K, uint8_t* z_out, double* f_out, const int32_t* rowptr,

@@ -417,6 +417,34 @@ int lrq_rank1_sweep(const void* q, int64_t n, int K, uint8_t* z_out, double* f_o
                       ws, dev_status, static_cast<cudaStream_t>(stream));
 }
 
+int lrq_two_eigvec_q(const void* V, int64_t n, int r, const double* lambda, void* q_out, void* stream) {
+  if (n < 1 || n >= (int64_t(1) << 31)) return fail(LRQ_EINVAL, "n must be in [1, 2^31)");
+  if (r < 2) return fail(LRQ_EINVAL, "r must be >= 2");
+  if (!V || !lambda || !q_out) return fail(LRQ_EINVAL, "NULL pointer argument");
+  return launch_two_eigvec_q(static_cast<const double2*>(V), n, r, lambda, static_cast<double2*>(q_out),
+                             static_cast<cudaStream_t>(stream));
+}
+
+int lrq_greedy_workspace_size(int64_t n, size_t* bytes) {
+  if (!bytes) return fail(LRQ_EINVAL, "bytes is NULL");
+  if (n < 1 || n >= (int64_t(1) << 31)) return fail(LRQ_EINVAL, "n must be in [1, 2^31)");
+  *bytes = greedy_workspace_bytes(n);
+  return LRQ_OK;
+}
+
+int lrq_greedy_cut(const int32_t* rowptr, const int32_t* colidx, int64_t n, int64_t nnz, int K, uint8_t* z,
+                   int64_t max_rounds, int64_t* cut_out, int64_t* rounds_out, int64_t* moves_out,
+                   int32_t* converged_out, void* ws, size_t ws_bytes, int32_t* dev_status, void* stream) {
+  if (n < 1 || n >= (int64_t(1) << 31)) return fail(LRQ_EINVAL, "n must be in [1, 2^31)");
+  if (K < 2 || K > 8) return fail(LRQ_EINVAL, "K must be in [2, 8]");
+  if (nnz < 0 || max_rounds < 0) return fail(LRQ_EINVAL, "nnz and max_rounds must be >= 0");
+  if (!rowptr || (nnz > 0 && !colidx) || !z || !dev_status) return fail(LRQ_EINVAL, "NULL pointer argument");
+  int e = check_ws(ws, ws_bytes, greedy_workspace_bytes(n));
+  if (e) return e;
+  return launch_greedy(rowptr, colidx, n, nnz, K, z, max_rounds, cut_out, rounds_out, moves_out, converged_out, ws,
+                       dev_status, static_cast<cudaStream_t>(stream));
+}
+
 int lrq_enumerate_workspace_size(int64_t n, int r, int K, size_t* bytes) {
   if (!bytes) return fail(LRQ_EINVAL, "bytes is NULL");
   int e = enumerate_check(n, r, K, 1e300);

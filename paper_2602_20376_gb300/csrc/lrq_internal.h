@@ -128,6 +128,12 @@ size_t rank1_workspace_bytes(int64_t n);
 int launch_rank1(const double2* q, int64_t n, int K, uint8_t* z_out, double* f_out, const int32_t* rowptr,
                  const int32_t* colidx, int64_t nnz, int64_t* cut_out, uint8_t* zcut_out, void* ws, int32_t* status,
                  cudaStream_t st);
+int launch_two_eigvec_q(const double2* V, int64_t n, int r, const double* lambda, double2* q, cudaStream_t st);
+// greedy local search (Max-K-Cut)
+size_t greedy_workspace_bytes(int64_t n);
+int launch_greedy(const int32_t* rowptr, const int32_t* colidx, int64_t n, int64_t nnz, int K, uint8_t* z,
+                  int64_t max_rounds, int64_t* cut_out, int64_t* rounds_out, int64_t* moves_out,
+                  int32_t* converged_out, void* ws, int32_t* status, cudaStream_t st);
 // vertex enumeration (FP64)
 int enumerate_check(int64_t n, int r, int K, double budget);
 size_t enum_workspace_bytes(int64_t n, int r);

@@ -147,6 +147,12 @@ def load() -> ctypes.CDLL:
         lib.lrq_rank1_workspace_size.restype = I
         lib.lrq_rank1_sweep.argtypes = [P, I64, I, P, P, P, P, I64, P, P, P, SZ, P, P]
         lib.lrq_rank1_sweep.restype = I
+        lib.lrq_two_eigvec_q.argtypes = [P, I64, I, P, P, P]
+        lib.lrq_two_eigvec_q.restype = I
+        lib.lrq_greedy_workspace_size.argtypes = [I64, ctypes.POINTER(SZ)]
+        lib.lrq_greedy_workspace_size.restype = I
+        lib.lrq_greedy_cut.argtypes = [P, P, I64, I64, I, P, I64, P, P, P, P, P, SZ, P, P]
+        lib.lrq_greedy_cut.restype = I
         lib.lrq_enumerate_workspace_size.argtypes = [I64, I, I, ctypes.POINTER(SZ)]
         lib.lrq_enumerate_workspace_size.restype = I
         lib.lrq_enumerate.argtypes = [P, I64, I, I, ctypes.c_double, P, P, P, P, SZ, P, P]
@@ -166,7 +172,8 @@ def exported_symbols():
     return ["lrq_status_string", "lrq_last_error", "lrq_abi_version", "lrq_sample_directions",
             "lrq_sample_score_workspace_size", "lrq_sample_score", "lrq_rescore_workspace_size",
             "lrq_rescore", "lrq_rescore_no_alloc", "lrq_truncate_workspace_size", "lrq_truncate",
-            "lrq_rank1_workspace_size", "lrq_rank1_sweep", "lrq_enumerate_workspace_size", "lrq_enumerate", "lrq_batched_plan_create", "lrq_batched_plan_destroy",
+            "lrq_rank1_workspace_size", "lrq_rank1_sweep", "lrq_two_eigvec_q", "lrq_greedy_workspace_size", "lrq_greedy_cut",
+            "lrq_enumerate_workspace_size", "lrq_enumerate", "lrq_batched_plan_create", "lrq_batched_plan_destroy",
             "lrq_batched_workspace_size", "lrq_batched_prepare", "lrq_batched_autotune", "lrq_batched_tile",
             "lrq_sample_score_batched", "lrq_batched_graph_create", "lrq_graph_launch", "lrq_graph_destroy",
             "lrq_proposal_num_features", "lrq_proposal_num_params", "lrq_proposal_features", "lrq_mlp_forward",
@@ -342,6 +349,38 @@ def lrq_rank1_sweep(q, K, z_out, f_out, rowptr, colidx, cut_out, zcut_out, ws, d
     _check(load().lrq_rank1_sweep(_ptr(q), n, int(K), _ptr(z_out), _ptr(f_out), _ptr(rowptr), _ptr(colidx), nnz,
                                   _ptr(cut_out), _ptr(zcut_out), _ptr(ws), ws.numel() * ws.element_size(),
                                   _ptr(dev_status), _stream(stream)), "lrq_rank1_sweep")
+
+
+def lrq_two_eigvec_q(V, lam, q_out, stream=None):
+    """V: n x r complex128 (device, r >= 2); lam: r float64 (device)."""
+    n, r = V.shape
+    _check(load().lrq_two_eigvec_q(_ptr(V), n, r, _ptr(lam), _ptr(q_out), _stream(stream)), "lrq_two_eigvec_q")
+
+
+def two_eigvec_q(V, lam, stream=None):
+    """q = u_1 + i u_2 from a real truncation (two-eigenvector rounding)."""
+    q = torch.empty(V.shape[0], dtype=torch.complex128, device=V.device)
+    lrq_two_eigvec_q(V, lam, q, stream)
+    return q
+
+
+def lrq_greedy_workspace_size(n: int) -> int:
+    out = ctypes.c_size_t(0)
+    _check(load().lrq_greedy_workspace_size(int(n), ctypes.byref(out)), "lrq_greedy_workspace_size")
+    return int(out.value)
+
+
+def lrq_greedy_cut(rowptr, colidx, K, z, max_rounds, cut_out, ws, dev_status, stream=None):
+    """rowptr/colidx: int32 CSR (device); z: n uint8 labels (device), refined
+    in place.  Returns (rounds that moved, vertices moved, converged)."""
+    n = z.numel()
+    nnz = colidx.numel()
+    rounds, moves, conv = ctypes.c_int64(0), ctypes.c_int64(0), ctypes.c_int32(0)
+    _check(load().lrq_greedy_cut(_ptr(rowptr), _ptr(colidx), n, nnz, int(K), _ptr(z), int(max_rounds),
+                                 _ptr(cut_out), ctypes.byref(rounds), ctypes.byref(moves), ctypes.byref(conv),
+                                 _ptr(ws), ws.numel() * ws.element_size(), _ptr(dev_status), _stream(stream)),
+           "lrq_greedy_cut")
+    return int(rounds.value), int(moves.value), bool(conv.value)
 
 
 def lrq_enumerate_workspace_size(n: int, r: int, K: int) -> int:
@@ -541,3 +580,16 @@ def rank1_sweep(q, K, rowptr=None, colidx=None, stream=None):
     zc = torch.empty(n, dtype=torch.uint8, device=dev) if rowptr is not None else None
     lrq_rank1_sweep(q, K, z, f, rowptr, colidx, cut, zc, ws, st, stream)
     return dict(z=z, f=f, cut=cut, zcut=zc, dev_status=st)
+
+
+def greedy_cut(rowptr, colidx, K, z, max_rounds=1 << 20, stream=None):
+    """Greedy Max-K-Cut local search from the labels z (left untouched; the
+    refined labels are returned): the hybrid solver's second step when z is
+    the rank-1 sweep's best-cut state."""
+    dev = z.device
+    zz = z.clone()
+    ws = workspace(lrq_greedy_workspace_size(zz.numel()), dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    cut = torch.zeros(1, dtype=torch.int64, device=dev)
+    rounds, moves, conv = lrq_greedy_cut(rowptr, colidx, K, zz, max_rounds, cut, ws, st, stream)
+    return dict(z=zz, cut=cut, rounds=rounds, moves=moves, converged=conv, dev_status=st)

@@ -179,3 +179,26 @@ def test_rank1_rejects_bad_arguments_on_host(lib):
     assert call(q=None) == 1
     assert call(rp=P(300)) == 1          # graph without colidx / outputs
     assert call(wsb=8) == 6
+
+
+def test_greedy_rejects_bad_arguments_on_host(lib):
+    P = ctypes.c_void_p
+    args = dict(rp=P(256), ci=P(512), n=100, nnz=400, K=3, z=P(1024), mr=10, cut=None, ws=P(4096), wsb=1 << 30,
+                st=P(8192))
+
+    def call(**kw):
+        a = dict(args)
+        a.update(kw)
+        return lib.lrq_greedy_cut(a["rp"], a["ci"], a["n"], a["nnz"], a["K"], a["z"], a["mr"], a["cut"], None,
+                                  None, None, a["ws"], a["wsb"], a["st"], None)
+    assert call(n=0) == 1
+    assert call(K=1) == 1
+    assert call(K=9) == 1
+    assert call(nnz=-1) == 1
+    assert call(mr=-1) == 1
+    assert call(z=None) == 1
+    assert call(ci=None) == 1
+    assert call(wsb=8) == 6
+    need = ctypes.c_size_t(0)
+    assert lib.lrq_greedy_workspace_size(100, ctypes.byref(need)) == 0 and need.value >= 500
+    assert lib.lrq_greedy_workspace_size(0, ctypes.byref(need)) == 1

@@ -109,3 +109,34 @@ def test_sbm_million_rank1_path(lrq):
     assert int(out["cut"].item()) >= oracle.cut_count(rowptr, colidx, z)
     qh = q.cpu().numpy()
     assert abs(oracle.objective(qh[:, None], 3, z) - float(out["f"].item())) <= 1e-9 * float(out["f"].item())
+
+
+def test_two_eigvec_q_matches_oracle(lrq):
+    # q = u_1 + i u_2 from the GPU truncation's V and lambda, against the
+    # oracle's formula on the same inputs (one FP64 division per entry)
+    n = 5001
+    V = I.complex_gaussian((n, 3), seed=40)
+    for lam in ([4.0, 2.5, 1.0], [3.0, -1.0, 0.5], [7.0, 0.0, 0.0]):
+        Vd = torch.from_numpy(V).to(DEV)
+        ld = torch.tensor(lam, dtype=torch.float64, device=DEV)
+        q = lrq.two_eigvec_q(Vd, ld).cpu().numpy()
+        q_ref = oracle.two_eigvec_q(V, np.array(lam))
+        assert np.abs(q - q_ref).max() <= 1e-15 * np.abs(q_ref).max()
+
+
+def test_two_eigvec_sweep_on_gpu_truncation(lrq):
+    # the whole rank-1 path for K = 3 on a graph: GPU rank-2 truncation, q,
+    # sweep with every state's cut; against the oracle's sweep on the same q
+    rowptr, colidx, _ = I.sbm_graph(20000, 4.0, 8.0, seed=41)
+    rp = torch.from_numpy(np.asarray(rowptr, np.int32)).to(DEV)
+    ci = torch.from_numpy(np.asarray(colidx, np.int32)).to(DEV)
+    tr = lrq.truncate(lrq.laplacian_matrix(rp, ci), 2, want_c64=False)
+    q = lrq.two_eigvec_q(tr["V"], tr["lam"])
+    out = lrq.rank1_sweep(q, 3, rp, ci)
+    torch.cuda.synchronize()
+    assert int(out["dev_status"].item()) == 0
+    qh = q.cpu().numpy()
+    f_ref, _ = oracle.rank1_sweep(qh, 3)
+    assert abs(float(out["f"].item()) - f_ref) <= 1e-9 * f_ref
+    assert set(np.unique(out["zcut"].cpu().numpy())) == {0, 1, 2}
+    assert int(out["cut"].item()) == oracle.cut_count(rowptr, colidx, out["zcut"].cpu().numpy())

@@ -438,3 +438,108 @@ def test_rank1_sweep_cut_bipartite_closed_form():
     q = ((a + b) % 2 * 2 - 1).ravel().astype(np.complex128)
     best, z, _ = O.rank1_sweep_cut(q, 2, rowptr, colidx)
     assert best == len(colidx) // 2
+
+
+# ----------------------------------------------------------------------------
+# Greedy local search on the cut (hybrid warm start)
+# ----------------------------------------------------------------------------
+def _cycle(n):
+    src = np.arange(n)
+    dst = (src + 1) % n
+    s = np.concatenate([src, dst])
+    d = np.concatenate([dst, src])
+    order = np.lexsort((d, s))
+    rowptr = np.concatenate([[0], np.cumsum(np.bincount(s, minlength=n))])
+    return rowptr.astype(np.int32), d[order].astype(np.int32)
+
+
+def _single_moves(rowptr, colidx, K, z):
+    """Brute force: the cut change of every single relabelling."""
+    base = O.cut_count(rowptr, colidx, z)
+    n = len(z)
+    d = np.zeros((n, K), dtype=np.int64)
+    for i in range(n):
+        for c in range(K):
+            zz = z.copy()
+            zz[i] = c
+            d[i, c] = O.cut_count(rowptr, colidx, zz) - base
+    return d
+
+
+def test_greedy_cycle_closed_form():
+    # even cycle, all labels 0, K = 2: every round only the lowest-indexed
+    # gaining vertex of each run moves, i.e. vertices 0, 2, 4, ... one per
+    # round; the end is the alternating colouring cutting every edge
+    n = 40
+    rowptr, colidx = _cycle(n)
+    z, rounds, moves, conv = O.greedy_cut(rowptr, colidx, 2, np.zeros(n, np.uint8))
+    assert conv and rounds == n // 2 and moves == n // 2
+    assert np.array_equal(z, (np.arange(n) % 2 == 0).astype(np.uint8))
+    assert O.cut_count(rowptr, colidx, z) == n
+
+
+@pytest.mark.parametrize("K,seed", [(2, 1), (3, 2), (4, 3), (5, 4)])
+def test_greedy_round_against_brute_force(K, seed):
+    # one round: every moved vertex takes its best single move (largest cut
+    # gain, smallest label on ties), the moved vertices are pairwise
+    # non-adjacent, the cut rises by the sum of their gains, and the steepest
+    # single move (smallest index on ties) is among them
+    rowptr, colidx, _ = I.sbm_graph(60, 3.0, 5.0, seed=seed)
+    z0 = I.rng(seed).integers(0, K, 60).astype(np.uint8)
+    d = _single_moves(rowptr, colidx, K, z0)
+    z1, rounds, moves, _ = O.greedy_cut(rowptr, colidx, K, z0, max_rounds=1)
+    mv = np.nonzero(z1 != z0)[0]
+    assert rounds == 1 and moves == len(mv) > 0
+    for i in mv:
+        assert d[i, z1[i]] == d[i].max() > 0
+        assert z1[i] == np.argmax(d[i])
+        nb = colidx[rowptr[i]:rowptr[i + 1]]
+        assert not np.isin(nb[nb != i], mv).any()
+    assert O.cut_count(rowptr, colidx, z1) - O.cut_count(rowptr, colidx, z0) == d[mv].max(axis=1).sum()
+    gmax = d.max(axis=1)
+    assert np.argmax(gmax) in mv
+
+
+def test_greedy_ends_in_local_optimum_and_rounds_raise_the_cut():
+    rowptr, colidx, _ = I.sbm_graph(80, 3.0, 6.0, seed=7)
+    K = 3
+    z0 = np.zeros(80, np.uint8)
+    z, rounds, moves, conv = O.greedy_cut(rowptr, colidx, K, z0)
+    assert conv and rounds > 1
+    assert _single_moves(rowptr, colidx, K, z).max() <= 0
+    cuts = [O.cut_count(rowptr, colidx, O.greedy_cut(rowptr, colidx, K, z0, max_rounds=t)[0])
+            for t in range(rounds + 1)]
+    assert np.all(np.diff(cuts) > 0) and cuts[-1] == O.cut_count(rowptr, colidx, z)
+    # a limit that stops the search early is reported
+    _, r2, _, conv2 = O.greedy_cut(rowptr, colidx, K, z0, max_rounds=1)
+    assert r2 == 1 and not conv2
+
+
+def test_greedy_self_loops_and_parallel_edges():
+    # vertices 0-1 joined twice, a self loop on 0: the double edge counts twice,
+    # the loop never
+    rowptr = np.array([0, 3, 5], np.int32)
+    colidx = np.array([0, 1, 1, 0, 0], np.int32)
+    z, rounds, moves, conv = O.greedy_cut(rowptr, colidx, 2, np.zeros(2, np.uint8))
+    assert conv and rounds == 1 and moves == 1
+    assert list(z) == [1, 0] and O.cut_count(rowptr, colidx, z) == 2
+
+
+def test_two_eigvec_q_is_a_pair_of_unit_eigenvectors():
+    # App. "Two-Eigenvector Complex Rounding": Re q and Im q are the top two
+    # unit eigenvectors of the Laplacian, and arg q reaches all three
+    # sectors for K = 3 where one real eigenvector reaches two
+    rowptr, colidx, _ = I.sbm_graph(300, 4.0, 8.0, seed=11)
+    L = O.laplacian_dense(rowptr, colidx).real
+    V, lam = O.truncate_laplacian(rowptr, colidx, 2)
+    q = O.two_eigvec_q(V, lam)
+    for u, l in ((q.real, lam[0]), (q.imag, lam[1])):
+        assert abs(np.linalg.norm(u) - 1) < 1e-10
+        assert np.linalg.norm(L @ u - l * u) < 1e-8 * l
+    assert abs(np.dot(q.real, q.imag)) < 1e-10
+    codes = lambda x: set(np.mod(np.floor(3 * np.angle(x) / (2 * np.pi)), 3).astype(int))
+    assert codes(q) == {0, 1, 2}
+    assert len(codes(q.real + 0j)) <= 2
+    # a column with a non-positive eigenvalue contributes nothing
+    q0 = O.two_eigvec_q(V, np.array([lam[0], 0.0]))
+    assert np.array_equal(q0.imag, np.zeros(300))
