@@ -429,8 +429,17 @@ def run_maxcut(args):
     ws = lrq.workspace(lrq.lrq_sample_score_workspace_size(n, 3, 3, SS, lrq.LRQ_MODE_BF16_TC, m), dev)
     wsr = lrq.workspace(lrq.lrq_rescore_workspace_size(n, 3, m), dev)
 
+    null = args.sampler == "null"
+    Cn = torch.empty((SS, 3), dtype=torch.complex64, device=dev)
+    draws = torch.zeros(1, dtype=torch.int64, device=dev)
+    nst = torch.zeros(1, dtype=torch.int32, device=dev)
+
     def step(i):
-        out = lrq.sample_score(V, 3, C=None, S=SS, seed=1 + i, mode=lrq.LRQ_MODE_BF16_TC, top_m=m, ws=ws)
+        if null:  # the null-vector sampler (randomised Algorithm 2) in place of the uniform sphere
+            lrq.lrq_sample_null_directions(V, 3, 1 + i, SS, Cn, draws, nst)
+            out = lrq.sample_score(V, 3, C=Cn, mode=lrq.LRQ_MODE_BF16_TC, top_m=m, ws=ws)
+        else:
+            out = lrq.sample_score(V, 3, C=None, S=SS, seed=1 + i, mode=lrq.LRQ_MODE_BF16_TC, top_m=m, ws=ws)
         rs = lrq.rescore(V, 3, out["C"], out["top_idx"], want_z=True, ws=wsr)
         row = torch.nonzero(out["top_idx"] == rs["best"]).flatten()[0]  # z rows follow top_idx
         lrq.lrq_cut_count(rp, ci, rs["z"][row], cut)
@@ -449,14 +458,19 @@ def run_maxcut(args):
         torch.cuda.synchronize()
     ms = sum(x.elapsed_time(y) for x, y in zip(a, b)) / args.steps
     edges = int(rowptr[-1]) // 2
+    extra = {}
+    if null:
+        lrq.check_status(nst, "lrq_sample_null_directions")
+        extra = {"sampler": "null-vector", "draws_last_step": int(draws.item()),
+                 "rejected_fraction": 1.0 - SS / int(draws.item())}
     _line("Max-3-Cut candidate*n evals/s (SBM n=10^6, S=2^17, r=3)", SS * n / (ms * 1e-3), UNIT, args, ms,
           {"workload": "planted 3-partition SBM n=10^6, p_in n=4, p_out n=8 (seed 1), unit weights, CSR int32; "
-                       "rank-3 FP64 Lanczos truncation of L; S=2^17 BF16 candidates, top-64 FP64 rescore, exact "
-                       "cut of the winner", "edges": edges},
+                       "rank-3 FP64 Lanczos truncation of L; S=2^17 BF16 candidates (%s), top-64 FP64 rescore, exact "
+                       "cut of the winner" % ("null-vector sampler" if null else "uniform sphere"), "edges": edges},
           dtype="bf16", gpu_launches=int(lrq.lrq_kernel_launches() - l0), clocks=clk.summary(),
           maxcut={"cut": int(cut.item()), "planted_cut": planted_cut, "edges": edges,
                   "cut_fraction": int(cut.item()) / edges, "best_f": float(rs["best_f"].item()),
-                  "lambda": lam, "truncate_ms": trunc_ms, "lanczos_steps": tr["iters"]})
+                  "lambda": lam, "truncate_ms": trunc_ms, "lanczos_steps": tr["iters"], **extra})
 
 
 def run_batched(args):
@@ -620,6 +634,8 @@ def main():
                     help="DRAM bytes per launch of the scoring kernel from an ncu capture")
     ap.add_argument("--workload", choices=["scale", "exact", "maxcut", "batched", "learned", "rank1", "hybrid"],
                     default="scale")
+    ap.add_argument("--sampler", choices=["uniform", "null"], default="uniform",
+                    help="direction sampler of the maxcut workload")
     ap.add_argument("--no-learned", action="store_true", help="leave samples_to_best out of the default line")
     ap.add_argument("--learned-n", type=int, default=4096)
     ap.add_argument("--learned-train", type=int, default=128)

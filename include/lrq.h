@@ -89,6 +89,39 @@ int lrq_abi_version(void);
 int lrq_sample_directions(uint64_t seed, int64_t S, int r, void* C_out, void* stream);
 
 /* --------------------------------------------------------------------------
+ * lrq_sample_null_directions -- the null-vector sampler (Sec. 5, "The
+ * analyzed sampler matches the one used in practice"): the randomised form
+ * of Algorithm 2, the alternative to lrq_sample_directions.
+ *
+ * Each candidate is the null vector of 2r - 1 rows of the augmented real
+ * matrix (Eq. 6), drawn uniformly without replacement from its N = n B_K
+ * rows h_(i,m) = [Im(rho_m V_i), Re(rho_m V_i)], rho_m = exp(-i pi(2m+1)/K),
+ * numbered R = i B_K + m (B_K = K/2 for even K, K for odd K).  Rows that are
+ * linearly dependent (FP64 elimination with full pivoting: largest
+ * remaining pivot <= 1e-10 max|H|) give no unique direction: the draw is
+ * rejected and the slot draws again, up to 64 times.
+ *
+ * Draws: Philox4x32-10, key (lo32 seed, hi32 seed); row j of attempt a of
+ * slot s, try t, uses counter (lo32 s, hi32 s, (a << 8) | (j << 4) | t,
+ * 0x4E56) and row R = high 64 bits of ((w0 << 32) | w1) * N; a row already
+ * in the attempt is drawn again with the next t (up to 16).  The null vector
+ * is scaled to unit norm with its largest-magnitude entry positive (first
+ * on ties), negated when bit 0 of w2 of the attempt's first draw is set;
+ * c = c~[0:r] + i c~[r:2r], rounded to complex64.
+ *
+ *   V         : n x r complex64 (device), the scoring input.
+ *   C_out     : S x r complex64 (device), unit-norm rows; feed it to
+ *               lrq_sample_score with generate_C = 0.
+ *   draws_out : 1 int64 (device): subsets drawn in total (S / draws is the
+ *               acceptance rate).
+ * Limits: 1 <= r <= 8, 2 <= K <= 64, 1 <= S < 2^31, n B_K >= 2r - 1.  A
+ * slot with no accepted draw in 64 gets a zero row and *dev_status =
+ * LRQ_EUNSUPPORTED (e.g. V of rank below r).
+ * ------------------------------------------------------------------------ */
+int lrq_sample_null_directions(const void* V, int64_t n, int r, int K, uint64_t seed, int64_t S, void* C_out,
+                               int64_t* draws_out, int32_t* dev_status, void* stream);
+
+/* --------------------------------------------------------------------------
  * lrq_sample_score -- score S candidate directions and select the top m.
  *
  * For every direction c_s (Sec. 4.2, Eq. 10):
@@ -288,6 +321,32 @@ int lrq_truncate_workspace_size(const lrq_matrix* Q, int r, int max_iter, size_t
 int lrq_truncate(const lrq_matrix* Q, int r, double tol, int max_iter, uint64_t seed, void* V_out, void* V32_out,
                  double* lambda_out, int64_t* iters_out, void* ws, size_t ws_bytes, int32_t* dev_status,
                  void* stream);
+
+/* --------------------------------------------------------------------------
+ * lrq_spectral_energy -- the spectral energy ratio rho_r (Sec. 5, "When does
+ * low-rank work?"): the share of Q's spectral energy that its top r
+ * eigenvalues leave out, a cheap test of whether a rank-r truncation (and so
+ * this library's solvers) suits the instance.
+ *
+ *   rho_r = 1 - sum_{j<=r} max(lambda_j, 0) / trace(Q).
+ *
+ * For the PSD Q of the paper's problem (Sec. 1) trace(Q) is the sum of all
+ * eigenvalues, so only the top r (from lrq_truncate) are needed; for an
+ * indefinite Q the denominator is still trace(Q) and rho_r is then not a
+ * share of the positive spectrum.
+ *
+ *   Q        : as for lrq_truncate (dense: sum of Re Q_ii; Laplacian: sum of
+ *              the edge weights over both rows, self loops ignored).
+ *   lambda   : r doubles (device), the top eigenvalues, e.g. lambda_out of
+ *              lrq_truncate; r >= 0.
+ *   trace_out, rho_out : 1 double each (device), written.  trace(Q) = 0
+ *              (Q = 0) gives rho_r = 0.
+ * Errors: a negative or non-finite trace, non-finite lambda, or a malformed
+ * CSR (as for lrq_truncate) -> LRQ_EINVAL in *dev_status.  The trace is an
+ * FP64 sum in a nondeterministic order (exact for unit weights).
+ * ------------------------------------------------------------------------ */
+int lrq_spectral_energy(const lrq_matrix* Q, const double* lambda, int r, double* trace_out, double* rho_out,
+                        int32_t* dev_status, void* stream);
 
 /* --------------------------------------------------------------------------
  * lrq_rank1_sweep -- exact maximiser for rank 1 by an angular sweep

@@ -21,6 +21,10 @@ Pieces and the passages they follow:
   the rank-1 sweep and their exact cuts; ``greedy_cut`` (numpy): greedy
   local search on the cut from a given partition (the hybrid warm start,
   App. "Hybrid Warm-Start"), in the round reading given in its docstring.
+* ``null_directions`` (numpy): the null-vector sampler of Sec. 5 (the
+  randomised Algorithm 2), drawing rows with the Philox generator above.
+* ``spectral_energy`` (numpy): the spectral energy ratio rho_r (Sec. 5)
+  from the full spectrum (LAPACK ``eigvalsh``).
 * ``truncate_dense`` / ``truncate_laplacian``: spectral truncation
   (Sec. 4.1, Algorithm 3) through LAPACK ``eigh`` and ARPACK ``eigsh``
   (the paper's own eigen-solver, Sec. 5).
@@ -362,6 +366,80 @@ def augmented_rows(Vd, K: int) -> np.ndarray:
     return H.reshape(n * BK, 2 * d)
 
 
+def full_rank_by_elimination(H, tol: float = 1e-10) -> bool:
+    """Rank test of an m x (m+1) matrix taken in the sampler's precision:
+    FP64 Gaussian elimination with full pivoting (first largest entry in
+    row-major order), failing when the largest remaining pivot is at or
+    below tol * max|H|."""
+    A = np.array(H, dtype=np.float64)
+    m = A.shape[0]
+    scale = np.abs(A).max() if A.size else 0.0
+    if scale == 0.0:
+        return False
+    for k in range(m):
+        sub = np.abs(A[k:, k:])
+        p = int(np.argmax(sub))
+        pr, pc = k + p // sub.shape[1], k + p % sub.shape[1]
+        if sub.flat[p] <= tol * scale:
+            return False
+        A[[k, pr]] = A[[pr, k]]
+        A[:, [k, pc]] = A[:, [pc, k]]
+        for i in range(k + 1, m):
+            A[i, k:] -= (A[i, k] / A[k, k]) * A[k, k:]
+    return True
+
+
+def null_directions(V, K: int, seed: int, S: int, attempts: int = 64):
+    """The null-vector sampler (Sec. 5; the randomised form of Algorithm 2):
+    each slot draws 2r - 1 distinct rows of the augmented matrix (Eq. 6)
+    until they are linearly independent, and returns their unit null vector
+    as c = c~[:r] + i c~[r:].  Draw convention (Philox4x32-10, the counter
+    layout and the sign rule) as stated for lrq_sample_null_directions; the
+    null vector is the last right singular vector (SVD, a library step).
+    Returns (C complex128 S x r, draws per slot; 0 rows where a slot failed)."""
+    V = _c128(V)
+    n, r = V.shape
+    rows = augmented_rows(V, K)
+    N = rows.shape[0]
+    m = 2 * r - 1
+    key = (seed & 0xFFFFFFFF, (seed >> 32) & 0xFFFFFFFF)
+    C = np.zeros((S, r), dtype=np.complex128)
+    draws = np.zeros(S, dtype=np.int64)
+    for s in range(S):
+        for a in range(attempts):
+            draws[s] += 1
+            idx, neg, ok = [], False, True
+            for j in range(m):
+                got = False
+                for t in range(16):
+                    w = philox4x32_10((s & 0xFFFFFFFF, s >> 32, (a << 8) | (j << 4) | t, 0x4E56), key)
+                    if j == 0 and t == 0:
+                        neg = bool(w[2] & 1)
+                    R = (((int(w[0]) << 32) | int(w[1])) * N) >> 64
+                    if R not in idx:
+                        idx.append(R)
+                        got = True
+                        break
+                if not got:
+                    ok = False
+                    break
+            if not ok:
+                continue
+            H = rows[idx]
+            if not full_rank_by_elimination(H):
+                continue
+            c = np.linalg.svd(H)[2][-1]
+            c = c / np.linalg.norm(c)
+            j = int(np.argmax(np.abs(c)))
+            if (c[j] < 0) != neg:
+                c = -c
+            C[s] = c[:r] + 1j * c[r:]
+            break
+        else:
+            C[s] = 0
+    return C, draws
+
+
 def valid_index_sets(n: int, BK: int, size: int) -> np.ndarray:
     """All index sets of `size` hyperplanes with at most two from any
     coordinate group (Sec. 3, 'Structural properties')."""
@@ -478,6 +556,20 @@ def candidate_set_size(n: int, r: int, K: int) -> int:
         for i in range(0, d):
             tot += comb(n, i) * comb(n - i, 2 * (d - i) - 1) * BK ** (2 * (d - i) - 2) * (BK - 1) ** i
     return tot
+
+
+# --------------------------------------------------------------------------
+# Spectral energy ratio (Sec. 5, "When does low-rank work?")
+# --------------------------------------------------------------------------
+def spectral_energy(Q, r: int) -> float:
+    """rho_r = 1 - (sum of the r largest positive eigenvalues) / (sum of all
+    positive eigenvalues) of a Hermitian Q, from its full spectrum (LAPACK
+    eigvalsh); 0 for Q without positive eigenvalues."""
+    lam = np.linalg.eigvalsh(0.5 * (np.asarray(Q) + np.asarray(Q).conj().T))
+    pos = np.sort(lam[lam > 0])[::-1]
+    if pos.size == 0:
+        return 0.0
+    return float(1.0 - pos[:r].sum() / pos.sum())
 
 
 # --------------------------------------------------------------------------

@@ -93,62 +93,6 @@ __host__ __device__ bool next_comb(int N, int m, int* idx) {
 __device__ __forceinline__ double vre(const double2* V, int r, int i, int j) { return V[i * r + j].x; }
 __device__ __forceinline__ double vim(const double2* V, int r, int i, int j) { return V[i * r + j].y; }
 
-// Null vector of the m x (m+1) matrix H (row-major, modified); returns false
-// if the rank is below m.  Full pivoting; pivots below tol * scale reject.
-__device__ bool null_vector(double* H, int m, double* c) {
-  const int nc = m + 1;
-  int colperm[kEnumMaxRows + 1];
-  for (int j = 0; j < nc; ++j) colperm[j] = j;
-  double scale = 0.0;
-  for (int t = 0; t < m * nc; ++t) scale = fmax(scale, fabs(H[t]));
-  if (scale == 0.0) return false;
-  for (int k = 0; k < m; ++k) {
-    int pr = k, pc = k;
-    double best = -1.0;
-    for (int i = k; i < m; ++i)
-      for (int j = k; j < nc; ++j)
-        if (fabs(H[i * nc + j]) > best) {
-          best = fabs(H[i * nc + j]);
-          pr = i;
-          pc = j;
-        }
-    if (best <= 1e-10 * scale) return false;
-    if (pr != k)
-      for (int j = 0; j < nc; ++j) {
-        double t = H[k * nc + j];
-        H[k * nc + j] = H[pr * nc + j];
-        H[pr * nc + j] = t;
-      }
-    if (pc != k) {
-      for (int i = 0; i < m; ++i) {
-        double t = H[i * nc + k];
-        H[i * nc + k] = H[i * nc + pc];
-        H[i * nc + pc] = t;
-      }
-      int t = colperm[k];
-      colperm[k] = colperm[pc];
-      colperm[pc] = t;
-    }
-    for (int i = k + 1; i < m; ++i) {
-      double f = H[i * nc + k] / H[k * nc + k];
-      for (int j = k; j < nc; ++j) H[i * nc + j] -= f * H[k * nc + j];
-    }
-  }
-  // free variable: permuted column m = 1, back-substitute
-  double y[kEnumMaxRows + 1];
-  y[m] = 1.0;
-  for (int k = m - 1; k >= 0; --k) {
-    double s = H[k * nc + m];
-    for (int j = k + 1; j < m; ++j) s += H[k * nc + j] * y[j];
-    y[k] = -s / H[k * nc + k];
-  }
-  double nrm = 0.0;
-  for (int j = 0; j < nc; ++j) nrm += y[j] * y[j];
-  nrm = 1.0 / sqrt(nrm);
-  for (int j = 0; j < nc; ++j) c[colperm[j]] = y[j] * nrm;
-  return true;
-}
-
 // Decision code and code set of coordinate value (x, y) for the superset rule.
 // Returns the number of options written to opt (1, 2 or K).
 __device__ int code_options(double x, double y, double rownorm, bool dbl, const EnumTables& tb, int* opt) {
@@ -322,7 +266,7 @@ __global__ void __launch_bounds__(kEnumThreads) enum_kernel(const double2* __res
       double H[kEnumMaxRows * 2 * kEnumMaxD];
       build_rows(V, r, d, I, m, tb, H);
       double ct[2 * kEnumMaxD];
-      if (!null_vector(H, m, ct)) continue;
+      if (!null_vector_fp64<kEnumMaxRows>(H, m, ct)) continue;
       ++nfull;
       eval_vertex(V, n, r, d, I, m, ct, +1, tb, rown, best, rk, -1, nullptr, nullptr, status);
       eval_vertex(V, n, r, d, I, m, ct, -1, tb, rown, best, rk, -1, nullptr, nullptr, status);
@@ -387,7 +331,7 @@ __global__ void enum_final_kernel(const double2* __restrict__ V, int n, int r, c
   double H[kEnumMaxRows * 2 * kEnumMaxD];
   build_rows(V, r, d, I, m, tb, H);
   double ct[2 * kEnumMaxD];
-  null_vector(H, m, ct);
+  null_vector_fp64<kEnumMaxRows>(H, m, ct);
   EnumBest dummy = best;
   double f = 0.0;
   eval_vertex(V, n, r, d, I, m, ct, best.sign, tb, rown, dummy, best.rank, static_cast<long long>(best.choice), z_out,

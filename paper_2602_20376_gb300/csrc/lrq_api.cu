@@ -425,6 +425,34 @@ int lrq_two_eigvec_q(const void* V, int64_t n, int r, const double* lambda, void
                              static_cast<cudaStream_t>(stream));
 }
 
+int lrq_sample_null_directions(const void* V, int64_t n, int r, int K, uint64_t seed, int64_t S, void* C_out,
+                               int64_t* draws_out, int32_t* dev_status, void* stream) {
+  if (n < 1 || S < 1 || S >= (int64_t(1) << 31)) return fail(LRQ_EINVAL, "need n >= 1 and 1 <= S < 2^31");
+  if (r < 1 || r > kMaxRank) return fail(LRQ_EINVAL, "r must be in [1, 8]");
+  if (K < 2 || K > kMaxK) return fail(LRQ_EINVAL, "K must be in [2, 64]");
+  if (n * static_cast<int64_t>(K) < 2 * r - 1) return fail(LRQ_EINVAL, "fewer augmented rows than 2r - 1");
+  if (!V || !C_out || !draws_out || !dev_status) return fail(LRQ_EINVAL, "NULL pointer argument");
+  return launch_null_sample(static_cast<const float2*>(V), n, r, K, seed, S, static_cast<float2*>(C_out), draws_out,
+                            dev_status, static_cast<cudaStream_t>(stream));
+}
+
+int lrq_spectral_energy(const lrq_matrix* Q, const double* lambda, int r, double* trace_out, double* rho_out,
+                        int32_t* dev_status, void* stream) {
+  if (!Q) return fail(LRQ_EINVAL, "Q is NULL");
+  if (Q->kind != LRQ_MATRIX_DENSE_C128 && Q->kind != LRQ_MATRIX_CSR_LAPLACIAN)
+    return fail(LRQ_EINVAL, "unknown matrix kind");
+  if (Q->n < 1 || Q->n >= (int64_t(1) << 31)) return fail(LRQ_EINVAL, "n must be in [1, 2^31)");
+  if (r < 0) return fail(LRQ_EINVAL, "r must be >= 0");
+  if ((r > 0 && !lambda) || !trace_out || !rho_out || !dev_status) return fail(LRQ_EINVAL, "NULL pointer argument");
+  if (Q->kind == LRQ_MATRIX_DENSE_C128) {
+    if (!Q->values || Q->ld < Q->n) return fail(LRQ_EINVAL, "dense values NULL or ld < n");
+  } else {
+    if (!Q->rowptr || (Q->nnz > 0 && !Q->colidx)) return fail(LRQ_EINVAL, "CSR pointer is NULL");
+    if (Q->nnz < 0 || Q->nnz >= (int64_t(1) << 31)) return fail(LRQ_EINVAL, "nnz must be in [0, 2^31)");
+  }
+  return launch_spectral_energy(Q, lambda, r, trace_out, rho_out, dev_status, static_cast<cudaStream_t>(stream));
+}
+
 int lrq_greedy_workspace_size(int64_t n, size_t* bytes) {
   if (!bytes) return fail(LRQ_EINVAL, "bytes is NULL");
   if (n < 1 || n >= (int64_t(1) << 31)) return fail(LRQ_EINVAL, "n must be in [1, 2^31)");

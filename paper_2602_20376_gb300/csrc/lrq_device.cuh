@@ -138,4 +138,65 @@ __device__ __forceinline__ int decide_fp64(double x, double y, int K, const doub
   return static_cast<int>(k);
 }
 
+// ---------------------------------------------------------------------------
+// Null vector (unit norm) of the m x (m+1) matrix H (row-major, modified;
+// m <= kMaxRows); returns false if the rank is below m.  FP64 Gaussian
+// elimination with full pivoting: a largest remaining pivot at or below
+// 1e-10 max|H| rejects.  The null space's generator solves the triangular
+// system with the last (permuted) unknown set to 1.
+template <int kMaxRows>
+__device__ bool null_vector_fp64(double* H, int m, double* c) {
+  const int nc = m + 1;
+  int colperm[kMaxRows + 1];
+  for (int j = 0; j < nc; ++j) colperm[j] = j;
+  double scale = 0.0;
+  for (int t = 0; t < m * nc; ++t) scale = fmax(scale, fabs(H[t]));
+  if (scale == 0.0) return false;
+  for (int k = 0; k < m; ++k) {
+    int pr = k, pc = k;
+    double best = -1.0;
+    for (int i = k; i < m; ++i)
+      for (int j = k; j < nc; ++j)
+        if (fabs(H[i * nc + j]) > best) {
+          best = fabs(H[i * nc + j]);
+          pr = i;
+          pc = j;
+        }
+    if (best <= 1e-10 * scale) return false;
+    if (pr != k)
+      for (int j = 0; j < nc; ++j) {
+        double t = H[k * nc + j];
+        H[k * nc + j] = H[pr * nc + j];
+        H[pr * nc + j] = t;
+      }
+    if (pc != k) {
+      for (int i = 0; i < m; ++i) {
+        double t = H[i * nc + k];
+        H[i * nc + k] = H[i * nc + pc];
+        H[i * nc + pc] = t;
+      }
+      int t = colperm[k];
+      colperm[k] = colperm[pc];
+      colperm[pc] = t;
+    }
+    for (int i = k + 1; i < m; ++i) {
+      double f = H[i * nc + k] / H[k * nc + k];
+      for (int j = k; j < nc; ++j) H[i * nc + j] -= f * H[k * nc + j];
+    }
+  }
+  // free variable: permuted column m = 1, back-substitute
+  double y[kMaxRows + 1];
+  y[m] = 1.0;
+  for (int k = m - 1; k >= 0; --k) {
+    double s = H[k * nc + m];
+    for (int j = k + 1; j < m; ++j) s += H[k * nc + j] * y[j];
+    y[k] = -s / H[k * nc + k];
+  }
+  double nrm = 0.0;
+  for (int j = 0; j < nc; ++j) nrm += y[j] * y[j];
+  nrm = 1.0 / sqrt(nrm);
+  for (int j = 0; j < nc; ++j) c[colperm[j]] = y[j] * nrm;
+  return true;
+}
+
 }  // namespace lrq

@@ -129,6 +129,12 @@ int launch_rank1(const double2* q, int64_t n, int K, uint8_t* z_out, double* f_o
                  const int32_t* colidx, int64_t nnz, int64_t* cut_out, uint8_t* zcut_out, void* ws, int32_t* status,
                  cudaStream_t st);
 int launch_two_eigvec_q(const double2* V, int64_t n, int r, const double* lambda, double2* q, cudaStream_t st);
+// null-vector direction sampler
+int launch_null_sample(const float2* V, int64_t n, int r, int K, uint64_t seed, int64_t S, float2* C,
+                       int64_t* draws_out, int32_t* status, cudaStream_t st);
+// spectral energy ratio
+int launch_spectral_energy(const lrq_matrix* Q, const double* lambda, int r, double* trace_out, double* rho_out,
+                           int32_t* status, cudaStream_t st);
 // greedy local search (Max-K-Cut)
 size_t greedy_workspace_bytes(int64_t n);
 int launch_greedy(const int32_t* rowptr, const int32_t* colidx, int64_t n, int64_t nnz, int K, uint8_t* z,

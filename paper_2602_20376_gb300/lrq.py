@@ -147,6 +147,10 @@ def load() -> ctypes.CDLL:
         lib.lrq_rank1_workspace_size.restype = I
         lib.lrq_rank1_sweep.argtypes = [P, I64, I, P, P, P, P, I64, P, P, P, SZ, P, P]
         lib.lrq_rank1_sweep.restype = I
+        lib.lrq_sample_null_directions.argtypes = [P, I64, I, I, U64, I64, P, P, P, P]
+        lib.lrq_sample_null_directions.restype = I
+        lib.lrq_spectral_energy.argtypes = [ctypes.POINTER(LrqMatrix), P, I, P, P, P, P]
+        lib.lrq_spectral_energy.restype = I
         lib.lrq_two_eigvec_q.argtypes = [P, I64, I, P, P, P]
         lib.lrq_two_eigvec_q.restype = I
         lib.lrq_greedy_workspace_size.argtypes = [I64, ctypes.POINTER(SZ)]
@@ -172,7 +176,7 @@ def exported_symbols():
     return ["lrq_status_string", "lrq_last_error", "lrq_abi_version", "lrq_sample_directions",
             "lrq_sample_score_workspace_size", "lrq_sample_score", "lrq_rescore_workspace_size",
             "lrq_rescore", "lrq_rescore_no_alloc", "lrq_truncate_workspace_size", "lrq_truncate",
-            "lrq_rank1_workspace_size", "lrq_rank1_sweep", "lrq_two_eigvec_q", "lrq_greedy_workspace_size", "lrq_greedy_cut",
+            "lrq_sample_null_directions", "lrq_spectral_energy", "lrq_rank1_workspace_size", "lrq_rank1_sweep", "lrq_two_eigvec_q", "lrq_greedy_workspace_size", "lrq_greedy_cut",
             "lrq_enumerate_workspace_size", "lrq_enumerate", "lrq_batched_plan_create", "lrq_batched_plan_destroy",
             "lrq_batched_workspace_size", "lrq_batched_prepare", "lrq_batched_autotune", "lrq_batched_tile",
             "lrq_sample_score_batched", "lrq_batched_graph_create", "lrq_graph_launch", "lrq_graph_destroy",
@@ -349,6 +353,37 @@ def lrq_rank1_sweep(q, K, z_out, f_out, rowptr, colidx, cut_out, zcut_out, ws, d
     _check(load().lrq_rank1_sweep(_ptr(q), n, int(K), _ptr(z_out), _ptr(f_out), _ptr(rowptr), _ptr(colidx), nnz,
                                   _ptr(cut_out), _ptr(zcut_out), _ptr(ws), ws.numel() * ws.element_size(),
                                   _ptr(dev_status), _stream(stream)), "lrq_rank1_sweep")
+
+
+def lrq_sample_null_directions(V, K, seed, S, C_out, draws_out, dev_status, stream=None):
+    """V: n x r complex64 (device); C_out: S x r complex64; draws_out: 1 int64."""
+    n, r = V.shape
+    _check(load().lrq_sample_null_directions(_ptr(V), n, r, int(K), int(seed), int(S), _ptr(C_out), _ptr(draws_out),
+                                             _ptr(dev_status), _stream(stream)), "lrq_sample_null_directions")
+
+
+def sample_null_directions(V, K, S, seed, stream=None):
+    """S null-vector directions (randomised Algorithm 2) and the draw count."""
+    C = torch.empty((S, V.shape[1]), dtype=torch.complex64, device=V.device)
+    draws = torch.zeros(1, dtype=torch.int64, device=V.device)
+    st = torch.zeros(1, dtype=torch.int32, device=V.device)
+    lrq_sample_null_directions(V, K, seed, S, C, draws, st, stream)
+    return dict(C=C, draws=draws, dev_status=st)
+
+
+def lrq_spectral_energy(Q, lam, trace_out, rho_out, dev_status, stream=None):
+    """Q: LrqMatrix; lam: r float64 (device)."""
+    _check(load().lrq_spectral_energy(ctypes.byref(Q), _ptr(lam), lam.numel(), _ptr(trace_out), _ptr(rho_out),
+                                      _ptr(dev_status), _stream(stream)), "lrq_spectral_energy")
+
+
+def spectral_energy(Q, lam, device="cuda", stream=None):
+    """rho_r = 1 - sum of the top r eigenvalues / trace(Q), and trace(Q)."""
+    tr = torch.zeros(1, dtype=torch.float64, device=device)
+    rho = torch.zeros(1, dtype=torch.float64, device=device)
+    st = torch.zeros(1, dtype=torch.int32, device=device)
+    lrq_spectral_energy(Q, lam, tr, rho, st, stream)
+    return dict(rho=rho, trace=tr, dev_status=st)
 
 
 def lrq_two_eigvec_q(V, lam, q_out, stream=None):

@@ -202,3 +202,17 @@ def test_greedy_rejects_bad_arguments_on_host(lib):
     need = ctypes.c_size_t(0)
     assert lib.lrq_greedy_workspace_size(100, ctypes.byref(need)) == 0 and need.value >= 500
     assert lib.lrq_greedy_workspace_size(0, ctypes.byref(need)) == 1
+
+
+def test_spectral_energy_rejects_bad_arguments_on_host(lib):
+    from paper_2602_20376_gb300 import lrq as L
+    P = ctypes.c_void_p
+    Q = L.LrqMatrix(L.LRQ_MATRIX_CSR_LAPLACIAN, 100, None, 0, 256, 512, None, 400)
+    assert lib.lrq_spectral_energy(None, P(256), 2, P(512), P(1024), P(2048), None) == 1
+    assert lib.lrq_spectral_energy(ctypes.byref(Q), P(256), -1, P(512), P(1024), P(2048), None) == 1
+    assert lib.lrq_spectral_energy(ctypes.byref(Q), None, 2, P(512), P(1024), P(2048), None) == 1
+    assert lib.lrq_spectral_energy(ctypes.byref(Q), P(256), 2, None, P(1024), P(2048), None) == 1
+    bad = L.LrqMatrix(7, 100, None, 0, 256, 512, None, 400)
+    assert lib.lrq_spectral_energy(ctypes.byref(bad), P(256), 2, P(512), P(1024), P(2048), None) == 1
+    dense = L.LrqMatrix(L.LRQ_MATRIX_DENSE_C128, 100, 4096, 50, None, None, None, 0)
+    assert lib.lrq_spectral_energy(ctypes.byref(dense), P(256), 2, P(512), P(1024), P(2048), None) == 1

@@ -543,3 +543,106 @@ def test_two_eigvec_q_is_a_pair_of_unit_eigenvectors():
     # a column with a non-positive eigenvalue contributes nothing
     q0 = O.two_eigvec_q(V, np.array([lam[0], 0.0]))
     assert np.array_equal(q0.imag, np.zeros(300))
+
+
+# ----------------------------------------------------------------------------
+# Spectral energy ratio
+# ----------------------------------------------------------------------------
+def test_spectral_energy_torus_closed_form():
+    # k1 x k2 torus Laplacian: eigenvalues 4 - 2cos(2 pi a/k1) - 2cos(2 pi b/k2),
+    # all >= 0, summing to the trace 4 k1 k2
+    k1, k2 = 10, 12
+    rowptr, colidx = I.torus_graph(k1, k2)
+    L = O.laplacian_dense(rowptr, colidx)
+    a = np.arange(k1)[:, None]
+    b = np.arange(k2)[None, :]
+    ev = np.sort((4 - 2 * np.cos(2 * np.pi * a / k1) - 2 * np.cos(2 * np.pi * b / k2)).ravel())[::-1]
+    for r in (1, 2, 5):
+        assert abs(O.spectral_energy(L, r) - (1 - ev[:r].sum() / (4 * k1 * k2))) < 1e-12
+
+
+def test_spectral_energy_exact_low_rank_and_negative_part():
+    V = I.factor(50, 3, seed=12, scales=(3.0, 2.0, 1.0))
+    Q = V @ V.conj().T
+    assert abs(O.spectral_energy(Q, 3)) < 1e-12
+    # the top eigenvalue of V V^H is the largest singular value squared
+    s = np.linalg.svd(V, compute_uv=False) ** 2
+    assert abs(O.spectral_energy(Q, 1) - (1 - s[0] / s.sum())) < 1e-12
+    # negative eigenvalues carry no energy
+    D = np.diag([5.0, 3.0, -4.0, 2.0, -1.0]).astype(np.complex128)
+    assert abs(O.spectral_energy(D, 1) - (1 - 5 / 10)) < 1e-15
+    assert O.spectral_energy(-np.eye(3), 2) == 0.0
+
+
+def test_spectral_energy_sbm_above_paper_level():
+    # the paper reports rho_2 > 98% on SBM and Erdos-Renyi graphs: the
+    # low-rank truncation misses almost all the spectral energy there
+    rowptr, colidx, _ = I.sbm_graph(1500, 4.0, 8.0, seed=13)
+    L = O.laplacian_dense(rowptr, colidx)
+    assert O.spectral_energy(L, 2) > 0.98
+
+
+# ----------------------------------------------------------------------------
+# Null-vector sampler (randomised Algorithm 2)
+# ----------------------------------------------------------------------------
+def _drawn_rows(K, r, N, seed, s, a):
+    """Re-draws the rows of attempt a of slot s from the stated convention."""
+    out = []
+    for j in range(2 * r - 1):
+        for t in range(16):
+            w = O.philox4x32_10((s, 0, (a << 8) | (j << 4) | t, 0x4E56), (seed, 0))
+            R = (((int(w[0]) << 32) | int(w[1])) * N) >> 64
+            if R not in out:
+                out.append(R)
+                break
+    return out
+
+
+@pytest.mark.parametrize("n,r,K", [(40, 2, 3), (30, 3, 4), (25, 1, 2), (20, 4, 5)])
+def test_null_directions_lie_on_the_drawn_boundaries(n, r, K):
+    # each direction puts V_i c exactly on the boundary m of every drawn row
+    # (i, m): Im(exp(-i theta_m) V_i c) = 0, written here with complex numbers
+    V = I.factor(n, r, seed=20 + r)
+    BK = K // 2 if K % 2 == 0 else K
+    C, draws = O.null_directions(V, K, seed=3, S=40)
+    assert np.allclose(np.linalg.norm(C, axis=1), 1.0, atol=1e-12)
+    for s in range(40):
+        rows = _drawn_rows(K, r, n * BK, 3, s, int(draws[s]) - 1)
+        assert len(set(rows)) == 2 * r - 1
+        for R in rows:
+            i, m = divmod(R, BK)
+            theta = np.pi * (2 * m + 1) / K
+            assert abs((np.exp(-1j * theta) * (V[i] @ C[s])).imag) < 1e-12 * np.abs(V[i]).sum()
+
+
+def test_null_directions_reject_dependent_rows():
+    # n = 2, r = 2, K = 3: the three rows of one coordinate span only a plane
+    # (the row is R-linear in rho_m), so of the C(6, 3) = 20 row sets exactly
+    # 2 are dependent; with generic V the rejection rate is 1/10
+    V = I.factor(2, 2, seed=30)
+    S = 3000
+    C, draws = O.null_directions(V, 3, seed=31, S=S)
+    rej = (draws.sum() - S) / draws.sum()
+    se = np.sqrt(0.1 * 0.9 / draws.sum())
+    assert abs(rej - 0.1) < 5 * se
+
+
+def test_null_directions_rank_deficient_v_fails_every_slot():
+    V = I.factor(30, 2, seed=32)
+    V[:, 1] = 0  # rank 1 < r: every 3 x 4 row set has rank <= 2
+    C, draws = O.null_directions(V, 3, seed=33, S=5)
+    assert np.all(draws == 64) and np.all(C == 0)
+
+
+def test_full_rank_by_elimination_matches_singular_values():
+    g = I.rng(34)
+    for _ in range(200):
+        m = int(g.integers(1, 8))
+        H = g.standard_normal((m, m + 1))
+        if g.random() < 0.5 and m > 1:
+            H[-1] = H[0] * 2.0 - H[1 if m > 2 else 0] * 0.5  # a dependent row
+            dep = True
+        else:
+            dep = False
+        sv = np.linalg.svd(H, compute_uv=False)
+        assert O.full_rank_by_elimination(H) == (not dep) == (sv[-1] > 1e-8 * sv[0])
