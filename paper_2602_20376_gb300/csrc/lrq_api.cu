@@ -18,9 +18,8 @@
 namespace lrq {
 
 int tc_rows_per_tile(int K);
-int tc_workers_per_cta(int K);
-size_t tc_bytes_vaug(int K, int r, int64_t n_tiles);
-size_t tc_bytes_b2(int K, int r, int64_t n_tiles);
+int tc_workers_per_cta(int K, int r);
+size_t tc_bytes_tiles(int K, int r, int64_t n_tiles);
 size_t tc_bytes_dirs(int r, int64_t c_tiles);
 
 static thread_local char g_last_error[512] = {0};
@@ -120,7 +119,7 @@ int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_
     p->n_tiles = ceil_div(n, p->rows_per_tile);
     // coordinate chunks: balance (chunk, candidate tile) items over the
     // workers (num_sms CTAs x workers per CTA)
-    const int64_t workers = static_cast<int64_t>(num_sms) * tc_workers_per_cta(K);
+    const int64_t workers = static_cast<int64_t>(num_sms) * tc_workers_per_cta(K, r);
     int best_ns = 1;
     double best_eff = -1.0;
     for (int ns = 1; ns <= 64 && ns <= p->n_tiles; ++ns) {
@@ -157,12 +156,12 @@ int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_
   p->sz_Tpart = 256 * 2 * kMaxRank * sizeof(double);
   p->off_Tpart = take(cur, p->sz_Tpart);
   if (mode == LRQ_MODE_BF16_TC) {
-    p->sz_vt = tc_bytes_vaug(K, r, p->n_tiles);
-    p->off_vt = take(cur, p->sz_vt);
-    p->sz_b2 = tc_bytes_b2(K, r, p->n_tiles);
-    p->off_b2 = take(cur, p->sz_b2);
+    p->sz_tiles = tc_bytes_tiles(K, r, p->n_tiles);
+    p->off_tiles = take(cur, p->sz_tiles);
     p->sz_ct = tc_bytes_dirs(r, p->c_tiles);
     p->off_ct = take(cur, p->sz_ct);
+    p->sz_scale = 4 * sizeof(float);
+    p->off_scale = take(cur, p->sz_scale);
   }
   p->sz_scores = static_cast<size_t>(S) * sizeof(float);
   p->off_scores = take(cur, p->sz_scores);
@@ -282,9 +281,9 @@ int lrq_sample_score(const void* V, int64_t n, int r, int K, void* C, int genera
       if ((e = launch_colsum(Vf, n, r, reinterpret_cast<double*>(w + p.off_Tpart), T, nb, st))) return e;
       Tuse = T;
     }
-    if ((e = launch_tc_pack(p, a, Vf, Cf, w + p.off_vt, w + p.off_b2, w + p.off_ct, st))) return e;
+    if ((e = launch_tc_pack(p, a, Vf, Cf, w + p.off_tiles, w + p.off_ct, w + p.off_scale, st))) return e;
     timing_start(st);
-    if ((e = launch_score_tc(p, a, w + p.off_vt, w + p.off_b2, w + p.off_ct, partial, dev_status, st))) return e;
+    if ((e = launch_score_tc(p, a, w + p.off_tiles, w + p.off_ct, w + p.off_scale, partial, dev_status, st))) return e;
     timing_stop(st);
   } else {
     timing_start(st);

@@ -63,9 +63,9 @@ struct ScorePlan {
   size_t off_partial, sz_partial;   // npart x S_pad x 2r doubles
   size_t off_T, sz_T;               // 2r doubles (column sums of conj(V), odd K)
   size_t off_Tpart, sz_Tpart;       // per-block partial column sums
-  size_t off_vt, sz_vt;             // packed augmented rows (bf16)
-  size_t off_b2, sz_b2;             // packed per-class coefficient rows (bf16)
+  size_t off_tiles, sz_tiles;       // packed coordinate tiles: augmented rows (bf16) | class rows (FP8 hi | lo)
   size_t off_ct, sz_ct;             // packed directions (bf16)
+  size_t off_scale, sz_scale;       // GEMM2 operand scale {s, 1/s, max|V|}
   size_t off_scores, sz_scores;     // S floats (when the caller passes none)
   size_t off_keys, sz_keys;         // selection keys
   size_t total;
@@ -146,10 +146,10 @@ size_t enum_workspace_bytes(int64_t n, int r);
 int launch_enumerate(const double2* V, int64_t n, int r, int K, uint8_t* z_out, double* f_out, int64_t* n_sets_out,
                      void* ws, int32_t* status, cudaStream_t st);
 // tensor-core path
-int launch_tc_pack(const ScorePlan& p, const Alphabet& a, const float2* V, const float2* C,
-                   void* vt, void* b2, void* ct, cudaStream_t st);
-int launch_score_tc(const ScorePlan& p, const Alphabet& a, const void* vt, const void* b2,
-                    const void* ct, double* partial, int32_t* status, cudaStream_t st);
+int launch_tc_pack(const ScorePlan& p, const Alphabet& a, const float2* V, const float2* C, void* tiles, void* ct,
+                   void* scale, cudaStream_t st);
+int launch_score_tc(const ScorePlan& p, const Alphabet& a, const void* tiles, const void* ct, const void* scale,
+                    double* partial, int32_t* status, cudaStream_t st);
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

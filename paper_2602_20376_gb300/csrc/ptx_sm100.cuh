@@ -4,7 +4,7 @@
 // memory / instruction descriptors of tcgen05.mma.
 //
 // Descriptor layouts follow the PTX ISA (tcgen05 "Shared memory descriptor"
-// and "Instruction descriptor" for .kind::f16).  All operand tiles used here
+// and "Instruction descriptor" for .kind::f16 and .kind::f8f6f4).  All operand tiles used here
 // are K-major without swizzle: an 8-row x 16-byte "core matrix" is stored
 // contiguously (rows 16 B apart); LBO is the byte distance between core
 // matrices adjacent along K, SBO the distance between 8-row groups along M/N.
@@ -187,6 +187,19 @@ __device__ __forceinline__ void mma_bf16_ts(uint32_t d_tmem, uint32_t a_tmem, ui
       : "memory");
 }
 
+// D[tmem] (+)= A[tmem] x B[smem]^T, FP8 E4M3 in, FP32 accumulate
+// (kind::f8f6f4); A is 128 lanes x 32 E4M3 values (8 columns, 4 per column,
+// lowest K in the lowest byte) of tensor memory.
+__device__ __forceinline__ void mma_e4m3_ts(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
+                                            uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+      "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+
 // Arrive on `bar` once all previously issued tcgen05 async operations of this
 // thread have completed.
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
@@ -261,6 +274,14 @@ __host__ __device__ constexpr uint32_t idesc_bf16_f32(int M, int N) {
   return (1u << 4)                                   // D format: F32
          | (1u << 7)                                 // A format: BF16
          | (1u << 10)                                // B format: BF16
+         | (static_cast<uint32_t>(N >> 3) << 17)     // N / 8
+         | (static_cast<uint32_t>(M >> 4) << 24);    // M / 16
+}
+
+// Instruction descriptor for kind::f8f6f4: E4M3 x E4M3 -> FP32, both K-major
+// (A and B format fields 0 = E4M3).
+__host__ __device__ constexpr uint32_t idesc_e4m3_f32(int M, int N) {
+  return (1u << 4)                                   // D format: F32
          | (static_cast<uint32_t>(N >> 3) << 17)     // N / 8
          | (static_cast<uint32_t>(M >> 4) << 24);    // M / 16
 }

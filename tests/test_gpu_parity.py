@@ -7,9 +7,9 @@ Tolerances (stated here, derived in the design doc):
   where the oracle's own angle margin to a boundary is below 1e-9 rad (a tie
   in FP64 arithmetic).
 * BF16 tensor-core scoring: per candidate, |sqrt(f) - sqrt(f_oracle)| within
-  the bfloat16 error bound of _bf16_bound (decision flips only where the
-  oracle's margin is inside the bf16 projection error, plus operand
-  rounding of the per-class sums); median relative error below 3e-3 for
+  the error bound of _bf16_bound (decision flips only where the oracle's
+  margin is inside the bf16 projection error, plus the hi + lo E4M3
+  rounding of the per-class sums' operand); median relative error below 3e-3 for
   n >= 1000.  The winner is decided after the FP64 re-scoring above.
 * Sampler: within 1e-6 of the oracle's Philox + Box-Muller stream.
 * Cuts: exact integers.
@@ -125,9 +125,13 @@ def _bf16_bound(V, K, C):
     2^-7 sum_k |V~_ik| |c~_k| <= 2^-7 sum_j |V_ij|_1 |c_j|_1 (taken here with a
     factor-2 margin as e_i = 2^-6 sum_j |V_ij|_1 |c_j|_1); a code can differ
     from the FP64 decision only where |w_i| sin(margin_i) <= e_i.  Each such
-    coordinate moves ||V^H z|| by at most 2 sin(pi/K) |V_i|.  GEMM2 rounds
-    beta_g conj(V_i) to bfloat16: at most 2^-8 sqrt(2) max|beta| |V_i| per
-    coordinate.  FP32 accumulation adds < 1e-5 relative."""
+    coordinate moves ||V^H z|| by at most 2 sin(pi/K) |V_i|.  GEMM2 scales
+    beta_g conj(V_i) by s = 2^(5 - ilogb(a)), a = max |Re V|, |Im V|, and
+    stores it as a hi + lo pair of E4M3 numbers (3-bit significands): a
+    component carries at most 2^-4 * 2^-4 = 2^-8 relative error, plus half an
+    E4M3 subnormal step, 2^-10 / s <= 2^-15 a, where the remainder is tiny;
+    so at most 2^-8 sqrt(2) max|beta| |V_i| + sqrt(2) 2^-15 a per coordinate.
+    FP32 accumulation adds < 1e-5 relative."""
     V = V.astype(np.complex128)
     C = C.astype(np.complex128)
     marg, absw = O.margins(V, K, C)
@@ -139,7 +143,8 @@ def _bf16_bound(V, K, C):
     flip = 2 * np.sin(np.pi / K) * (unsure * rown[None, :]).sum(axis=1)
     w = np.exp(2j * np.pi * np.arange(K) / K)
     beta = np.abs(w - 1).max() if K % 2 else np.abs(np.diff(np.append(w, w[0]))).max() / 2
-    rnd = 2.0 ** -8 * np.sqrt(2) * beta * rown.sum()
+    amax = max(np.abs(V.real).max(), np.abs(V.imag).max())
+    rnd = 2.0 ** -8 * np.sqrt(2) * beta * rown.sum() + np.sqrt(2) * 2.0 ** -15 * amax * V.shape[0]
     return flip + rnd
 
 
