@@ -176,22 +176,28 @@ __device__ __forceinline__ uint32_t sign_bytes4(uint32_t a, uint32_t b, uint32_t
 struct TcCursor {
   int64_t item;
   int j, ntile;
-  int64_t ic;  // items passed
+  int64_t ic;     // items passed
+  int64_t chunk;  // coordinate chunk of the item
+  int64_t ct;     // candidate tile of the item
+  int64_t t0;     // first coordinate tile of the chunk
 };
 
-__device__ __forceinline__ int tc_tiles_of(const TcParams& prm, int64_t it) {
-  if (it >= prm.num_items) return 0;
-  const int64_t t0 = (it / prm.c_tiles) * prm.tiles_per_chunk;
-  return static_cast<int>(min(prm.n_tiles, t0 + prm.tiles_per_chunk) - t0);
+// The item's chunk, candidate tile and tile range, computed once per item
+// (64-bit divisions are kept off the per-tile path).
+__device__ __forceinline__ TcCursor tc_start(const TcParams& prm, int64_t item, int64_t ic) {
+  TcCursor c;
+  c.item = item;
+  c.j = 0;
+  c.ic = ic;
+  c.chunk = item / prm.c_tiles;
+  c.ct = item - c.chunk * prm.c_tiles;
+  c.t0 = c.chunk * prm.tiles_per_chunk;
+  c.ntile = item < prm.num_items ? static_cast<int>(min(prm.n_tiles, c.t0 + prm.tiles_per_chunk) - c.t0) : 0;
+  return c;
 }
 
 __device__ __forceinline__ void tc_advance(const TcParams& prm, int64_t workers, TcCursor& c) {
-  if (++c.j == c.ntile) {
-    c.item += workers;
-    c.ntile = tc_tiles_of(prm, c.item);
-    c.j = 0;
-    ++c.ic;
-  }
+  if (++c.j == c.ntile) c = tc_start(prm, c.item + workers, c.ic + 1);
 }
 
 template <int K, int KCH>
@@ -275,7 +281,7 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
   constexpr uint32_t lbo_b2 = L::N2R * 16;
   float2* acc = reinterpret_cast<float2*>(wsm + L::W_ACC) + row * 16;  // (hi, lo) per component
 
-  TcCursor cc{gw, 0, tc_tiles_of(prm, gw), 0};  // consumer: the tile being rounded
+  TcCursor cc = tc_start(prm, gw, 0);           // consumer: the tile being rounded
   TcCursor lc = cc;                             // issuer: the next tile to load
   int64_t lg = 0, cg = 0;                       // tiles loaded / stages waited for
   int64_t la = 0, ca = 0;                       // direction tiles loaded / waited for
@@ -284,7 +290,7 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
   auto load_tile = [&]() {
     const uint32_t s = static_cast<uint32_t>(lg % NST);
     uint8_t* st = wsm + s * L::STAGE_BYTES;
-    const int64_t t = (lc.item / prm.c_tiles) * prm.tiles_per_chunk + lc.j;
+    const int64_t t = lc.t0 + lc.j;
     ptx::mbar_arrive_expect_tx(&full_b[s], L::STAGE_TX);
     ptx::tma_load_2d(st, &tm_vt, 0, static_cast<int>(t * (L::TILE_BYTES / 256)), &full_b[s]);
     ++lg;
@@ -296,7 +302,7 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
     const uint32_t b = static_cast<uint32_t>(la & 1);
     ptx::mbar_arrive_expect_tx(&a1_full[b], L::A1_BYTES);
     ptx::tma_load_2d(wsm + L::W_A1 + b * L::A1_BYTES, &tm_ct, 0,
-                     static_cast<int>((it % prm.c_tiles) * (L::A1_BYTES / 256)), &a1_full[b]);
+                     static_cast<int>((it % prm.c_tiles) * (L::A1_BYTES / 256)), &a1_full[b]);  // once per item
     ++la;
   };
   auto wait_stage = [&]() -> bool {  // the stage of tile cg
@@ -339,7 +345,7 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
     const bool first = pos == 0;
     const bool item_end = (cc.j == cc.ntile - 1);
     const bool last = (pos == F - 1) || item_end;
-    const bool has_next = !item_end || tc_tiles_of(prm, cc.item + workers) > 0;
+    const bool has_next = !item_end || cc.item + workers < prm.num_items;
     bad = bad || !warp_wait(d1_full, g & 1u, abort_flag, lane);
     // ---- round the projections of tile g into indicator words in A2
     if (!bad) {
@@ -438,7 +444,7 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
         }
         ptx::tc_fence_before();
         const int r2 = 2 * prm.r;
-        double* out = partial + ((cc.item / prm.c_tiles) * prm.S_pad + (cc.item % prm.c_tiles) * kTcM + row) * r2;
+        double* out = partial + (cc.chunk * prm.S_pad + cc.ct * kTcM + row) * r2;
 #pragma unroll
         for (int jj = 0; jj < NOUT; ++jj) {
           if (jj < r2) {
