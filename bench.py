@@ -239,6 +239,13 @@ def run_ours(args):
     res_host = torch.empty(TOP_M + 2, dtype=torch.float64).pin_memory()
     e_start = torch.cuda.Event(enable_timing=True)
     e_stop = torch.cuda.Event(enable_timing=True)
+    for i in range(min(args.warmup, 2)):  # untimed: the host-buffer path once warmed up
+        V.copy_(V_host, non_blocking=True)
+        step(args.warmup + i)
+        res_host[:TOP_M].copy_(f64, non_blocking=True)
+        res_host[TOP_M:TOP_M + 1].copy_(best_f, non_blocking=True)
+        res_host[TOP_M + 1:].copy_(best.to(torch.float64), non_blocking=True)
+        torch.cuda.current_stream().synchronize()
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     e_start.record(stream)

@@ -202,7 +202,8 @@ __device__ __forceinline__ void tc_advance(const TcParams& prm, int64_t workers,
 
 template <int K, int KCH>
 __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
-    score_tc_kernel(const __grid_constant__ CUtensorMap tm_vt, const __grid_constant__ CUtensorMap tm_ct, TcParams prm, const float* __restrict__ scale,
+    score_tc_kernel(const __grid_constant__ CUtensorMap tm_vt, const __grid_constant__ CUtensorMap tm_ct,
+                    TcParams prm, const float* __restrict__ scale, const uint32_t* __restrict__ iw,
                     double* __restrict__ partial, int32_t* status) {
   using Sh = TcShape<K, KCH>;
   using L = TcLayout<K, KCH>;
@@ -346,6 +347,20 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
     const bool item_end = (cc.j == cc.ntile - 1);
     const bool last = (pos == F - 1) || item_end;
     const bool has_next = !item_end || cc.item + workers < prm.num_items;
+    // indicator magnitudes 2^(g - e_i) of the tile's coordinates (E4M3 bytes),
+    // read while D1 is on its way
+    uint32_t mag[CW];
+    {
+      const uint4* iwt = reinterpret_cast<const uint4*>(iw + (cc.t0 + cc.j) * CW);
+#pragma unroll
+      for (int c = 0; c < CW / 4; ++c) {
+        const uint4 v4 = __ldg(iwt + c);
+        mag[4 * c] = v4.x;
+        mag[4 * c + 1] = v4.y;
+        mag[4 * c + 2] = v4.z;
+        mag[4 * c + 3] = v4.w;
+      }
+    }
     bad = bad || !warp_wait(d1_full, g & 1u, abort_flag, lane);
     // ---- round the projections of tile g into indicator words in A2
     if (!bad) {
@@ -386,9 +401,9 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
 #pragma unroll
           for (int gc = 0; gc < G; ++gc) {
             if constexpr (K % 2 == 1)
-              wv[gc * CW + h * 4 + p] = ~nm[gc] & nm[gc + 1] & 0x38383838u;  // p_{k-1} > 0 and p_k < 0
+              wv[gc * CW + h * 4 + p] = ~nm[gc] & nm[gc + 1] & mag[h * 4 + p];  // p_{k-1} > 0 and p_k < 0
             else
-              wv[gc * CW + h * 4 + p] = (nm[gc] & 0x80808080u) | 0x38383838u;  // sign(p_m) as +-1
+              wv[gc * CW + h * 4 + p] = (nm[gc] & 0x80808080u) | mag[h * 4 + p];  // sign(p_m) as +-1
           }
         }
         }
@@ -539,9 +554,16 @@ __global__ void pack_vaug_kernel(const float2* __restrict__ V, int64_t n, int r,
   }
 }
 
-// Scale of the GEMM2 operand: B2 entries are components of beta conj(V_i)
-// with |beta| <= 2, so |B2| < 3 max|V component|; s = 2^(5 - ilogb(amax))
-// puts 3 amax s below 192 (E4M3 reaches 448).  scale = {s, 1/s, amax bits}.
+// Scales of the GEMM2 operands.  B2 entries are components of
+// beta conj(V_i) with |beta| <= 2, so |B2| < 3 m_i, m_i = max |V_i component|.
+// Coordinate i is scaled by 2^e_i, e_i = 5 - ilogb(m_i), which moves m_i into
+// [32, 64) and its entries below 192 (E4M3 reaches 448): every coordinate
+// keeps the full hi + lo precision however small its row.
+// Its indicator carries the inverse, 2^(g - e_i), so each product is the
+// entry times 2^g, one global power of two (g = 5 - ilogb(max_i m_i)) that the
+// epilogue removes.  2^(g - e_i) must be an E4M3 number (down to 2^-9), so
+// e_i <= g + 9: rows more than 2^9 below the largest lose relative precision
+// (their share of the sums is as small).  scale = {2^g, 2^-g, max m_i bits}.
 __global__ void b2_amax_kernel(const float2* __restrict__ V, int64_t count, float* __restrict__ scale) {
   float m = 0.f;
   for (int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; q < count;
@@ -555,12 +577,27 @@ __global__ void b2_amax_kernel(const float2* __restrict__ V, int64_t count, floa
   if ((threadIdx.x & 31) == 0 && m > 0.f) atomicMax(reinterpret_cast<unsigned*>(scale + 2), __float_as_uint(m));
 }
 
+__device__ __forceinline__ int b2_global_exp(const float* scale) {
+  const float a = scale[2];
+  return 5 - ((a > 0.f && isfinite(a)) ? ilogbf(a) : 5);
+}
+
 __global__ void b2_scale_kernel(float* scale) {
   if (threadIdx.x != 0) return;
-  const float a = scale[2];
-  const int ex = (a > 0.f && isfinite(a)) ? ilogbf(a) : 5;
-  scale[0] = ldexpf(1.f, 5 - ex);
-  scale[1] = ldexpf(1.f, ex - 5);
+  const int g = b2_global_exp(scale);
+  scale[0] = ldexpf(1.f, g);
+  scale[1] = ldexpf(1.f, -g);
+}
+
+// e_i of coordinate ig (see above); g for a zero row
+__device__ __forceinline__ int b2_coord_exp(const float2* __restrict__ V, int64_t ig, int r, int g) {
+  float m = 0.f;
+  for (int jj = 0; jj < r; ++jj) {
+    const float2 v = V[ig * r + jj];
+    m = fmaxf(m, fmaxf(fabsf(v.x), fabsf(v.y)));
+  }
+  const int e = (m > 0.f && isfinite(m)) ? 5 - ilogbf(m) : g;
+  return e < g ? g : (e > g + 9 ? g + 9 : e);
 }
 
 // GEMM2 B rows (FP8 E4M3): tile t, K-chunk kc (16 reduction entries), row nr:
@@ -579,7 +616,7 @@ __global__ void pack_b2_kernel(const float2* __restrict__ V, int64_t n, int r, i
   const int kc = within / L::N2R, nr = within % L::N2R;
   const bool lo = nr >= Sh::NOUT;
   const int nc = lo ? nr - Sh::NOUT : nr;
-  const float s = scale[0];
+  const int g = b2_global_exp(scale);
   __align__(16) uint8_t h[16];
 #pragma unroll
   for (int k = 0; k < 16; ++k) {
@@ -592,13 +629,32 @@ __global__ void pack_b2_kernel(const float2* __restrict__ V, int64_t n, int r, i
       float2 v = V[ig * r + jj];
       const float br = tb.beta_r[gc], bi = tb.beta_i[gc];
       // beta conj(V) = (br vr + bi vi) + i (bi vr - br vi)
-      val = s * ((nc & 1) ? fmaf(bi, v.x, -br * v.y) : fmaf(br, v.x, bi * v.y));
+      val = ldexpf((nc & 1) ? fmaf(bi, v.x, -br * v.y) : fmaf(br, v.x, bi * v.y), b2_coord_exp(V, ig, r, g));
     }
     const __nv_fp8_e4m3 hi(val);
     h[k] = lo ? __nv_fp8_e4m3(val - static_cast<float>(hi)).__x : hi.__x;
   }
   *reinterpret_cast<uint4*>(tiles + t * L::TILE_BYTES + L::B2_OFF_IN_STAGE + within * 16) =
       *reinterpret_cast<uint4*>(h);
+}
+
+// Indicator magnitudes 2^(g - e_i) as E4M3 bytes, four coordinates per word
+// (lowest coordinate in the lowest byte), R / 4 words per tile; 0 past n.
+__global__ void pack_indicator_scale_kernel(const float2* __restrict__ V, int64_t n, int r, int64_t words,
+                                            const float* __restrict__ scale, uint32_t* __restrict__ iw) {
+  const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (q >= words) return;
+  const int g = b2_global_exp(scale);
+  uint32_t w = 0;
+  for (int c = 0; c < 4; ++c) {
+    const int64_t ig = q * 4 + c;
+    if (ig >= n) continue;
+    const int d = g - b2_coord_exp(V, ig, r, g);  // in [-9, 0]
+    // E4M3 2^d: normal ((d + 7) << 3) down to 2^-6, subnormal 0x4 >> (-7 - d) below
+    const uint32_t code = d >= -6 ? static_cast<uint32_t>(d + 7) << 3 : (0x4u >> (-7 - d));
+    w |= code << (8 * c);
+  }
+  iw[q] = w;
 }
 
 // directions: candidate tile ct, chunk ch, row s: slots [Re c, Im c, 0...]
@@ -642,7 +698,7 @@ static PackTables make_pack_tables(const Alphabet& a) {
 
 template <int K, int KCH>
 static int pack_impl(const ScorePlan& p, const Alphabet& a, const float2* V, const float2* C, void* tiles,
-                     void* ct, float* scale, cudaStream_t st) {
+                     void* ct, float* scale, uint32_t* iw, cudaStream_t st) {
   using Sh = TcShape<K, KCH>;
   using L = TcLayout<K, KCH>;
   PackTables tb = make_pack_tables(a);
@@ -660,7 +716,10 @@ static int pack_impl(const ScorePlan& p, const Alphabet& a, const float2* V, con
   int64_t nb = p.n_tiles * L::B2ROWS;
   pack_b2_kernel<K, KCH><<<static_cast<unsigned>(ceil_div(nb, 256)), 256, 0, st>>>(
       V, p.n, p.r, p.n_tiles, tb, scale, static_cast<uint8_t*>(tiles));
-  count_launch();
+  const int64_t words = p.n_tiles * (Sh::ROWS / 4);
+  pack_indicator_scale_kernel<<<static_cast<unsigned>(ceil_div(words, 256)), 256, 0, st>>>(V, p.n, p.r, words, scale,
+                                                                                          iw);
+  count_launch(2);
   int64_t nc = p.c_tiles * kTcM;
   pack_dirs_kernel<KCH><<<static_cast<unsigned>(ceil_div(nc, 256)), 256, 0, st>>>(C, p.S, p.r, p.c_tiles,
                                                                                   static_cast<__nv_bfloat16*>(ct));
@@ -712,8 +771,8 @@ static int make_rows_map(CUtensorMap* map, const void* base, size_t total_bytes,
 }
 
 template <int K, int KCH>
-static int score_impl(const ScorePlan& p, const void* tiles, const void* ct, const float* scale, double* partial,
-                      int32_t* status, cudaStream_t st) {
+static int score_impl(const ScorePlan& p, const void* tiles, const void* ct, const float* scale,
+                      const uint32_t* iw, double* partial, int32_t* status, cudaStream_t st) {
   using Sh = TcShape<K, KCH>;
   using L = TcLayout<K, KCH>;
   CUtensorMap m_vt, m_ct;
@@ -735,7 +794,7 @@ static int score_impl(const ScorePlan& p, const void* tiles, const void* ct, con
   prm.r = p.r;
   prm.flush = kTcFlush;
   int grid = static_cast<int>(std::min<int64_t>(ceil_div(prm.num_items, Sh::NW), num_sms_current()));
-  score_tc_kernel<K, KCH><<<grid, Sh::THREADS, L::TOTAL, st>>>(m_vt, m_ct, prm, scale, partial, status);
+  score_tc_kernel<K, KCH><<<grid, Sh::THREADS, L::TOTAL, st>>>(m_vt, m_ct, prm, scale, iw, partial, status);
   count_launch();
   return cuda_check(cudaGetLastError(), "score_tc_kernel");
 }
@@ -775,6 +834,10 @@ size_t tc_bytes_tiles(int K, int r, int64_t n_tiles) {
 #undef LRQ_TILE
 }
 
+size_t tc_bytes_indicator_scale(int K, int64_t n_tiles) {
+  return static_cast<size_t>(n_tiles) * static_cast<size_t>(tc_rows_per_tile(K));  // one byte per coordinate
+}
+
 size_t tc_bytes_dirs(int r, int64_t c_tiles) {
   int kch = r <= 4 ? 1 : 2;
   return static_cast<size_t>(c_tiles) * kch * kTcM * 16;
@@ -796,14 +859,15 @@ size_t tc_bytes_dirs(int r, int64_t c_tiles) {
   } while (0)
 
 int launch_tc_pack(const ScorePlan& p, const Alphabet& a, const float2* V, const float2* C, void* tiles, void* ct,
-                   void* scale, cudaStream_t st) {
-  LRQ_TC_DISPATCH(pack_impl, p, a, V, C, tiles, ct, static_cast<float*>(scale), st);
+                   void* scale, void* iw, cudaStream_t st) {
+  LRQ_TC_DISPATCH(pack_impl, p, a, V, C, tiles, ct, static_cast<float*>(scale), static_cast<uint32_t*>(iw), st);
 }
 
 int launch_score_tc(const ScorePlan& p, const Alphabet& a, const void* tiles, const void* ct, const void* scale,
-                    double* partial, int32_t* status, cudaStream_t st) {
+                    const void* iw, double* partial, int32_t* status, cudaStream_t st) {
   (void)a;
-  LRQ_TC_DISPATCH(score_impl, p, tiles, ct, static_cast<const float*>(scale), partial, status, st);
+  LRQ_TC_DISPATCH(score_impl, p, tiles, ct, static_cast<const float*>(scale), static_cast<const uint32_t*>(iw),
+                  partial, status, st);
 }
 
 }  // namespace lrq

@@ -20,6 +20,7 @@ namespace lrq {
 int tc_rows_per_tile(int K);
 int tc_workers_per_cta(int K, int r);
 size_t tc_bytes_tiles(int K, int r, int64_t n_tiles);
+size_t tc_bytes_indicator_scale(int K, int64_t n_tiles);
 size_t tc_bytes_dirs(int r, int64_t c_tiles);
 
 static thread_local char g_last_error[512] = {0};
@@ -162,6 +163,8 @@ int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_
     p->off_ct = take(cur, p->sz_ct);
     p->sz_scale = 4 * sizeof(float);
     p->off_scale = take(cur, p->sz_scale);
+    p->sz_iw = tc_bytes_indicator_scale(K, p->n_tiles);
+    p->off_iw = take(cur, p->sz_iw);
   }
   p->sz_scores = static_cast<size_t>(S) * sizeof(float);
   p->off_scores = take(cur, p->sz_scores);
@@ -281,9 +284,12 @@ int lrq_sample_score(const void* V, int64_t n, int r, int K, void* C, int genera
       if ((e = launch_colsum(Vf, n, r, reinterpret_cast<double*>(w + p.off_Tpart), T, nb, st))) return e;
       Tuse = T;
     }
-    if ((e = launch_tc_pack(p, a, Vf, Cf, w + p.off_tiles, w + p.off_ct, w + p.off_scale, st))) return e;
+    if ((e = launch_tc_pack(p, a, Vf, Cf, w + p.off_tiles, w + p.off_ct, w + p.off_scale, w + p.off_iw, st)))
+      return e;
     timing_start(st);
-    if ((e = launch_score_tc(p, a, w + p.off_tiles, w + p.off_ct, w + p.off_scale, partial, dev_status, st))) return e;
+    if ((e = launch_score_tc(p, a, w + p.off_tiles, w + p.off_ct, w + p.off_scale, w + p.off_iw, partial, dev_status,
+                             st)))
+      return e;
     timing_stop(st);
   } else {
     timing_start(st);

@@ -65,7 +65,8 @@ struct ScorePlan {
   size_t off_Tpart, sz_Tpart;       // per-block partial column sums
   size_t off_tiles, sz_tiles;       // packed coordinate tiles: augmented rows (bf16) | class rows (FP8 hi | lo)
   size_t off_ct, sz_ct;             // packed directions (bf16)
-  size_t off_scale, sz_scale;       // GEMM2 operand scale {s, 1/s, max|V|}
+  size_t off_scale, sz_scale;       // GEMM2 operand scale {2^g, 2^-g, max|V component|}
+  size_t off_iw, sz_iw;             // per-coordinate indicator magnitudes (E4M3, 1 byte per coordinate)
   size_t off_scores, sz_scores;     // S floats (when the caller passes none)
   size_t off_keys, sz_keys;         // selection keys
   size_t total;
@@ -147,9 +148,9 @@ int launch_enumerate(const double2* V, int64_t n, int r, int K, uint8_t* z_out, 
                      void* ws, int32_t* status, cudaStream_t st);
 // tensor-core path
 int launch_tc_pack(const ScorePlan& p, const Alphabet& a, const float2* V, const float2* C, void* tiles, void* ct,
-                   void* scale, cudaStream_t st);
+                   void* scale, void* iw, cudaStream_t st);
 int launch_score_tc(const ScorePlan& p, const Alphabet& a, const void* tiles, const void* ct, const void* scale,
-                    double* partial, int32_t* status, cudaStream_t st);
+                    const void* iw, double* partial, int32_t* status, cudaStream_t st);
 
 __host__ __device__ inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 __host__ __device__ inline int64_t ceil_div(int64_t a, int64_t b) { return (a + b - 1) / b; }

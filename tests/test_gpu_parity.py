@@ -126,11 +126,13 @@ def _bf16_bound(V, K, C):
     factor-2 margin as e_i = 2^-6 sum_j |V_ij|_1 |c_j|_1); a code can differ
     from the FP64 decision only where |w_i| sin(margin_i) <= e_i.  Each such
     coordinate moves ||V^H z|| by at most 2 sin(pi/K) |V_i|.  GEMM2 scales
-    beta_g conj(V_i) by s = 2^(5 - ilogb(a)), a = max |Re V|, |Im V|, and
-    stores it as a hi + lo pair of E4M3 numbers (3-bit significands): a
-    component carries at most 2^-4 * 2^-4 = 2^-8 relative error, plus half an
-    E4M3 subnormal step, 2^-10 / s <= 2^-15 a, where the remainder is tiny;
-    so at most 2^-8 sqrt(2) max|beta| |V_i| + sqrt(2) 2^-15 a per coordinate.
+    the row beta_g conj(V_i) by a power of two chosen per coordinate (its
+    indicator carries the inverse, at most 2^9 above the scale of the largest
+    row, a = max |Re V|, |Im V|) and stores it as a hi + lo pair of E4M3
+    numbers (3-bit significands): a component carries at most
+    2^-4 * 2^-4 = 2^-8 relative error, plus half an E4M3 subnormal step,
+    below 2^-15 a, where the remainder or the row is tiny; so at most
+    2^-8 sqrt(2) max|beta| |V_i| + sqrt(2) 2^-15 a per coordinate.
     FP32 accumulation adds < 1e-5 relative."""
     V = V.astype(np.complex128)
     C = C.astype(np.complex128)
