@@ -8,8 +8,10 @@
 //
 // Method (the paper calls ARPACK; this is a Lanczos of our own design):
 //   * Lanczos with full reorthogonalisation: after w = Q u_j, w is projected
-//     off every stored vector twice (classical Gram-Schmidt applied twice),
-//     alpha_j = u_j^H Q u_j is the sum of the two projections onto u_j, and
+//     off u_j and u_{j-1} (the three-term step, which removes its large
+//     components) and then off every stored vector (one classical
+//     Gram-Schmidt pass over components of rounding size); alpha_j =
+//     u_j^H Q u_j is the sum of the two projections onto u_j, and
 //     beta_j = ||w||.  The tridiagonal T_J is real for Hermitian Q.
 //   * Convergence: eigenvalues of T_J by multisection on Sturm counts, their
 //     eigenvectors by inverse iteration (Gaussian elimination with partial
@@ -698,15 +700,16 @@ struct LzRun {
 
   void matvec(const T* x, T* y) const;
 
-  // w -= U[:, :nc] (U[:, :nc]^H w), projections into h
-  void project(int nc, T* h) const {
+  // w -= U[:, first:first+nc] (U[:, first:first+nc]^H w), projections into
+  // h[first:first+nc]
+  void project(int first, int nc, T* h) const {
     if (nc <= 0) return;
     dim3 g(p.nch, static_cast<unsigned>(ceil_div(nc, kLzGroup)));
-    lz_dots<T><<<g, kLzThreads, 0, st>>>(U(), n, nc, w(), part(), p.nch, p.chunk, state());
+    lz_dots<T><<<g, kLzThreads, 0, st>>>(col(first), n, nc, w(), part(), p.nch, p.chunk, state());
     lz_reduce<T><<<static_cast<unsigned>(ceil_div(static_cast<int64_t>(nc) * 32, 256)), 256, 0, st>>>(
-        part(), nc, p.nch, h, state());
+        part(), nc, p.nch, h + first, state());
     lz_update<T><<<static_cast<unsigned>(std::min<int64_t>(ceil_div(n, 32), 152 * 16)), kLzThreads, 0, st>>>(
-        U(), n, nc, h, w(), state());
+        col(first), n, nc, h + first, w(), state());
     count_launch(3);
   }
   // normalise w into column c; mode 0 closes Lanczos step j (column c - 1)
@@ -734,14 +737,21 @@ struct LzRun {
     if (e) return e;
     lz_start<T><<<lz_rows_grid(n), kLzThreads, 0, st>>>(w(), n, seed, run_id, state());
     count_launch();
-    project(L, h1());
-    project(L, h2());
+    project(0, L, h1());
+    project(0, L, h2());
     close(L, 0, 1);
     for (int j = 0; j < p.maxit && L + j < n; ++j) {
       const int c = L + j;
       matvec(col(c), w());
-      project(c + 1, h1());
-      project(c + 1, h2());
+      // the three-term step: the large components of w = Q u_j lie along u_j
+      // and u_{j-1}; taking them out first leaves components of rounding size
+      // along every other stored vector, which one full Gram-Schmidt pass then
+      // removes (alpha_j = h1[c] + h2[c])
+      if (j > 0)
+        project(c - 1, 2, h1());
+      else
+        project(c, 1, h1());
+      project(0, c + 1, h2());
       close(c + 1, j, 0);
       ++*steps;
       const int J = j + 1;
