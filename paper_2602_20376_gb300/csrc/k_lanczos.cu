@@ -117,39 +117,51 @@ struct LzCheck {
 // ---------------------------------------------------------------------------
 // operators
 // ---------------------------------------------------------------------------
-// y = L x for L = D - A: 8 lanes per row, 4 rows per warp.  Reads are
-// bounds-guarded so that a malformed CSR cannot read outside its arrays
-// (lz_check_csr reports it through the status word).
+// y = L x = D x - A x for the graph Laplacian, a thread per row: the
+// weighted degrees D are precomputed (lz_degree), so a row costs one FP64
+// add or FMA per stored edge (GB300's FP64 rate, not memory, bounds this
+// operator).  Self loops are skipped, out-of-range columns ignored (they are
+// reported by lz_check_csr).
 __global__ void __launch_bounds__(kLzThreads) lz_matvec_laplacian(const int32_t* __restrict__ rowptr,
                                                                   const int32_t* __restrict__ colidx,
-                                                                  const double* __restrict__ wts, int64_t n,
+                                                                  const double* __restrict__ wts,
+                                                                  const double* __restrict__ deg, int64_t n,
                                                                   int64_t nnz, const double* __restrict__ x,
                                                                   double* __restrict__ y, const LzState* st) {
   if (st->stop) return;
-  const int lane = threadIdx.x & 31, sub = lane & 7;
-  const int64_t warp = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = static_cast<int64_t>(gridDim.x) * (blockDim.x >> 5);
-  for (int64_t rb = warp * 4; rb < n; rb += nwarps * 4) {  // warp-uniform trip count
-    const int64_t i = rb + (lane >> 3);
-    double deg = 0.0, acc = 0.0;
-    if (i < n) {
-      int64_t k0 = rowptr[i], k1 = rowptr[i + 1];
-      k0 = k0 < 0 ? 0 : (k0 > nnz ? nnz : k0);
-      k1 = k1 < k0 ? k0 : (k1 > nnz ? nnz : k1);
-      for (int64_t k = k0 + sub; k < k1; k += 8) {
-        const int32_t j = colidx[k];
-        if (j < 0 || j >= n || j == i) continue;
-        const double wk = wts ? wts[k] : 1.0;
-        deg += wk;
-        acc = fma(wk, x[j], acc);
-      }
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    int64_t k0 = rowptr[i], k1 = rowptr[i + 1];
+    k0 = k0 < 0 ? 0 : (k0 > nnz ? nnz : k0);
+    k1 = k1 < k0 ? k0 : (k1 > nnz ? nnz : k1);
+    double acc = 0.0;
+    for (int64_t k = k0; k < k1; ++k) {
+      const int32_t j = colidx[k];
+      if (j < 0 || j >= n || j == i) continue;
+      acc = wts ? fma(wts[k], x[j], acc) : acc + x[j];
     }
-#pragma unroll
-    for (int m = 4; m > 0; m >>= 1) {
-      deg += __shfl_xor_sync(0xffffffffu, deg, m);
-      acc += __shfl_xor_sync(0xffffffffu, acc, m);
+    y[i] = fma(deg[i], x[i], -acc);
+  }
+}
+
+// deg[i] = sum of the row's edge weights (self loops and invalid columns
+// skipped), once per truncation
+__global__ void __launch_bounds__(kLzThreads) lz_degree(const int32_t* __restrict__ rowptr,
+                                                        const int32_t* __restrict__ colidx,
+                                                        const double* __restrict__ wts, int64_t n, int64_t nnz,
+                                                        double* __restrict__ deg) {
+  const int64_t stride = static_cast<int64_t>(gridDim.x) * blockDim.x;
+  for (int64_t i = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n; i += stride) {
+    int64_t k0 = rowptr[i], k1 = rowptr[i + 1];
+    k0 = k0 < 0 ? 0 : (k0 > nnz ? nnz : k0);
+    k1 = k1 < k0 ? k0 : (k1 > nnz ? nnz : k1);
+    double d = 0.0;
+    for (int64_t k = k0; k < k1; ++k) {
+      const int32_t j = colidx[k];
+      if (j < 0 || j >= n || j == i) continue;
+      d += wts ? wts[k] : 1.0;
     }
-    if (sub == 0 && i < n) y[i] = fma(deg, x[i], -acc);
+    deg[i] = d;
   }
 }
 
@@ -291,9 +303,13 @@ template <typename T>
 __global__ void lz_finish(const double* __restrict__ npart, int nch, const T* __restrict__ h1,
                           const T* __restrict__ h2, int c, int j, int mode, double* __restrict__ alpha,
                           double* __restrict__ beta, LzState* st) {
-  if (threadIdx.x != 0 || blockIdx.x != 0 || st->stop) return;
+  if (blockIdx.x != 0 || st->stop) return;
+  // the chunk norms, lane-strided then a fixed shuffle tree (deterministic)
   double s = 0.0;
-  for (int k = 0; k < nch; ++k) s += npart[k];
+  for (int k = threadIdx.x; k < nch; k += 32) s += npart[k];
+#pragma unroll
+  for (int m = 16; m > 0; m >>= 1) s += __shfl_xor_sync(0xffffffffu, s, m);
+  if (threadIdx.x != 0) return;
   const double b = sqrt(s);
   if (mode == 1) {
     // start vector: b is its norm after projection; a zero vector means the
@@ -624,7 +640,7 @@ struct LzPlan {
   int r, maxit, lmax, cap, nch, chunk, ldx;
   size_t esz;
   size_t off_U, off_w, off_Y, off_part, off_h1, off_h2, off_npart, off_alpha, off_beta, off_state, off_check, off_X,
-      off_work, total;
+      off_work, off_deg, total;
 };
 
 size_t lz_take(size_t& cur, size_t bytes) {
@@ -659,6 +675,7 @@ void lz_plan(int64_t n, int r, int maxit, bool cplx, LzPlan* p) {
   p->off_check = lz_take(cur, sizeof(LzCheck));
   p->off_X = lz_take(cur, static_cast<size_t>(kLzWant) * p->ldx * sizeof(double));
   p->off_work = lz_take(cur, static_cast<size_t>(kLzWant) * 5 * p->ldx * sizeof(double));
+  p->off_deg = lz_take(cur, cplx ? 0 : static_cast<size_t>(n) * sizeof(double));  // Laplacian degrees
   p->total = cur;
 }
 
@@ -697,8 +714,10 @@ struct LzRun {
   LzCheck* check() const { return reinterpret_cast<LzCheck*>(ws + p.off_check); }
   double* X() const { return reinterpret_cast<double*>(ws + p.off_X); }
   double* work() const { return reinterpret_cast<double*>(ws + p.off_work); }
+  double* deg() const { return reinterpret_cast<double*>(ws + p.off_deg); }
 
   void matvec(const T* x, T* y) const;
+  void prepare() const;  // operator set-up once per truncation (Laplacian degrees)
 
   // w -= U[:, first:first+nc] (U[:, first:first+nc]^H w), projections into
   // h[first:first+nc]
@@ -780,6 +799,7 @@ struct LzRun {
     bool verify = false;
     double tn = 0.0;
     int e;
+    prepare();
     while (L < n) {
       if (!verify && L >= r) verify = true;
       const int p_want = verify ? 1 : static_cast<int>(std::min<int64_t>(r - L, n - L));
@@ -839,10 +859,18 @@ struct LzRun {
 
 template <>
 void LzRun<double>::matvec(const double* x, double* y) const {
-  const int blocks = static_cast<int>(std::max<int64_t>(1, std::min<int64_t>(ceil_div(n, 32), 152 * 16)));
-  lz_matvec_laplacian<<<blocks, kLzThreads, 0, st>>>(rowptr, colidx, wts, n, nnz, x, y, state());
+  lz_matvec_laplacian<<<lz_rows_grid(n), kLzThreads, 0, st>>>(rowptr, colidx, wts, deg(), n, nnz, x, y, state());
   count_launch();
 }
+
+template <>
+void LzRun<double>::prepare() const {
+  lz_degree<<<lz_rows_grid(n), kLzThreads, 0, st>>>(rowptr, colidx, wts, n, nnz, deg());
+  count_launch();
+}
+
+template <>
+void LzRun<double2>::prepare() const {}
 
 template <>
 void LzRun<double2>::matvec(const double2* x, double2* y) const {
