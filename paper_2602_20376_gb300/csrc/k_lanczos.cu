@@ -46,6 +46,7 @@ constexpr int kLzGroup = 8;        // basis vectors per block in the projection 
 constexpr int kLzWant = kMaxRank;  // at most 8 wanted pairs per run
 constexpr int kLzMaxIter = 4096;
 constexpr int kLzDefaultIter = 500;
+constexpr int kLzLag = 2;          // Lanczos steps run while a convergence check is in flight
 
 // ---------------------------------------------------------------------------
 // scalar helpers: real (graph Laplacian) and complex (dense Hermitian) paths
@@ -640,7 +641,7 @@ struct LzPlan {
   int r, maxit, lmax, cap, nch, chunk, ldx;
   size_t esz;
   size_t off_U, off_w, off_Y, off_part, off_h1, off_h2, off_npart, off_alpha, off_beta, off_state, off_check, off_X,
-      off_work, off_deg, total;
+      off_work, off_deg, off_snap, total;
 };
 
 size_t lz_take(size_t& cur, size_t bytes) {
@@ -676,6 +677,7 @@ void lz_plan(int64_t n, int r, int maxit, bool cplx, LzPlan* p) {
   p->off_X = lz_take(cur, static_cast<size_t>(kLzWant) * p->ldx * sizeof(double));
   p->off_work = lz_take(cur, static_cast<size_t>(kLzWant) * 5 * p->ldx * sizeof(double));
   p->off_deg = lz_take(cur, cplx ? 0 : static_cast<size_t>(n) * sizeof(double));  // Laplacian degrees
+  p->off_snap = lz_take(cur, sizeof(LzState));  // the state a convergence check reads
   p->total = cur;
 }
 
@@ -699,6 +701,9 @@ struct LzRun {
   uint8_t* ws;
   int32_t* status;
   cudaStream_t st;
+  cudaStream_t side;  // convergence checks run here, beside the next Lanczos steps
+  cudaEvent_t ev;     // step done (the check waits for it)
+  cudaEvent_t done;   // check done (the host polls it)
 
   T* U() const { return reinterpret_cast<T*>(ws + p.off_U); }
   T* col(int c) const { return U() + static_cast<int64_t>(c) * n; }
@@ -715,6 +720,7 @@ struct LzRun {
   double* X() const { return reinterpret_cast<double*>(ws + p.off_X); }
   double* work() const { return reinterpret_cast<double*>(ws + p.off_work); }
   double* deg() const { return reinterpret_cast<double*>(ws + p.off_deg); }
+  LzState* snap() const { return reinterpret_cast<LzState*>(ws + p.off_snap); }
 
   void matvec(const T* x, T* y) const;
   void prepare() const;  // operator set-up once per truncation (Laplacian degrees)
@@ -738,13 +744,34 @@ struct LzRun {
     lz_scale_into<T><<<lz_rows_grid(n), kLzThreads, 0, st>>>(w(), n, col(c), state());
     count_launch(3);
   }
-  int sync_check(LzCheck* hc) const {
-    int32_t hs = 0;
-    int e = cuda_check(cudaMemcpyAsync(hc, check(), sizeof(LzCheck), cudaMemcpyDeviceToHost, st), "copy check");
+  // A convergence check reads alpha, beta and a snapshot of the state of
+  // step J and runs on the side stream, so the next Lanczos steps (which
+  // only append to alpha, beta and the basis) proceed meanwhile; its verdict
+  // is read kLzLag steps later: the host waits for it with those steps
+  // queued, so the GPU is not left idle and at most kLzLag steps run past
+  // convergence.
+  int launch_check(int p_want) const {
+    int e = cuda_check(cudaMemcpyAsync(snap(), state(), sizeof(LzState), cudaMemcpyDeviceToDevice, st),
+                       "snapshot state");
     if (e) return e;
-    if ((e = cuda_check(cudaMemcpyAsync(&hs, status, sizeof(int32_t), cudaMemcpyDeviceToHost, st), "copy status")))
+    if ((e = cuda_check(cudaEventRecord(ev, st), "record step event"))) return e;
+    if ((e = cuda_check(cudaStreamWaitEvent(side, ev, 0), "order check after step"))) return e;
+    lz_tridiag<<<1, 256, 0, side>>>(alpha(), beta(), p_want, tol, p.ldx, X(), work(), snap(), check());
+    count_launch();
+    if ((e = cuda_check(cudaGetLastError(), "lz_tridiag"))) return e;
+    return cuda_check(cudaEventRecord(done, side), "record check event");
+  }
+  int finish_check(LzCheck* hc) const {
+    int32_t hs = 0;
+    int e = cuda_check(cudaEventSynchronize(done), "wait for the check");
+    if (e) return e;
+    if ((e = cuda_check(cudaMemcpyAsync(hc, check(), sizeof(LzCheck), cudaMemcpyDeviceToHost, side), "copy check")))
       return e;
-    if ((e = cuda_check(cudaStreamSynchronize(st), "lanczos sync"))) return e;
+    if (e) return e;
+    if ((e = cuda_check(cudaMemcpyAsync(&hs, status, sizeof(int32_t), cudaMemcpyDeviceToHost, side),
+                        "copy status")))
+      return e;
+    if ((e = cuda_check(cudaStreamSynchronize(side), "lanczos sync"))) return e;
     if (hs != 0) return fail(hs, "lrq_truncate: the device reported an invalid input or error");
     return LRQ_OK;
   }
@@ -759,6 +786,16 @@ struct LzRun {
     project(0, L, h1());
     project(0, L, h2());
     close(L, 0, 1);
+    int pending = 0, since = 0;  // a check in flight, and steps taken since it started
+    // the verdict of the check in flight: 1 = this run is over, 0 = go on
+    auto verdict = [&](int* over) -> int {
+      pending = 0;
+      int e2 = finish_check(hc);
+      if (e2) return e2;
+      if (hc->breakdown == 2) hc->nvalid = 0;  // the start vector had no part outside the locked space
+      *over = hc->breakdown || hc->converged || L + hc->J >= n;
+      return LRQ_OK;
+    };
     for (int j = 0; j < p.maxit && L + j < n; ++j) {
       const int c = L + j;
       matvec(col(c), w());
@@ -773,20 +810,25 @@ struct LzRun {
       project(0, c + 1, h2());
       close(c + 1, j, 0);
       ++*steps;
+      ++since;
       const int J = j + 1;
       const bool last = J == p.maxit || L + J >= n;
       const int every = J < 16 ? 2 : (J < 64 ? 4 : 8);
-      if ((J >= p_want && J % every == 0) || last) {
-        lz_tridiag<<<1, 256, 0, st>>>(alpha(), beta(), p_want, tol, p.ldx, X(), work(), state(), check());
-        count_launch();
-        if ((e = cuda_check(cudaGetLastError(), "lanczos kernels"))) return e;
-        if ((e = sync_check(hc))) return e;
-        if (hc->breakdown == 2) {  // the start vector had no part outside the locked space
-          hc->nvalid = 0;
-          return LRQ_OK;
-        }
-        if (hc->converged || hc->breakdown || L + hc->J >= n) return LRQ_OK;
-        if (last) return fail(LRQ_ENOCONV, "lrq_truncate: Lanczos did not converge within max_iter steps");
+      const bool due = J >= p_want && J % every == 0;
+      int over = 0;
+      if (pending && (due || last || since >= kLzLag)) {
+        if ((e = verdict(&over))) return e;
+        if (over) return LRQ_OK;
+      }
+      if (due || last) {
+        if ((e = launch_check(p_want))) return e;
+        pending = J;
+        since = 0;
+      }
+      if (last) {
+        if ((e = verdict(&over))) return e;
+        if (over) return LRQ_OK;
+        return fail(LRQ_ENOCONV, "lrq_truncate: Lanczos did not converge within max_iter steps");
       }
     }
     return fail(LRQ_ENOCONV, "lrq_truncate: Lanczos did not converge within max_iter steps");
@@ -907,10 +949,33 @@ size_t truncate_workspace_bytes(const lrq_matrix* Q, int r, int max_iter) {
   return p.total;
 }
 
+namespace {
+// the side stream and event of one truncation call, released on every path
+struct LzSide {
+  cudaStream_t side = nullptr;
+  cudaEvent_t ev = nullptr, done = nullptr;
+  int init() {
+    int e = cuda_check(cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking), "create check stream");
+    if (e) return e;
+    if ((e = cuda_check(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming), "create step event"))) return e;
+    return cuda_check(cudaEventCreateWithFlags(&done, cudaEventDisableTiming), "create check event");
+  }
+  ~LzSide() {
+    if (side) cudaStreamSynchronize(side);
+    if (done) cudaEventDestroy(done);
+    if (ev) cudaEventDestroy(ev);
+    if (side) cudaStreamDestroy(side);
+  }
+};
+}  // namespace
+
 int launch_truncate(const lrq_matrix* Q, int r, double tol, int max_iter, uint64_t seed, double2* V, float2* V32,
                     double* lambda_out, int64_t* iters_out, void* ws, int32_t* status, cudaStream_t st) {
   const int it = static_cast<int>(std::min<int64_t>(max_iter > 0 ? max_iter : kLzDefaultIter, Q->n));
   const double t = tol > 0.0 ? tol : 1e-10;
+  LzSide sd;
+  int e = sd.init();
+  if (e) return e;
   if (Q->kind == LRQ_MATRIX_DENSE_C128) {
     LzRun<double2> R;
     R.dense = true;
@@ -927,6 +992,9 @@ int launch_truncate(const lrq_matrix* Q, int r, double tol, int max_iter, uint64
     R.ws = static_cast<uint8_t*>(ws);
     R.status = status;
     R.st = st;
+    R.side = sd.side;
+    R.ev = sd.ev;
+    R.done = sd.done;
     lz_check_dense<<<lz_rows_grid(Q->n * Q->n), kLzThreads, 0, st>>>(R.Q, Q->n, Q->ld, status);
     count_launch();
     return R.solve(r, lambda_out, V, V32, iters_out);
@@ -946,6 +1014,9 @@ int launch_truncate(const lrq_matrix* Q, int r, double tol, int max_iter, uint64
   R.ws = static_cast<uint8_t*>(ws);
   R.status = status;
   R.st = st;
+  R.side = sd.side;
+  R.ev = sd.ev;
+  R.done = sd.done;
   lz_check_csr<<<lz_rows_grid(std::max<int64_t>(Q->n, Q->nnz)), kLzThreads, 0, st>>>(Q->rowptr, Q->colidx,
                                                                                      Q->weights, Q->n, Q->nnz,
                                                                                      status);
