@@ -191,6 +191,29 @@ def test_score_bf16_best_of_s_in_top_m(lrq):
         assert best in set(idx.tolist())
 
 
+@pytest.mark.parametrize("K", [3, 4])
+def test_score_bf16_heavy_tailed_rows(lrq, K):
+    # rows spread over ten orders of magnitude, as in the localised top
+    # eigenvectors of a sparse graph's Laplacian: the GEMM2 operand is scaled
+    # per coordinate, so small rows keep their relative precision, rows more
+    # than 2^9 below the largest are clamped (their share of the sums is
+    # below the bound's floor term), and zero rows stay exact
+    n, r, S = 6000, 3, 512
+    V = I.factor(n, r, seed=90 + K, dtype=np.complex64)
+    g = I.rng(91)
+    mag = 10.0 ** g.uniform(-6.0, 4.0, n)
+    V = (V * mag[:, None]).astype(np.complex64)
+    V[g.choice(n, 30, replace=False)] = 0
+    C = I.directions(S, r, seed=92)
+    out = _score(lrq, V, K, C, BF16, 8)
+    f = out["scores"].cpu().numpy().astype(np.float64)
+    ref = O.score(V, K, C)
+    bound = _bf16_bound(V, K, C) + 1e-5 * np.sqrt(ref)
+    dev = np.abs(np.sqrt(f) - np.sqrt(ref))
+    assert np.all(dev <= bound), (np.max(dev / bound), np.argmax(dev / bound))
+    assert np.median(np.abs(f - ref) / ref) < 3e-3
+
+
 def test_score_bf16_many_chunks(lrq):
     # long coordinate axis: several accumulation periods and chunks per item
     _check_bf16(lrq, 200000, 4, 3, 256, 16)
