@@ -58,7 +58,7 @@ typedef enum {
 
 typedef enum {
   LRQ_MODE_FP32 = 0,     /* CUDA-core FP32 scoring                                      */
-  LRQ_MODE_BF16_TC = 1   /* tcgen05 tensor-core scoring: BF16 / FP8 x2 operands, FP32 accumulate */
+  LRQ_MODE_BF16_TC = 1   /* tcgen05 tensor-core scoring: F16 signs, FP8 x2 class sums, FP32 accumulate */
 } lrq_mode;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -139,13 +139,15 @@ int lrq_sample_null_directions(const void* V, int64_t n, int r, int K, uint64_t 
  *              otherwise C is read as given (rows need not be unit norm).
  *   S        : number of candidates, S >= 1, S < 2^31.
  *   mode     : LRQ_MODE_FP32 or LRQ_MODE_BF16_TC.  The tensor-core mode
- *              rounds the operands of w = V c to bfloat16, and those of the
- *              per-class sums of V^H z to a hi + lo pair of FP8 E4M3
- *              numbers after scaling by a power of two (about bfloat16's
- *              precision; the class indicators are exact); it accumulates
- *              in FP32 (partial sums are combined in FP64) and supports
- *              K <= 8 and r <= 8.  FP32 mode computes w and V^H z in FP32
- *              with FP64 partials.
+ *              computes the sector signs from w = V c in F16 (operands
+ *              and accumulator; every row of V and every direction scaled
+ *              by a power of two, which changes no sign), and the
+ *              per-class sums of V^H z from a hi + lo pair of FP8 E4M3
+ *              numbers per entry, scaled by a power of two per coordinate
+ *              (about bfloat16's precision; the class indicators are
+ *              exact), accumulated in FP32 and combined in FP64; it
+ *              supports K <= 8 and r <= 8.  FP32 mode computes w and V^H z
+ *              in FP32 with FP64 partials.
  *   top_m    : 1 <= top_m <= 512 and top_m <= S.
  *   scores_out  : optional S floats (device) receiving f_s; may be NULL.
  *   top_idx_out : top_m int64 (device): candidate indices, best first.

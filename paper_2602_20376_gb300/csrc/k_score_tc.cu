@@ -3,21 +3,26 @@
 // The scoring of Sec. 4.2, Eq. 10 is cast as two contractions per
 // (128-candidate tile, coordinate tile):
 //
-// GEMM1 (boundary projections, BF16).  The augmented real matrix of Eq. 6 has
+// GEMM1 (boundary projections, F16).  The augmented real matrix of Eq. 6 has
 // one row per (coordinate i, boundary m): [Im(rho_m V_i), Re(rho_m V_i)] with
 // rho_m = exp(-i theta_m), theta_m = pi(2m+1)/K, m < B_K (Definition 2.1).
 // Against c~ = [Re c; Im c] a row gives p_m = Im(rho_m V_i c), whose sign says
 // on which side of decision boundary m the value w_i = V_i c lies.  So
 //   D1[s, (m, i)] = sum_k C~[s, k] * Vaug[(m, i), k]     (M = 128, K = 2r -> 16)
-// and the decision rule (Sec. 3, Eq. 9) becomes a sign test per row.
+// and the decision rule (Sec. 3, Eq. 9) becomes a sign test per row.  Signs
+// do not change under positive scales, so every coordinate row and every
+// direction is scaled by a power of two (largest component into [1, 2)) and
+// GEMM1 runs in F16 with an F16 accumulator: full range safety, F16's
+// precision, and the projections come back two per register.
 //
 // Sector rounding in the epilogue.  With N_m the sign mask of p_m:
 //   odd K  : class k in 1..K-1 iff p_{k-1} > 0 and p_k < 0  -> indicator 1/0
 //   even K : z = sum_m beta_m sign(p_m), beta_m = (w^{m+1} - w^m)/2   -> +-1
 // (w = exp(2 pi i/K)).  Indicators are exact in FP8 (E4M3 0x38 = 1.0, 0xB8 =
-// -1.0); four coordinates' signs are gathered into one word with byte
-// permutes (sign replication) and turned into indicators with one 3-input
-// logic op -- no trigonometry, no branches.
+// -1.0, times a per-coordinate power of two, see GEMM2); the signs of four
+// coordinates are gathered into one word by one byte permute (sign
+// replication) of two packed F16 registers and turned into indicators with
+// one 3-input logic op -- no trigonometry, no branches.
 //
 // GEMM2 (per-class sums, FP8 x FP8 -> FP32).  V^H z = T + sum_k (w^k - 1) P_k
 // (odd K, T the column sum of conj(V)) or sum_m beta_m S_m (even K), where
@@ -49,6 +54,7 @@
 // returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -165,12 +171,6 @@ __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volati
   return __shfl_sync(0xffffffffu, ok, 0) != 0;
 }
 
-// signs of four FP32 values as bytes (0xFF where negative): the top byte of
-// each is gathered, then its sign bit replicated
-__device__ __forceinline__ uint32_t sign_bytes4(uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
-  return ptx::prmt(ptx::prmt(a, b, 0x0073u), ptx::prmt(c, d, 0x0073u), 0xDC98u);
-}
-
 // The worker's sequence of tiles: items gw, gw + workers, ... and the tiles of
 // each item in order.
 struct TcCursor {
@@ -277,7 +277,7 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
   const bool issuer = (qtr == 0 && lane == 0);
   const uint32_t lane_base = static_cast<uint32_t>(qtr * 32) << 16;
   const uint32_t tw = tmem + w * Sh::WCOLS;  // this worker's TMEM slice
-  constexpr uint32_t idesc1 = ptx::idesc_bf16_f32(kTcM, Sh::N1);
+  constexpr uint32_t idesc1 = ptx::idesc_f16_f16(kTcM, Sh::N1);
   constexpr uint32_t idesc2 = ptx::idesc_e4m3_f32(kTcM, Sh::N2);
   constexpr uint32_t lbo_b2 = L::N2R * 16;
   float2* acc = reinterpret_cast<float2*>(wsm + L::W_ACC) + row * 16;  // (hi, lo) per component
@@ -366,46 +366,45 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
     if (!bad) {
       ptx::tc_fence_after();
       uint32_t wv[G * CW];
-      // 16-coordinate chunks read per tensor-memory wait (all when they fit)
-      constexpr int HB = (BKG * R <= 64) ? R / 16 : 1;
+      // D1 holds F16 projections, one per column; a packed load gives two
+      // coordinates per register, so one byte permute gathers the signs of
+      // four coordinates
+      constexpr int RC = R < 32 ? R : 32;  // coordinates per load
 #pragma unroll
-      for (int h0 = 0; h0 < R / 16; h0 += HB) {
-        uint32_t plh[HB][BKG][16];
+      for (int ch = 0; ch < R / RC; ++ch) {
+        uint32_t pl[BKG][RC / 2];
 #pragma unroll
-        for (int hh = 0; hh < HB; ++hh)
-#pragma unroll
-          for (int b = 0; b < BKG; ++b)
-            ptx::tmem_ld_x16(tw + lane_base + Sh::D1_OFF + b * R + (h0 + hh) * 16, plh[hh][b]);
+        for (int b = 0; b < BKG; ++b) {
+          const uint32_t ta = tw + lane_base + Sh::D1_OFF + b * R + ch * RC;
+          if constexpr (RC == 32)
+            ptx::tmem_ld_x16_pack16(ta, *reinterpret_cast<uint32_t(*)[16]>(pl[b]));
+          else
+            ptx::tmem_ld_x8_pack16(ta, *reinterpret_cast<uint32_t(*)[8]>(pl[b]));
+        }
         ptx::tmem_wait_ld();
 #pragma unroll
-        for (int hh = 0; hh < HB; ++hh) {
-        const int h = h0 + hh;
-        uint32_t (&pl)[BKG][16] = plh[hh];
-#pragma unroll
-        for (int p = 0; p < 4; ++p) {
+        for (int p = 0; p < RC / 4; ++p) {
           uint32_t nm[BK];
           if constexpr (K == 3) {
-            // p_1 = -(p_0 + p_2): the three boundary directions sum to zero
-            uint32_t q[4];
-#pragma unroll
-            for (int c = 0; c < 4; ++c)
-              q[c] = __float_as_uint(-(__uint_as_float(pl[0][4 * p + c]) + __uint_as_float(pl[1][4 * p + c])));
-            nm[0] = sign_bytes4(pl[0][4 * p], pl[0][4 * p + 1], pl[0][4 * p + 2], pl[0][4 * p + 3]);
-            nm[1] = sign_bytes4(q[0], q[1], q[2], q[3]);
-            nm[2] = sign_bytes4(pl[1][4 * p], pl[1][4 * p + 1], pl[1][4 * p + 2], pl[1][4 * p + 3]);
+            // p_1 = -(p_0 + p_2): the three boundary directions sum to zero, so
+            // p_1 < 0 exactly where p_0 + p_2 > 0
+            const uint32_t sum_neg = ptx::prmt(ptx::hadd2(pl[0][2 * p], pl[1][2 * p]),
+                                               ptx::hadd2(pl[0][2 * p + 1], pl[1][2 * p + 1]), 0xFDB9u);
+            nm[0] = ptx::prmt(pl[0][2 * p], pl[0][2 * p + 1], 0xFDB9u);
+            nm[1] = ~sum_neg;
+            nm[2] = ptx::prmt(pl[1][2 * p], pl[1][2 * p + 1], 0xFDB9u);
           } else {
 #pragma unroll
-            for (int m = 0; m < BK; ++m)
-              nm[m] = sign_bytes4(pl[m][4 * p], pl[m][4 * p + 1], pl[m][4 * p + 2], pl[m][4 * p + 3]);
+            for (int m = 0; m < BK; ++m) nm[m] = ptx::prmt(pl[m][2 * p], pl[m][2 * p + 1], 0xFDB9u);
           }
+          const int wi = ch * (RC / 4) + p;
 #pragma unroll
           for (int gc = 0; gc < G; ++gc) {
             if constexpr (K % 2 == 1)
-              wv[gc * CW + h * 4 + p] = ~nm[gc] & nm[gc + 1] & mag[h * 4 + p];  // p_{k-1} > 0 and p_k < 0
+              wv[gc * CW + wi] = ~nm[gc] & nm[gc + 1] & mag[wi];  // p_{k-1} > 0 and p_k < 0
             else
-              wv[gc * CW + h * 4 + p] = (nm[gc] & 0x80808080u) | mag[h * 4 + p];  // sign(p_m) as +-1
+              wv[gc * CW + wi] = (nm[gc] & 0x80808080u) | mag[wi];  // sign(p_m) as +-1
           }
-        }
         }
       }
 #pragma unroll
@@ -537,19 +536,28 @@ __global__ void pack_vaug_kernel(const float2* __restrict__ V, int64_t n, int r,
 #pragma unroll
   for (int k = 0; k < 16; ++k) slot[k] = 0.f;
   if (ig < n) {
+    // a row's signs do not change under a positive scale: a power of two
+    // brings its largest component into [1, 2), so every product and the F16
+    // accumulator stay far inside the F16 range and keep its precision
+    float mx = 0.f;
+    for (int jj = 0; jj < r; ++jj) {
+      const float2 v = V[ig * r + jj];
+      mx = fmaxf(mx, fmaxf(fabsf(v.x), fabsf(v.y)));
+    }
+    const int sh = (mx > 0.f && isfinite(mx)) ? -ilogbf(mx) : 0;
     const float bc = tb.bcos[m], bs = tb.bsin[m];
     for (int jj = 0; jj < r; ++jj) {
-      float2 v = V[ig * r + jj];
+      const float2 v = V[ig * r + jj];
       // rho_m V = (bc - i bs)(vr + i vi)
-      slot[jj] = fmaf(bc, v.y, -bs * v.x);     // Im(rho_m V_ij)
-      slot[r + jj] = fmaf(bc, v.x, bs * v.y);  // Re(rho_m V_ij)
+      slot[jj] = ldexpf(fmaf(bc, v.y, -bs * v.x), sh);     // Im(rho_m V_ij)
+      slot[r + jj] = ldexpf(fmaf(bc, v.x, bs * v.y), sh);  // Re(rho_m V_ij)
     }
   }
 #pragma unroll
   for (int ch = 0; ch < KCH; ++ch) {
-    __align__(16) __nv_bfloat16 h[8];
+    __align__(16) __half h[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) h[k] = __float2bfloat16_rn(slot[ch * 8 + k]);
+    for (int k = 0; k < 8; ++k) h[k] = __float2half_rn(slot[ch * 8 + k]);
     *reinterpret_cast<uint4*>(tiles + t * L::TILE_BYTES + (ch * Sh::N1 + rowin) * 16) = *reinterpret_cast<uint4*>(h);
   }
 }
@@ -660,7 +668,7 @@ __global__ void pack_indicator_scale_kernel(const float2* __restrict__ V, int64_
 // directions: candidate tile ct, chunk ch, row s: slots [Re c, Im c, 0...]
 template <int KCH>
 __global__ void pack_dirs_kernel(const float2* __restrict__ C, int64_t S, int r, int64_t c_tiles,
-                                 __nv_bfloat16* __restrict__ ctp) {
+                                 __half* __restrict__ ctp) {
   const int64_t total = c_tiles * kTcM;
   int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= total) return;
@@ -670,17 +678,25 @@ __global__ void pack_dirs_kernel(const float2* __restrict__ C, int64_t S, int r,
 #pragma unroll
   for (int k = 0; k < 16; ++k) slot[k] = 0.f;
   if (q < S) {
+    // a positive power-of-two scale (the largest component into [1, 2))
+    // changes no decision and keeps the F16 products in range
+    float mx = 0.f;
     for (int jj = 0; jj < r; ++jj) {
-      float2 c = C[q * r + jj];
-      slot[jj] = c.x;
-      slot[r + jj] = c.y;
+      const float2 c = C[q * r + jj];
+      mx = fmaxf(mx, fmaxf(fabsf(c.x), fabsf(c.y)));
+    }
+    const int sh = (mx > 0.f && isfinite(mx)) ? -ilogbf(mx) : 0;
+    for (int jj = 0; jj < r; ++jj) {
+      const float2 c = C[q * r + jj];
+      slot[jj] = ldexpf(c.x, sh);
+      slot[r + jj] = ldexpf(c.y, sh);
     }
   }
 #pragma unroll
   for (int ch = 0; ch < KCH; ++ch) {
-    __align__(16) __nv_bfloat16 h[8];
+    __align__(16) __half h[8];
 #pragma unroll
-    for (int k = 0; k < 8; ++k) h[k] = __float2bfloat16_rn(slot[ch * 8 + k]);
+    for (int k = 0; k < 8; ++k) h[k] = __float2half_rn(slot[ch * 8 + k]);
     *reinterpret_cast<uint4*>(ctp + ((ct * KCH + ch) * kTcM + row) * 8) = *reinterpret_cast<uint4*>(h);
   }
 }
@@ -722,7 +738,7 @@ static int pack_impl(const ScorePlan& p, const Alphabet& a, const float2* V, con
   count_launch(2);
   int64_t nc = p.c_tiles * kTcM;
   pack_dirs_kernel<KCH><<<static_cast<unsigned>(ceil_div(nc, 256)), 256, 0, st>>>(C, p.S, p.r, p.c_tiles,
-                                                                                  static_cast<__nv_bfloat16*>(ct));
+                                                                                  static_cast<__half*>(ct));
   count_launch();
   return cuda_check(cudaGetLastError(), "tc pack kernels");
 }

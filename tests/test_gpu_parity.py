@@ -6,9 +6,9 @@ Tolerances (stated here, derived in the design doc):
 * FP64 re-scoring: f within 1e-9 relative; codes equal the oracle's except
   where the oracle's own angle margin to a boundary is below 1e-9 rad (a tie
   in FP64 arithmetic).
-* BF16 tensor-core scoring: per candidate, |sqrt(f) - sqrt(f_oracle)| within
+* Tensor-core scoring: per candidate, |sqrt(f) - sqrt(f_oracle)| within
   the error bound of _bf16_bound (decision flips only where the oracle's
-  margin is inside the bf16 projection error, plus the hi + lo E4M3
+  margin is inside the F16 projection error, plus the hi + lo E4M3
   rounding of the per-class sums' operand); median relative error below 3e-3 for
   n >= 1000.  The winner is decided after the FP64 re-scoring above.
 * Sampler: within 1e-6 of the oracle's Philox + Box-Muller stream.
@@ -120,10 +120,11 @@ def test_rescore_rejects_out_of_range_index(lrq):
 def _bf16_bound(V, K, C):
     """Per-candidate bound on |sqrt(f_bf16) - sqrt(f)| for the BF16 mode.
 
-    GEMM1 rounds both operands to bfloat16 (8-bit significand, unit roundoff
-    2^-8), so a projection carries an error of at most
-    2^-7 sum_k |V~_ik| |c~_k| <= 2^-7 sum_j |V_ij|_1 |c_j|_1 (taken here with a
-    factor-2 margin as e_i = 2^-6 sum_j |V_ij|_1 |c_j|_1); a code can differ
+    GEMM1 scales each row and direction by a power of two (no effect on the
+    signs), rounds both operands to F16 (unit roundoff 2^-11) and accumulates
+    its 16 products in F16, so a projection carries an error of at most
+    (2^-10 + 16 * 2^-11) sum_k |V~_ik| |c~_k| < 2^-6.8 sum_j |V_ij|_1 |c_j|_1
+    (taken here as e_i = 2^-6 sum_j |V_ij|_1 |c_j|_1); a code can differ
     from the FP64 decision only where |w_i| sin(margin_i) <= e_i.  Each such
     coordinate moves ||V^H z|| by at most 2 sin(pi/K) |V_i|.  GEMM2 scales
     the row beta_g conj(V_i) by a power of two chosen per coordinate (its
