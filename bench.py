@@ -55,7 +55,8 @@ def _config(mode: str, world: int):
     return {"workload": "scale: n=2^20, r=4, K=3, S=2^16 uniform directions per GPU per step; "
                         "V ~ CN(0,1) diag(4,2,1,0.5) complex64; top-64 FP64 rescore",
             "n": N, "r": R, "K": K, "S_per_gpu": S, "top_m": TOP_M,
-            "mode": "BF16 tensor-core + FP64 rescore" if mode == "bf16" else "FP32 CUDA-core + FP64 rescore",
+            "mode": ("tensor-core (F16 signs, FP8 hi+lo class sums) + FP64 rescore" if mode == "bf16"
+                     else "FP32 CUDA-core + FP64 rescore"),
             "parallelism": "replicas over candidates (dp%d)" % world,
             "l2": "flushed before every timed step (512 MiB write, untimed)"}
 
@@ -273,7 +274,7 @@ def run_ours(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if args.mode == "bf16" else "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16+e4m3" if args.mode == "bf16" else "f32",
         "data": "synthetic", "config": _config(args.mode, world),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
                      "frac": achieved / peak_tf, "traffic": args.traffic,
@@ -472,9 +473,9 @@ def run_maxcut(args):
                  "rejected_fraction": 1.0 - SS / int(draws.item())}
     _line("Max-3-Cut candidate*n evals/s (SBM n=10^6, S=2^17, r=3)", SS * n / (ms * 1e-3), UNIT, args, ms,
           {"workload": "planted 3-partition SBM n=10^6, p_in n=4, p_out n=8 (seed 1), unit weights, CSR int32; "
-                       "rank-3 FP64 Lanczos truncation of L; S=2^17 BF16 candidates (%s), top-64 FP64 rescore, exact "
+                       "rank-3 FP64 Lanczos truncation of L; S=2^17 tensor-core-scored candidates (%s), top-64 FP64 rescore, exact "
                        "cut of the winner" % ("null-vector sampler" if null else "uniform sphere"), "edges": edges},
-          dtype="bf16", gpu_launches=int(lrq.lrq_kernel_launches() - l0), clocks=clk.summary(),
+          dtype="f16+e4m3", gpu_launches=int(lrq.lrq_kernel_launches() - l0), clocks=clk.summary(),
           maxcut={"cut": int(cut.item()), "planted_cut": planted_cut, "edges": edges,
                   "cut_fraction": int(cut.item()) / edges, "best_f": float(rs["best_f"].item()),
                   "lambda": lam, "truncate_ms": trunc_ms, "lanczos_steps": tr["iters"], **extra})
