@@ -473,8 +473,9 @@ def run_maxcut(args):
                  "rejected_fraction": 1.0 - SS / int(draws.item())}
     _line("Max-3-Cut candidate*n evals/s (SBM n=10^6, S=2^17, r=3)", SS * n / (ms * 1e-3), UNIT, args, ms,
           {"workload": "planted 3-partition SBM n=10^6, p_in n=4, p_out n=8 (seed 1), unit weights, CSR int32; "
-                       "rank-3 FP64 Lanczos truncation of L; S=2^17 tensor-core-scored candidates (%s), top-64 FP64 rescore, exact "
-                       "cut of the winner" % ("null-vector sampler" if null else "uniform sphere"), "edges": edges},
+                       "rank-3 FP64 Lanczos truncation of L; S=2^17 tensor-core-scored candidates (%s), "
+                       "top-64 FP64 rescore, exact cut of the winner" % ("null-vector sampler" if null else "uniform sphere"),
+           "edges": edges},
           dtype="f16+e4m3", gpu_launches=int(lrq.lrq_kernel_launches() - l0), clocks=clk.summary(),
           maxcut={"cut": int(cut.item()), "planted_cut": planted_cut, "edges": edges,
                   "cut_fraction": int(cut.item()) / edges, "best_f": float(rs["best_f"].item()),
