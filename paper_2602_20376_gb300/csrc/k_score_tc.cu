@@ -42,13 +42,13 @@
 // NW independent workers per CTA, each a warpgroup (one thread per candidate
 // of the 128-candidate tile) with its own stage ring and TMEM slice (D1
 // projections, A2 indicator words, D2 accumulator).  One fixed thread of each
-// worker issues every tcgen05 and TMA operation of the worker: per tile,
-// after the warpgroup has turned D1 into indicator words in A2, it issues
-// GEMM2 of this tile and GEMM1 of the next behind one commit, then refills
-// the stage ring while the tensor core works (a stage is free once the D1 of
-// this tile has landed, which certifies every earlier MMA of that thread;
-// each packed tile -- GEMM1 rows and GEMM2 rows -- is one TMA box).  The
-// workers of a CTA
+// worker issues its tcgen05 operations: per tile, after the warpgroup has
+// turned D1 into indicator words in A2, it issues GEMM2 of this tile and
+// GEMM1 of the next behind one commit.  A second thread of the worker keeps
+// the stage ring full: a stage is free once the D1 of the next tile has
+// landed, which certifies every earlier MMA of the issuing thread; each
+// packed tile -- GEMM1 rows and GEMM2 rows -- is one TMA box.  The workers of
+// a CTA
 // interleave on the tensor core.  Every wait is bounded; on expiry the kernel
 // records LRQ_ETIMEOUT, drains its in-flight copies and MMAs, frees TMEM and
 // returns.
@@ -269,12 +269,13 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
   //   them into A2 -> one warpgroup rendezvous -> the issuer issues GEMM2(g)
   //   and then GEMM1(g+1), both committed behind one d1_full arrival, so
   //   seeing D1(g+1) also certifies that GEMM2(g) has released A2 and stage g
-  //   (tcgen05.commit tracks every earlier MMA of the committing thread), and
-  //   refills the stages freed by tile g-1 -> every `flush` tiles fold D2
-  //   into the two-sum partials.
+  //   (tcgen05.commit tracks every earlier MMA of the committing thread) ->
+  //   every `flush` tiles fold D2 into the two-sum partials.  The loader
+  //   refills the stages freed by tile g-1 right after it sees D1(g).
   const int qtr = warp & 3;         // TMEM lane quarter
   const int row = qtr * 32 + lane;  // candidate row within the tile
-  const bool issuer = (qtr == 0 && lane == 0);
+  const bool issuer = (qtr == 0 && lane == 0);  // issues the worker's MMAs
+  const bool loader = (qtr == 1 && lane == 0);  // issues the worker's TMA copies
   const uint32_t lane_base = static_cast<uint32_t>(qtr * 32) << 16;
   const uint32_t tw = tmem + w * Sh::WCOLS;  // this worker's TMEM slice
   constexpr uint32_t idesc1 = ptx::idesc_f16_f16(kTcM, Sh::N1);
@@ -329,11 +330,14 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
   uint32_t g = 0, pe = 0;
   int pos = 0;       // tile position within the accumulation period
   bool bad = false;  // this thread saw a wait give up (carried to the next barrier)
-  if (cc.item < prm.num_items && issuer) {
-    // prologue: directions of the first two items, the first NST tiles, GEMM1(0)
+  if (cc.item < prm.num_items && loader) {
+    // prologue: directions of the first two items, the first NST tiles
     load_dirs();
     load_dirs();
     while (lg < NST && lc.item < prm.num_items) load_tile();
+  }
+  if (cc.item < prm.num_items && issuer) {
+    // GEMM1(0) once its operands have landed
     const bool ok = wait_dirs() && wait_stage();
     if (ok) {
       ptx::tc_fence_after();
@@ -362,6 +366,12 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
       }
     }
     bad = bad || !warp_wait(d1_full, g & 1u, abort_flag, lane);
+    if (loader && !bad) {
+      // D1(g) has landed, so every MMA before GEMM1(g) is done: the stages up
+      // to tile g-1 are free, and at the end of an item its direction buffer
+      while (lg <= static_cast<int64_t>(g) - 1 + NST && lc.item < prm.num_items) load_tile();
+      if (item_end) load_dirs();
+    }
     // ---- round the projections of tile g into indicator words in A2
     if (!bad) {
       ptx::tc_fence_after();
@@ -430,15 +440,7 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
         ok = ok && wait_stage();
         if (ok) gemm1((g + 1) % NST, static_cast<uint32_t>((cc.ic + (item_end ? 1 : 0)) & 1));
       }
-      if (ok) {
-        // D1(g) had landed, so every MMA before GEMM1(g) is done: the stages up
-        // to tile g-1 are free, and at the end of an item its direction buffer
-        // (refilled here, while the tensor core works)
-        while (lg <= static_cast<int64_t>(g) - 1 + NST && lc.item < prm.num_items) load_tile();
-        if (item_end) load_dirs();
-      } else {
-        *abort_flag = 1;
-      }
+      if (!ok) *abort_flag = 1;
     }
     // ---- fold the period's accumulator into the two-sum partials
     if (last) {
@@ -489,15 +491,21 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
     *abort_flag = 1;
     dev_fail(status, LRQ_ETIMEOUT);
   }
-  // drain: the issuer's MMAs and copies complete before TMEM and shared
-  // memory are released
+  // drain: the issuer's MMAs and the loader's copies complete before TMEM and
+  // shared memory are released (a stage or direction buffer is refilled only
+  // after its previous copy was consumed, so only the last NST tile copies and
+  // the last two direction copies can be outstanding)
   if (issuer) {
     volatile int never = 0;
     ptx::mma_commit(drain_bar);
     ptx::mbar_wait(drain_bar, 0u, &never, kWaitLimit);
-    for (; cg < lg; ++cg)
-      ptx::mbar_wait(&full_b[cg % NST], static_cast<uint32_t>((cg / NST) & 1), &never, kWaitLimit);
-    for (; ca < la; ++ca) ptx::mbar_wait(&a1_full[ca & 1], static_cast<uint32_t>((ca >> 1) & 1), &never, kWaitLimit);
+  }
+  if (loader) {
+    volatile int never = 0;
+    for (int64_t t = lg > NST ? lg - NST : 0; t < lg; ++t)
+      ptx::mbar_wait(&full_b[t % NST], static_cast<uint32_t>((t / NST) & 1), &never, kWaitLimit);
+    for (int64_t t = la > 2 ? la - 2 : 0; t < la; ++t)
+      ptx::mbar_wait(&a1_full[t & 1], static_cast<uint32_t>((t >> 1) & 1), &never, kWaitLimit);
   }
   // ------------------------------------------------------------ teardown
   ptx::tc_fence_before();
