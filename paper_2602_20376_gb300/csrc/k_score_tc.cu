@@ -270,8 +270,8 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
   //   and then GEMM1(g+1), both committed behind one d1_full arrival, so
   //   seeing D1(g+1) also certifies that GEMM2(g) has released A2 and stage g
   //   (tcgen05.commit tracks every earlier MMA of the committing thread) ->
-  //   every `flush` tiles fold D2 into the two-sum partials.  The loader
-  //   refills the stages freed by tile g-1 right after it sees D1(g).
+  //   every `flush` tiles fold D2 into the two-sum partials.  After the
+  //   rendezvous the loader refills the stages freed by tile g-1.
   const int qtr = warp & 3;         // TMEM lane quarter
   const int row = qtr * 32 + lane;  // candidate row within the tile
   const bool issuer = (qtr == 0 && lane == 0);  // issues the worker's MMAs
@@ -366,12 +366,6 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
       }
     }
     bad = bad || !warp_wait(d1_full, g & 1u, abort_flag, lane);
-    if (loader && !bad) {
-      // D1(g) has landed, so every MMA before GEMM1(g) is done: the stages up
-      // to tile g-1 are free, and at the end of an item its direction buffer
-      while (lg <= static_cast<int64_t>(g) - 1 + NST && lc.item < prm.num_items) load_tile();
-      if (item_end) load_dirs();
-    }
     // ---- round the projections of tile g into indicator words in A2
     if (!bad) {
       ptx::tc_fence_after();
@@ -425,6 +419,13 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
     ptx::tc_fence_before();
     // D1 read and A2 written by the whole warpgroup; all leave together on failure
     if (ptx::named_barrier_or(1 + w, 128, bad)) break;
+    // ---- the loader: D1(g) had landed, so every MMA before GEMM1(g) is done:
+    // the stages up to tile g-1 are free, and at the end of an item its
+    // direction buffer (refilled while the issuer works)
+    if (loader) {
+      while (lg <= static_cast<int64_t>(g) - 1 + NST && lc.item < prm.num_items) load_tile();
+      if (item_end) load_dirs();
+    }
     // ---- the issuing thread: GEMM2(g), then GEMM1(g+1)
     if (issuer) {
       ptx::tc_fence_after();
