@@ -33,25 +33,27 @@
 // significant bits (like BF16).  hi and lo are separate output columns
 // (N = 2 x 8, or 2 x 16 for r > 4); the epilogue adds them and divides by s.
 // An FP8 MMA reduces 32 entries where a BF16 one reduces 16, so GEMM2 takes
-// half the MMA instructions -- and MMA issue, not arithmetic, bounds this
-// kernel (N is the problem's 2r outputs).  D2 accumulates in TMEM (FP32) for
+// half the MMA instructions (N is the problem's 2r outputs, so the MMAs are
+// small and the kernel is bounded by each worker's per-tile chain of waits,
+// issues and rounding, not by arithmetic).  D2 accumulates in TMEM (FP32) for
 // at most `flush` tiles, then is folded into FP32 two-sum registers
 // (error-free) and written as FP64 partials per coordinate chunk.
 //
 // Pipeline (one CTA per SM, persistent over (chunk, candidate tile) items):
 // NW independent workers per CTA, each a warpgroup (one thread per candidate
 // of the 128-candidate tile) with its own stage ring and TMEM slice (D1
-// projections, A2 indicator words, D2 accumulator).  One fixed thread of each
-// worker issues its tcgen05 operations: per tile, after the warpgroup has
-// turned D1 into indicator words in A2, it issues GEMM2 of this tile and
-// GEMM1 of the next behind one commit.  A second thread of the worker keeps
-// the stage ring full: a stage is free once the D1 of the next tile has
-// landed, which certifies every earlier MMA of the issuing thread; each
-// packed tile -- GEMM1 rows and GEMM2 rows -- is one TMA box.  The workers of
-// a CTA
-// interleave on the tensor core.  Every wait is bounded; on expiry the kernel
-// records LRQ_ETIMEOUT, drains its in-flight copies and MMAs, frees TMEM and
-// returns.
+// projections, A2 indicator words, D2 accumulator).  Per tile, after the
+// warpgroup has turned D1 into indicator words in A2 and met at a barrier,
+// its warp 0 issues GEMM1 of the next tile and its warp 2 GEMM2 of this one,
+// each from the whole converged warp through one elected lane (measured:
+// about a third of the cost of issuing from a lone active lane).  Separate
+// commits (D1 ready; A2 free) let the two run side by side; the rounding
+// threads wait for "A2 free" only just before they overwrite A2.  One lane of
+// warp 1 keeps the stage ring full: a stage is free once both GEMMs of its
+// tile are known complete; each packed tile -- GEMM1 rows and GEMM2 rows -- is
+// one TMA box.  The workers of a CTA interleave on the tensor core.  Every
+// wait is bounded; on expiry the kernel records LRQ_ETIMEOUT, drains its
+// in-flight copies and MMAs, frees TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -137,8 +139,9 @@ struct TcLayout {
   static constexpr int W_ACC = W_A1 + align1k(2 * A1_BYTES);
   static constexpr int ZERO_OFF = Sh::NW * WSMEM;
   static constexpr int BAR_OFF = ZERO_OFF + ZERO_BYTES;
-  // per worker: full per stage, A1 full x 2, D1-full, D2-ready, drain
-  static constexpr int WBARS = NST + 5;
+  // per worker: full per stage, A1 full x 2, D1-full, D2-ready, drain of the
+  // GEMM1 warp, A2-free, drain of the GEMM2 warp
+  static constexpr int WBARS = NST + 7;
   static constexpr int USED = BAR_OFF + Sh::NW * WBARS * 8 + 16;
   // at least 120 KB so that two CTAs never share an SM (each holds all 512
   // TMEM columns)
@@ -163,12 +166,11 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   e = (a - (s - bb)) + (b - bb);
 }
 
-// One lane of the warp polls the barrier (keeps shared-memory traffic low);
-// the outcome is broadcast to the warp, which is converged afterwards.
-__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort, int lane) {
-  int ok = 1;
-  if (lane == 0) ok = ptx::mbar_wait(bar, parity, abort, kWaitLimit) ? 1 : 0;
-  return __shfl_sync(0xffffffffu, ok, 0) != 0;
+// Every lane of the warp polls the barrier and the warp agrees on the outcome
+// (measured: cheaper than one lane polling while the rest of its warp waits).
+__device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  const bool ok = ptx::mbar_wait(bar, parity, abort, kWaitLimit);
+  return __all_sync(0xffffffffu, ok);
 }
 
 // The worker's sequence of tiles: items gw, gw + workers, ... and the tiles of
@@ -263,18 +265,20 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
   uint64_t* d1_full = a1_full + 2;
   uint64_t* d2_ready = a1_full + 3;
   uint64_t* drain_bar = a1_full + 4;
+  uint64_t* a2_free = a1_full + 5;
+  uint64_t* drain2 = a1_full + 6;
 
   // Thread `row` owns candidate `row` of every tile.  Per tile g:
-  //   wait D1(g) -> round its R coordinates into indicator words -> store
-  //   them into A2 -> one warpgroup rendezvous -> the issuer issues GEMM2(g)
-  //   and then GEMM1(g+1), both committed behind one d1_full arrival, so
-  //   seeing D1(g+1) also certifies that GEMM2(g) has released A2 and stage g
-  //   (tcgen05.commit tracks every earlier MMA of the committing thread) ->
-  //   every `flush` tiles fold D2 into the two-sum partials.  After the
-  //   rendezvous the loader refills the stages freed by tile g-1.
+  //   wait D1(g) -> round its R coordinates into indicator words -> wait until
+  //   GEMM2(g-1) has released A2 -> store them into A2 -> one warpgroup
+  //   rendezvous -> warp 0 issues GEMM1(g+1) behind d1_full while warp 2
+  //   issues GEMM2(g) behind a2_free (and d2_ready at the end of a period);
+  //   both issue from the converged warp through one elected lane, and every
+  //   wait is polled by whole warps -> every `flush` tiles fold D2 into the
+  //   two-sum partials.  After the rendezvous the loader (one lane of warp 1)
+  //   refills the stages freed by tile g-1.
   const int qtr = warp & 3;         // TMEM lane quarter
   const int row = qtr * 32 + lane;  // candidate row within the tile
-  const bool issuer = (qtr == 0 && lane == 0);  // issues the worker's MMAs
   const bool loader = (qtr == 1 && lane == 0);  // issues the worker's TMA copies
   const uint32_t lane_base = static_cast<uint32_t>(qtr * 32) << 16;
   const uint32_t tw = tmem + w * Sh::WCOLS;  // this worker's TMEM slice
@@ -284,11 +288,11 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
   float2* acc = reinterpret_cast<float2*>(wsm + L::W_ACC) + row * 16;  // (hi, lo) per component
 
   TcCursor cc = tc_start(prm, gw, 0);           // consumer: the tile being rounded
-  TcCursor lc = cc;                             // issuer: the next tile to load
+  TcCursor lc = cc;                             // loader: the next tile to load
   int64_t lg = 0, cg = 0;                       // tiles loaded / stages waited for
   int64_t la = 0, ca = 0;                       // direction tiles loaded / waited for
 
-  // issuer helpers: copies into the stage ring and the direction buffers
+  // loader helpers: copies into the stage ring and the direction buffers
   auto load_tile = [&]() {
     const uint32_t s = static_cast<uint32_t>(lg % NST);
     uint8_t* st = wsm + s * L::STAGE_BYTES;
@@ -307,13 +311,13 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
                      static_cast<int>((it % prm.c_tiles) * (L::A1_BYTES / 256)), &a1_full[b]);  // once per item
     ++la;
   };
-  auto wait_stage = [&]() -> bool {  // the stage of tile cg
-    const bool ok = ptx::mbar_wait(&full_b[cg % NST], static_cast<uint32_t>((cg / NST) & 1), abort_flag, kWaitLimit);
+  auto wait_stage = [&]() -> bool {  // the stage of tile cg (warp 0)
+    const bool ok = warp_wait(&full_b[cg % NST], static_cast<uint32_t>((cg / NST) & 1), abort_flag);
     ++cg;
     return ok;
   };
-  auto wait_dirs = [&]() -> bool {  // the direction buffer of item ca
-    const bool ok = ptx::mbar_wait(&a1_full[ca & 1], static_cast<uint32_t>((ca >> 1) & 1), abort_flag, kWaitLimit);
+  auto wait_dirs = [&]() -> bool {  // the direction buffer of item ca (warp 0)
+    const bool ok = warp_wait(&a1_full[ca & 1], static_cast<uint32_t>((ca >> 1) & 1), abort_flag);
     ++ca;
     return ok;
   };
@@ -323,8 +327,9 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
     const uint32_t lbo_a1 = two_chunks ? kTcM * 16u : (smem_base + L::ZERO_OFF - a1);
     const uint32_t b1 = wsm_s + stage * L::STAGE_BYTES + L::B1_OFF_IN_STAGE;
     const uint32_t lbo_b1 = two_chunks ? Sh::N1 * 16u : (smem_base + L::ZERO_OFF - b1);
-    ptx::mma_bf16_ss(tw + Sh::D1_OFF, ptx::smem_desc(a1, lbo_a1, 128), ptx::smem_desc(b1, lbo_b1, 128), idesc1, 0u);
-    ptx::mma_commit(d1_full);
+    ptx::mma_f16_ss_elect(tw + Sh::D1_OFF, ptx::smem_desc(a1, lbo_a1, 128), ptx::smem_desc(b1, lbo_b1, 128), idesc1,
+                          0u);
+    ptx::mma_commit_elect(d1_full);
   };
 
   uint32_t g = 0, pe = 0;
@@ -336,13 +341,13 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
     load_dirs();
     while (lg < NST && lc.item < prm.num_items) load_tile();
   }
-  if (cc.item < prm.num_items && issuer) {
+  if (cc.item < prm.num_items && qtr == 0) {
     // GEMM1(0) once its operands have landed
     const bool ok = wait_dirs() && wait_stage();
     if (ok) {
       ptx::tc_fence_after();
       gemm1(0u, 0u);
-    } else {
+    } else if (lane == 0) {
       *abort_flag = 1;
     }
   }
@@ -365,7 +370,7 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
         mag[4 * c + 3] = v4.w;
       }
     }
-    bad = bad || !warp_wait(d1_full, g & 1u, abort_flag, lane);
+    bad = bad || !warp_wait(d1_full, g & 1u, abort_flag);
     // ---- round the projections of tile g into indicator words in A2
     if (!bad) {
       ptx::tc_fence_after();
@@ -411,41 +416,51 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
           }
         }
       }
+      // GEMM2(g-1) has released A2
+      if (g > 0) bad = !warp_wait(a2_free, (g - 1) & 1u, abort_flag);
+      if (!bad) {
+        ptx::tc_fence_after();
 #pragma unroll
-      for (int c = 0; c < Sh::A2COLS / 8; ++c)
-        ptx::tmem_st_x8(tw + lane_base + Sh::A2_OFF + c * 8, *reinterpret_cast<const uint32_t(*)[8]>(&wv[c * 8]));
-      ptx::tmem_wait_st();
+        for (int c = 0; c < Sh::A2COLS / 8; ++c)
+          ptx::tmem_st_x8(tw + lane_base + Sh::A2_OFF + c * 8, *reinterpret_cast<const uint32_t(*)[8]>(&wv[c * 8]));
+        ptx::tmem_wait_st();
+      }
     }
     ptx::tc_fence_before();
     // D1 read and A2 written by the whole warpgroup; all leave together on failure
     if (ptx::named_barrier_or(1 + w, 128, bad)) break;
-    // ---- the loader: D1(g) had landed, so every MMA before GEMM1(g) is done:
-    // the stages up to tile g-1 are free, and at the end of an item its
-    // direction buffer (refilled while the issuer works)
+    // ---- the loader: GEMM1(g) is done (D1(g) was seen) and so is GEMM2(g-1)
+    // (every warp saw a2_free before storing A2): the stages up to tile g-1
+    // are free, and at the end of an item its direction buffer
     if (loader) {
       while (lg <= static_cast<int64_t>(g) - 1 + NST && lc.item < prm.num_items) load_tile();
       if (item_end) load_dirs();
     }
-    // ---- the issuing thread: GEMM2(g), then GEMM1(g+1)
-    if (issuer) {
+    // ---- warp 0: GEMM1(g+1) into D1
+    if (qtr == 0) {
       ptx::tc_fence_after();
-      const uint32_t b2 = wsm_s + (g % NST) * L::STAGE_BYTES + L::B2_OFF_IN_STAGE;
-#pragma unroll
-      for (int q = 0; q < Sh::KD2 / 32; ++q)
-        ptx::mma_e4m3_ts(tw + Sh::D2_OFF, tw + Sh::A2_OFF + q * 8, ptx::smem_desc(b2 + q * 2 * lbo_b2, lbo_b2, 128),
-                         idesc2, (q > 0 || !first) ? 1u : 0u);
-      if (last) ptx::mma_commit(d2_ready);
       bool ok = true;
       if (has_next) {
         ok = item_end ? wait_dirs() : true;
         ok = ok && wait_stage();
         if (ok) gemm1((g + 1) % NST, static_cast<uint32_t>((cc.ic + (item_end ? 1 : 0)) & 1));
       }
-      if (!ok) *abort_flag = 1;
+      if (!ok && lane == 0) *abort_flag = 1;
+    }
+    // ---- warp 2: GEMM2(g) from A2 and the tile's stage into D2
+    if (qtr == 2) {
+      ptx::tc_fence_after();
+      const uint32_t b2 = wsm_s + (g % NST) * L::STAGE_BYTES + L::B2_OFF_IN_STAGE;
+#pragma unroll
+      for (int q = 0; q < Sh::KD2 / 32; ++q)
+        ptx::mma_e4m3_ts_elect(tw + Sh::D2_OFF, tw + Sh::A2_OFF + q * 8,
+                               ptx::smem_desc(b2 + q * 2 * lbo_b2, lbo_b2, 128), idesc2, (q > 0 || !first) ? 1u : 0u);
+      if (last) ptx::mma_commit_elect(d2_ready);
+      ptx::mma_commit_elect(a2_free);
     }
     // ---- fold the period's accumulator into the two-sum partials
     if (last) {
-      bad = !warp_wait(d2_ready, pe & 1u, abort_flag, lane);
+      bad = !warp_wait(d2_ready, pe & 1u, abort_flag);
       if (!bad) {
         ptx::tc_fence_after();
         uint32_t dh[16], dl[16];
@@ -492,14 +507,15 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
     *abort_flag = 1;
     dev_fail(status, LRQ_ETIMEOUT);
   }
-  // drain: the issuer's MMAs and the loader's copies complete before TMEM and
-  // shared memory are released (a stage or direction buffer is refilled only
-  // after its previous copy was consumed, so only the last NST tile copies and
-  // the last two direction copies can be outstanding)
-  if (issuer) {
+  // drain: the MMAs of warps 0 and 2 and the loader's copies complete before
+  // TMEM and shared memory are released (a stage or direction buffer is
+  // refilled only after its previous copy was consumed, so only the last NST
+  // tile copies and the last two direction copies can be outstanding)
+  if (qtr == 0 || qtr == 2) {
     volatile int never = 0;
-    ptx::mma_commit(drain_bar);
-    ptx::mbar_wait(drain_bar, 0u, &never, kWaitLimit);
+    uint64_t* db = qtr == 0 ? drain_bar : drain2;
+    ptx::mma_commit_elect(db);
+    warp_wait(db, 0u, &never);
   }
   if (loader) {
     volatile int never = 0;
