@@ -54,12 +54,24 @@ __device__ __forceinline__ void acc_dot2(float& hi, float& lo, float a, float bh
   lo += e4 + small;
 }
 
-template <int K>
+// Work split: a block takes kRsCpb candidates and one chunk of coordinates;
+// the chunk's rows of V are staged through shared memory 256 at a time
+// (component-major, so that the 32 lanes of a warp read 32 consecutive
+// entries) and every warp evaluates its kRsCpw candidates on them, one row
+// per lane.  V is thus read from memory once per kRsCpb candidates instead of
+// once per candidate.  RM is the largest rank the instance handles (4 or 8):
+// it sizes the per-thread accumulators.
+constexpr int kRsCpw = 2;                              // candidates per warp
+constexpr int kRsCpb = kRsCpw * (kRsThreads / 32);     // candidates per block
+constexpr int kRsTile = 256;                           // rows staged at a time
+
+template <int K, int RM>
 __global__ void __launch_bounds__(kRsThreads) rescore_partial_kernel(
     const float2* __restrict__ V, int64_t n, int r, const float2* __restrict__ C, int64_t S,
-    const int64_t* __restrict__ idx, int nchunk, int64_t rows_per_chunk, const __grid_constant__ RescoreTables tab,
+    const int64_t* __restrict__ idx, int m, int nchunk, int64_t rows_per_chunk, const __grid_constant__ RescoreTables tab,
     double* __restrict__ part, uint8_t* __restrict__ z_out, int32_t* status) {
-  __shared__ double red[kRsThreads];
+  __shared__ float2 vs[RM][kRsTile];
+  __shared__ float2 cs[kRsCpb][RM];
   __shared__ float sbc[kMaxK], sbs[kMaxK], szrh[kMaxK], szrl[kMaxK], szih[kMaxK], szil[kMaxK];
   __shared__ double sbc64[kMaxK], sbs64[kMaxK];
   const int Kr = (K > 0) ? K : tab.K;
@@ -73,100 +85,134 @@ __global__ void __launch_bounds__(kRsThreads) rescore_partial_kernel(
     szih[k] = tab.zih[k];
     szil[k] = tab.zil[k];
   }
-  __syncthreads();
-  const int t = blockIdx.x;  // candidate position
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int chunk = blockIdx.y;
-  int64_t s = idx[t];
-  bool ok = (s >= 0 && s < S);
-  if (!ok) {
-    if (threadIdx.x == 0 && chunk == 0) dev_fail(status, LRQ_EINVAL);
-    s = 0;
+  const int tb = blockIdx.x * kRsCpb;  // first candidate position of the block
+  for (int e = threadIdx.x; e < kRsCpb * RM; e += blockDim.x) {
+    const int c = e / RM, j = e % RM;
+    const int t = tb + c;
+    float2 v = make_float2(0.f, 0.f);
+    if (t < m && j < r) {
+      const int64_t s = idx[t];
+      if (s >= 0 && s < S) v = C[s * r + j];
+    }
+    cs[c][j] = v;
   }
-  float cr[kMaxRank], ci[kMaxRank];
+  __syncthreads();
+
+  // this warp's candidates
+  int tc[kRsCpw];
+  bool act[kRsCpw], ok[kRsCpw];
 #pragma unroll
-  for (int j = 0; j < kMaxRank; ++j) {
-    float2 c = (j < r) ? C[s * r + j] : make_float2(0.f, 0.f);
-    cr[j] = c.x;
-    ci[j] = c.y;
+  for (int q = 0; q < kRsCpw; ++q) {
+    tc[q] = tb + warp * kRsCpw + q;
+    act[q] = tc[q] < m;
+    const int64_t s = act[q] ? idx[tc[q]] : 0;
+    ok[q] = act[q] && s >= 0 && s < S;
+    if (act[q] && !ok[q] && lane == 0 && chunk == 0) dev_fail(status, LRQ_EINVAL);
   }
+  float cr[kRsCpw][RM], ci[kRsCpw][RM];
+#pragma unroll
+  for (int q = 0; q < kRsCpw; ++q)
+#pragma unroll
+    for (int j = 0; j < RM; ++j) {
+      const float2 c = cs[warp * kRsCpw + q][j];
+      cr[q][j] = c.x;
+      ci[q][j] = c.y;
+    }
   const float u = 5.9604644775390625e-08f;  // 2^-24, unit roundoff of FP32
   const float gamma = static_cast<float>(2 * r + 4) * 2.0f * u;
-  float hi[2 * kMaxRank], lo[2 * kMaxRank];
+  float hi[kRsCpw][2 * RM], lo[kRsCpw][2 * RM];
 #pragma unroll
-  for (int j = 0; j < 2 * kMaxRank; ++j) hi[j] = lo[j] = 0.f;
+  for (int q = 0; q < kRsCpw; ++q)
+#pragma unroll
+    for (int j = 0; j < 2 * RM; ++j) hi[q][j] = lo[q][j] = 0.f;
 
   const int64_t i0 = static_cast<int64_t>(chunk) * rows_per_chunk;
   const int64_t i1 = min(n, i0 + rows_per_chunk);
-  for (int64_t i = i0 + threadIdx.x; i < i1; i += kRsThreads) {
-    float vr[kMaxRank], vi[kMaxRank];
-#pragma unroll
-    for (int j = 0; j < kMaxRank; ++j) {
-      float2 v = (j < r) ? V[i * r + j] : make_float2(0.f, 0.f);
-      vr[j] = v.x;
-      vi[j] = v.y;
+  for (int64_t ts = i0; ts < i1; ts += kRsTile) {
+    const int rows = static_cast<int>(min(static_cast<int64_t>(kRsTile), i1 - ts));
+    __syncthreads();  // the previous tile has been read
+    for (int e = threadIdx.x; e < rows * r; e += blockDim.x) {
+      const int row = e / r, j = e - row * r;
+      vs[j][row] = V[ts * r + e];
     }
-    float x = 0.f, y = 0.f, mag = 0.f;
+    __syncthreads();
+    for (int ro = lane; ro < rows; ro += 32) {
+      const int64_t i = ts + ro;
+      float vr[RM], vi[RM];
 #pragma unroll
-    for (int j = 0; j < kMaxRank; ++j) {
-      x = fmaf(vr[j], cr[j], x);
-      x = fmaf(-vi[j], ci[j], x);
-      y = fmaf(vr[j], ci[j], y);
-      y = fmaf(vi[j], cr[j], y);
-      mag = fmaf(fabsf(vr[j]) + fabsf(vi[j]), fabsf(cr[j]) + fabsf(ci[j]), mag);
-    }
-    int k;
-    if constexpr (K > 0) {
-      constexpr int BK = (K % 2 == 0) ? K / 2 : K;
-      float bc[BK], bs[BK];
-#pragma unroll
-      for (int m = 0; m < BK; ++m) {
-        bc[m] = sbc[m];
-        bs[m] = sbs[m];
+      for (int j = 0; j < RM; ++j) {
+        const float2 v = (j < r) ? vs[j][ro] : make_float2(0.f, 0.f);
+        vr[j] = v.x;
+        vi[j] = v.y;
       }
-      k = decide_fp32<K>(x, y, bc, bs);
-    } else {
-      k = decide_fp32_generic(x, y, Kr);
-    }
-    // certify: w strictly inside sector k, away from both bounding lines by
-    // more than the rounding bound (boundary k-1 below, boundary k above)
-    const float bound = gamma * mag + 4.0f * u * (fabsf(x) + fabsf(y));
-    const int ma = (k == 0) ? Kr - 1 : k - 1;
-    const float pa = fmaf(y, sbc[ma], -x * sbs[ma]);
-    const float pb = fmaf(y, sbc[k], -x * sbs[k]);
-    if (!(pa > bound && pb < -bound)) {
-      double xd = 0.0, yd = 0.0;
 #pragma unroll
-      for (int j = 0; j < kMaxRank; ++j) {
-        xd = fma(static_cast<double>(vr[j]), static_cast<double>(cr[j]), xd);
-        xd = fma(-static_cast<double>(vi[j]), static_cast<double>(ci[j]), xd);
-        yd = fma(static_cast<double>(vr[j]), static_cast<double>(ci[j]), yd);
-        yd = fma(static_cast<double>(vi[j]), static_cast<double>(cr[j]), yd);
-      }
-      k = decide_fp64(xd, yd, Kr, sbc64, sbs64);
-    }
-    if (z_out && ok) z_out[static_cast<int64_t>(t) * n + i] = static_cast<uint8_t>(k);
-    const float zrh = szrh[k], zrl = szrl[k], zih = szih[k], zil = szil[k];
+      for (int q = 0; q < kRsCpw; ++q) {
+        if (!act[q]) continue;
+        float x = 0.f, y = 0.f, mag = 0.f;
 #pragma unroll
-    for (int j = 0; j < kMaxRank; ++j) {
-      if (j < r) {
-        // Re(conj(V) z) = vr zr + vi zi ; Im(conj(V) z) = vr zi - vi zr
-        acc_dot2(hi[2 * j], lo[2 * j], vr[j], zrh, zrl, vi[j], zih, zil);
-        acc_dot2(hi[2 * j + 1], lo[2 * j + 1], vr[j], zih, zil, -vi[j], zrh, zrl);
+        for (int j = 0; j < RM; ++j) {
+          x = fmaf(vr[j], cr[q][j], x);
+          x = fmaf(-vi[j], ci[q][j], x);
+          y = fmaf(vr[j], ci[q][j], y);
+          y = fmaf(vi[j], cr[q][j], y);
+          mag = fmaf(fabsf(vr[j]) + fabsf(vi[j]), fabsf(cr[q][j]) + fabsf(ci[q][j]), mag);
+        }
+        int k;
+        if constexpr (K > 0) {
+          constexpr int BK = (K % 2 == 0) ? K / 2 : K;
+          float bc[BK], bs[BK];
+#pragma unroll
+          for (int mm = 0; mm < BK; ++mm) {
+            bc[mm] = sbc[mm];
+            bs[mm] = sbs[mm];
+          }
+          k = decide_fp32<K>(x, y, bc, bs);
+        } else {
+          k = decide_fp32_generic(x, y, Kr);
+        }
+        // certify: w strictly inside sector k, away from both bounding lines
+        // by more than the rounding bound (boundary k-1 below, k above)
+        const float bound = gamma * mag + 4.0f * u * (fabsf(x) + fabsf(y));
+        const int ma = (k == 0) ? Kr - 1 : k - 1;
+        const float pa = fmaf(y, sbc[ma], -x * sbs[ma]);
+        const float pb = fmaf(y, sbc[k], -x * sbs[k]);
+        if (!(pa > bound && pb < -bound)) {
+          double xd = 0.0, yd = 0.0;
+#pragma unroll
+          for (int j = 0; j < RM; ++j) {
+            xd = fma(static_cast<double>(vr[j]), static_cast<double>(cr[q][j]), xd);
+            xd = fma(-static_cast<double>(vi[j]), static_cast<double>(ci[q][j]), xd);
+            yd = fma(static_cast<double>(vr[j]), static_cast<double>(ci[q][j]), yd);
+            yd = fma(static_cast<double>(vi[j]), static_cast<double>(cr[q][j]), yd);
+          }
+          k = decide_fp64(xd, yd, Kr, sbc64, sbs64);
+        }
+        if (z_out && ok[q]) z_out[static_cast<int64_t>(tc[q]) * n + i] = static_cast<uint8_t>(k);
+        const float zrh = szrh[k], zrl = szrl[k], zih = szih[k], zil = szil[k];
+#pragma unroll
+        for (int j = 0; j < RM; ++j) {
+          if (j < r) {
+            // Re(conj(V) z) = vr zr + vi zi ; Im(conj(V) z) = vr zi - vi zr
+            acc_dot2(hi[q][2 * j], lo[q][2 * j], vr[j], zrh, zrl, vi[j], zih, zil);
+            acc_dot2(hi[q][2 * j + 1], lo[q][2 * j + 1], vr[j], zih, zil, -vi[j], zrh, zrl);
+          }
+        }
       }
     }
   }
-  // combine threads in FP64, component by component (fixed tree)
+  // combine the 32 lanes in FP64, component by component (fixed tree)
 #pragma unroll
-  for (int j = 0; j < 2 * kMaxRank; ++j) {
-    if (j < 2 * r) {
-      red[threadIdx.x] = static_cast<double>(hi[j]) + static_cast<double>(lo[j]);
-      __syncthreads();
-      for (int h = kRsThreads / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
-        __syncthreads();
+  for (int q = 0; q < kRsCpw; ++q) {
+#pragma unroll
+    for (int j = 0; j < 2 * RM; ++j) {
+      if (j < 2 * r) {
+        double v = static_cast<double>(hi[q][j]) + static_cast<double>(lo[q][j]);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        if (lane == 0 && act[q]) part[(static_cast<int64_t>(tc[q]) * nchunk + chunk) * (2 * kMaxRank) + j] = v;
       }
-      if (threadIdx.x == 0) part[(static_cast<int64_t>(t) * nchunk + chunk) * (2 * kMaxRank) + j] = red[0];
-      __syncthreads();
     }
   }
 }
@@ -178,19 +224,37 @@ __global__ void rescore_final_kernel(const double* __restrict__ part, int m, int
   __shared__ int bt[256];
   double my_best = -1.0;
   int my_t = 0x7fffffff;
-  for (int t = threadIdx.x; t < m; t += blockDim.x) {
-    double f = 0.0;
-    for (int j = 0; j < 2 * r; ++j) {
-      double a = 0.0;
-      for (int c = 0; c < nchunk; ++c) a += part[(static_cast<int64_t>(t) * nchunk + c) * (2 * kMaxRank) + j];
-      f += a * a;
+  // one warp per candidate: lanes sum fixed subsets of the chunks, then a
+  // fixed shuffle tree adds the lanes (deterministic order)
+  const int lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  for (int t = threadIdx.x >> 5; t < m; t += nwarp) {
+    double a[2 * kMaxRank];
+#pragma unroll
+    for (int j = 0; j < 2 * kMaxRank; ++j) a[j] = 0.0;
+    for (int c = lane; c < nchunk; c += 32) {
+      const double* pc = part + (static_cast<int64_t>(t) * nchunk + c) * (2 * kMaxRank);
+#pragma unroll
+      for (int j = 0; j < 2 * kMaxRank; ++j)
+        if (j < 2 * r) a[j] += pc[j];
     }
-    int64_t s = idx[t];
-    if (s < 0 || s >= S) f = -1.0;
-    f_out[t] = f;
-    if (f > my_best || (f == my_best && t < my_t)) {
-      my_best = f;
-      my_t = t;
+    double f = 0.0;
+#pragma unroll
+    for (int j = 0; j < 2 * kMaxRank; ++j) {
+      if (j < 2 * r) {
+        double v = a[j];
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
+        f += v * v;  // meaningful in lane 0
+      }
+    }
+    if (lane == 0) {
+      const int64_t s = idx[t];
+      if (s < 0 || s >= S) f = -1.0;
+      f_out[t] = f;
+      if (f > my_best || (f == my_best && t < my_t)) {
+        my_best = f;
+        my_t = t;
+      }
     }
   }
   bf[threadIdx.x] = my_best;
@@ -214,6 +278,8 @@ __global__ void rescore_final_kernel(const double* __restrict__ part, int m, int
   }
 }
 
+int rescore_blocks_x(int m) { return (m + kRsCpb - 1) / kRsCpb; }
+
 int launch_rescore(const RescorePlan& p, const Alphabet& a, const float2* V, const float2* C, int64_t S,
                    const int64_t* idx, double* part, double* f_out, uint8_t* z_out, int64_t* best_out,
                    double* best_f_out, int32_t* status, cudaStream_t st) {
@@ -236,14 +302,19 @@ int launch_rescore(const RescorePlan& p, const Alphabet& a, const float2* V, con
     tab.zih[k] = static_cast<float>(zi);
     tab.zil[k] = static_cast<float>(zi - static_cast<double>(tab.zih[k]));
   }
-  dim3 grid(static_cast<unsigned>(p.m), static_cast<unsigned>(p.nchunk));
+  dim3 grid(static_cast<unsigned>(rescore_blocks_x(p.m)), static_cast<unsigned>(p.nchunk));
+  const bool r4 = p.r <= 4;
   switch (a.K) {
-#define LRQ_RS_CASE(KK)                                                                                   \
-  case KK:                                                                                                \
-    rescore_partial_kernel<KK><<<grid, kRsThreads, 0, st>>>(V, p.n, p.r, C, S, idx, p.nchunk,             \
-                                                            p.rows_per_chunk, tab, part, z_out, status); \
+#define LRQ_RS_CASE(KK)                                                                                          \
+  case KK:                                                                                                       \
+    if (r4)                                                                                                      \
+      rescore_partial_kernel<KK, 4><<<grid, kRsThreads, 0, st>>>(V, p.n, p.r, C, S, idx, p.m, p.nchunk,          \
+                                                                 p.rows_per_chunk, tab, part, z_out, status);    \
+    else                                                                                                         \
+      rescore_partial_kernel<KK, kMaxRank><<<grid, kRsThreads, 0, st>>>(V, p.n, p.r, C, S, idx, p.m, p.nchunk,   \
+                                                                        p.rows_per_chunk, tab, part, z_out,      \
+                                                                        status);                                 \
     break;
-    count_launch();
     LRQ_RS_CASE(2)
     LRQ_RS_CASE(3)
     LRQ_RS_CASE(4)
@@ -253,10 +324,14 @@ int launch_rescore(const RescorePlan& p, const Alphabet& a, const float2* V, con
     LRQ_RS_CASE(8)
 #undef LRQ_RS_CASE
     default:
-      rescore_partial_kernel<0><<<grid, kRsThreads, 0, st>>>(V, p.n, p.r, C, S, idx, p.nchunk, p.rows_per_chunk,
-                                                              tab, part, z_out, status);
-      count_launch();
+      if (r4)
+        rescore_partial_kernel<0, 4><<<grid, kRsThreads, 0, st>>>(V, p.n, p.r, C, S, idx, p.m, p.nchunk,
+                                                                  p.rows_per_chunk, tab, part, z_out, status);
+      else
+        rescore_partial_kernel<0, kMaxRank><<<grid, kRsThreads, 0, st>>>(V, p.n, p.r, C, S, idx, p.m, p.nchunk,
+                                                                         p.rows_per_chunk, tab, part, z_out, status);
   }
+  count_launch();
   int e = cuda_check(cudaGetLastError(), "rescore_partial_kernel");
   if (e) return e;
   rescore_final_kernel<<<1, 256, 0, st>>>(part, p.m, p.nchunk, p.r, idx, S, f_out, best_out, best_f_out);

@@ -81,6 +81,7 @@ struct RescorePlan {
   size_t total;
 };
 int plan_rescore(int64_t n, int r, int m, RescorePlan* p);
+int rescore_blocks_x(int m);  // candidate blocks of the re-scoring grid
 
 int num_sms_current();
 
