@@ -61,6 +61,24 @@ def _config(mode: str, world: int):
             "l2": "flushed before every timed step (512 MiB write, untimed)"}
 
 
+# DRAM bytes (read + write) of one score_tc_kernel launch of the default scale
+# workload (n = 2^20, r = 4, K = 3, S = 2^16, tensor-core mode), from a one-pass
+# ncu capture of the launch after the L2 flush: 72.44 MB read + 137.84 MB
+# written (the FP64 partials, S x 2r doubles per coordinate chunk, dominate
+# the writes; part of them is still in L2 when the kernel ends).
+# The command that measured it is in profiles/score_tc_kernel_n2e20_S2e16_dram.md;
+# it must be taken again whenever the kernel changes.
+SCALE_TRAFFIC_BYTES = 72.44e6 + 137.84e6
+
+
+def _traffic(args):
+    if args.traffic is not None:
+        return args.traffic
+    if args.mode == "bf16" and args.candidates == S and args.workload == "scale":
+        return SCALE_TRAFFIC_BYTES
+    return None
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -277,7 +295,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "f16+e4m3" if args.mode == "bf16" else "f32",
         "data": "synthetic", "config": _config(args.mode, world),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tf, "traffic": args.traffic,
+                     "frac": achieved / peak_tf, "traffic": _traffic(args),
                      "kernel": "score_tc_kernel" if args.mode == "bf16" else "score_fp32_kernel",
                      "kernel_ms": kern_avg_s * 1e3, "peak_kind": peak_kind + " bf16 dense (burst)",
                      "flops_per_launch": flops},
