@@ -64,6 +64,8 @@ __device__ __forceinline__ void acc_dot2(float& hi, float& lo, float a, float bh
 constexpr int kRsCpw = 2;                              // candidates per warp
 constexpr int kRsCpb = kRsCpw * (kRsThreads / 32);     // candidates per block
 constexpr int kRsTile = 256;                           // rows staged at a time
+constexpr int kRsFlush = 256 * 32 / kRsTile;           // tiles between FP64 flushes (256 rows per lane)
+static_assert(kRsCpw * 16 == 32 && 2 * kMaxRank <= 16, "one lane per (candidate, component) total");
 
 template <int K, int RM>
 __global__ void __launch_bounds__(kRsThreads) rescore_partial_kernel(
@@ -127,10 +129,36 @@ __global__ void __launch_bounds__(kRsThreads) rescore_partial_kernel(
   for (int q = 0; q < kRsCpw; ++q)
 #pragma unroll
     for (int j = 0; j < 2 * RM; ++j) hi[q][j] = lo[q][j] = 0.f;
+  // Every kRsFlush tiles (at most 256 rows per lane, which bounds the error
+  // of the FP32 low parts) the lanes' (hi, lo) pairs are added in FP64 over
+  // the warp (xor tree) and the total of component j of candidate q is kept
+  // by lane q * 16 + j.
+  double tot = 0.0;
+  auto flush = [&]() {
+#pragma unroll
+    for (int q = 0; q < kRsCpw; ++q) {
+#pragma unroll
+      for (int j = 0; j < 2 * RM; ++j) {
+        if (j < 2 * r) {
+          double v = static_cast<double>(hi[q][j]) + static_cast<double>(lo[q][j]);
+#pragma unroll
+          for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+          if (lane == q * 16 + j) tot += v;
+          hi[q][j] = lo[q][j] = 0.f;
+        }
+      }
+    }
+  };
+  int tiles = 0;
 
   const int64_t i0 = static_cast<int64_t>(chunk) * rows_per_chunk;
   const int64_t i1 = min(n, i0 + rows_per_chunk);
   for (int64_t ts = i0; ts < i1; ts += kRsTile) {
+    if (tiles == kRsFlush) {
+      flush();
+      tiles = 0;
+    }
+    ++tiles;
     const int rows = static_cast<int>(min(static_cast<int64_t>(kRsTile), i1 - ts));
     __syncthreads();  // the previous tile has been read
     for (int e = threadIdx.x; e < rows * r; e += blockDim.x) {
@@ -202,18 +230,10 @@ __global__ void __launch_bounds__(kRsThreads) rescore_partial_kernel(
       }
     }
   }
-  // combine the 32 lanes in FP64, component by component (fixed tree)
-#pragma unroll
-  for (int q = 0; q < kRsCpw; ++q) {
-#pragma unroll
-    for (int j = 0; j < 2 * RM; ++j) {
-      if (j < 2 * r) {
-        double v = static_cast<double>(hi[q][j]) + static_cast<double>(lo[q][j]);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) v += __shfl_down_sync(0xffffffffu, v, off);
-        if (lane == 0 && act[q]) part[(static_cast<int64_t>(tc[q]) * nchunk + chunk) * (2 * kMaxRank) + j] = v;
-      }
-    }
+  flush();
+  {
+    const int q = lane >> 4, j = lane & 15;
+    if (j < 2 * r && act[q]) part[(static_cast<int64_t>(tc[q]) * nchunk + chunk) * (2 * kMaxRank) + j] = tot;
   }
 }
 

@@ -179,10 +179,10 @@ int plan_rescore(int64_t n, int r, int m, RescorePlan* p) {
   p->n = n;
   p->r = r;
   p->m = m;
-  // blocks of (candidates x coordinate chunk): about four per SM, at most 256
-  // rows per thread (a chunk is shared by the 32 lanes of a warp), at least
-  // one staged tile of 256 rows per chunk
-  const int64_t max_rows = int64_t(32) * 256;
+  // blocks of (candidates x coordinate chunk): about four per SM, at most
+  // 65536 rows per chunk (which bounds the scratch: m x nchunk x 2 kMaxRank
+  // doubles), at least one staged tile of 256 rows per chunk
+  const int64_t max_rows = int64_t(65536);
   const int64_t bx = rescore_blocks_x(m);
   int64_t nchunk = std::max<int64_t>(ceil_div(int64_t(4) * num_sms_current(), bx), ceil_div(n, max_rows));
   nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, std::max<int64_t>(1, ceil_div(n, 256))));
