@@ -95,6 +95,18 @@ def test_workspace_queries(lib):
         lrq.lrq_sample_score_workspace_size(1 << 20, 4, 9, 1 << 16, lrq.LRQ_MODE_BF16_TC, 64)
 
 
+def test_rescore_scratch_sizes(lib):
+    # the re-scoring scratch is m x chunks x 16 doubles with at most 65536
+    # coordinates per chunk: m = 64 fits the no-alloc entry point's fixed
+    # 4 MiB up to n = 2^25, m = 4096 at n = 2^20 does not
+    from paper_2602_20376_gb300 import lrq
+    assert lrq.lrq_rescore_workspace_size(1 << 25, 4, 64) <= 4 * 1024 * 1024
+    assert lrq.lrq_rescore_workspace_size((1 << 25) + 65536, 4, 64) > 4 * 1024 * 1024
+    assert lrq.lrq_rescore_workspace_size(1 << 20, 4, 4096) > 4 * 1024 * 1024
+    # independent of the rank: the partials are sized for the largest rank
+    assert lrq.lrq_rescore_workspace_size(1 << 20, 1, 64) == lrq.lrq_rescore_workspace_size(1 << 20, 8, 64)
+
+
 @pytest.mark.parametrize("n,r,K,budget,code", [
     (0, 2, 3, 0.0, 1), (12, 0, 3, 0.0, 1), (12, 2, 1, 0.0, 1),   # invalid
     (513, 1, 3, 0.0, 2), (6, 5, 3, 0.0, 2), (12, 2, 9, 0.0, 2),  # beyond the enumerator's limits
