@@ -186,6 +186,7 @@ int plan_rescore(int64_t n, int r, int m, RescorePlan* p) {
   const int64_t bx = rescore_blocks_x(m);
   int64_t nchunk = std::max<int64_t>(ceil_div(int64_t(4) * num_sms_current(), bx), ceil_div(n, max_rows));
   nchunk = std::max<int64_t>(1, std::min<int64_t>(nchunk, std::max<int64_t>(1, ceil_div(n, 256))));
+  nchunk = std::min<int64_t>(nchunk, 65535);  // grid y limit; longer chunks are fine (periodic FP64 flushes)
   p->rows_per_chunk = ceil_div(n, nchunk);
   p->nchunk = static_cast<int>(ceil_div(n, p->rows_per_chunk));
   size_t cur = 0;
