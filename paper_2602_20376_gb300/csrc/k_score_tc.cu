@@ -636,9 +636,17 @@ __device__ __forceinline__ int b2_coord_exp(const float2* __restrict__ V, int64_
 // GEMM2 B rows (FP8 E4M3): tile t, K-chunk kc (16 reduction entries), row nr:
 // output column nr (hi part) for nr < NOUT, output column nr - NOUT (lo part,
 // the rounding remainder of hi) above
+// e_i from the coordinate's indicator magnitude byte 2^(g - e_i) (written by
+// pack_indicator_scale_kernel, below): d = g - e_i in [-9, 0]
+__device__ __forceinline__ int b2_exp_from_code(uint32_t code, int g) {
+  const int d = code >= 8u ? static_cast<int>(code >> 3) - 7 : (code == 4u ? -7 : (code == 2u ? -8 : -9));
+  return g - d;
+}
+
 template <int K, int KCH>
 __global__ void pack_b2_kernel(const float2* __restrict__ V, int64_t n, int r, int64_t n_tiles, PackTables tb,
-                               const float* __restrict__ scale, uint8_t* __restrict__ tiles) {
+                               const float* __restrict__ scale, const uint8_t* __restrict__ iwb,
+                               uint8_t* __restrict__ tiles) {
   using Sh = TcShape<K, KCH>;
   using L = TcLayout<K, KCH>;
   const int64_t total = n_tiles * L::B2ROWS;
@@ -662,7 +670,7 @@ __global__ void pack_b2_kernel(const float2* __restrict__ V, int64_t n, int r, i
       float2 v = V[ig * r + jj];
       const float br = tb.beta_r[gc], bi = tb.beta_i[gc];
       // beta conj(V) = (br vr + bi vi) + i (bi vr - br vi)
-      val = ldexpf((nc & 1) ? fmaf(bi, v.x, -br * v.y) : fmaf(br, v.x, bi * v.y), b2_coord_exp(V, ig, r, g));
+      val = ldexpf((nc & 1) ? fmaf(bi, v.x, -br * v.y) : fmaf(br, v.x, bi * v.y), b2_exp_from_code(iwb[ig], g));
     }
     const __nv_fp8_e4m3 hi(val);
     h[k] = lo ? __nv_fp8_e4m3(val - static_cast<float>(hi)).__x : hi.__x;
@@ -754,12 +762,13 @@ static int pack_impl(const ScorePlan& p, const Alphabet& a, const float2* V, con
                                                                                                            scale);
   b2_scale_kernel<<<1, 32, 0, st>>>(scale);
   count_launch(2);
-  int64_t nb = p.n_tiles * L::B2ROWS;
-  pack_b2_kernel<K, KCH><<<static_cast<unsigned>(ceil_div(nb, 256)), 256, 0, st>>>(
-      V, p.n, p.r, p.n_tiles, tb, scale, static_cast<uint8_t*>(tiles));
+  // the per-coordinate exponents first: the GEMM2 rows read them back
   const int64_t words = p.n_tiles * (Sh::ROWS / 4);
   pack_indicator_scale_kernel<<<static_cast<unsigned>(ceil_div(words, 256)), 256, 0, st>>>(V, p.n, p.r, words, scale,
                                                                                           iw);
+  int64_t nb = p.n_tiles * L::B2ROWS;
+  pack_b2_kernel<K, KCH><<<static_cast<unsigned>(ceil_div(nb, 256)), 256, 0, st>>>(
+      V, p.n, p.r, p.n_tiles, tb, scale, reinterpret_cast<const uint8_t*>(iw), static_cast<uint8_t*>(tiles));
   count_launch(2);
   int64_t nc = p.c_tiles * kTcM;
   pack_dirs_kernel<KCH><<<static_cast<unsigned>(ceil_div(nc, 256)), 256, 0, st>>>(C, p.S, p.r, p.c_tiles,
