@@ -1,9 +1,10 @@
 """Benchmark of the candidate-scoring hot path on the scale workload.
 
 One step = one pass of the whole path over one batch of synthetic input:
-draw S uniform directions (Philox, on the GPU), score them with the BF16
-tensor-core kernel (GEMM1 projections -> sector rounding -> GEMM2 per-class
-sums -> f), select the top 64, re-score those in FP64 and pick the winner.
+draw S uniform directions (Philox, on the GPU), score them with the
+tensor-core kernel (F16 GEMM1 projections -> sector rounding -> FP8 GEMM2
+per-class sums -> f), select the top 64, re-score those in FP64 and pick the
+winner.
 
 Workload: n = 2^20, r = 4, K = 3, S = 2^16 directions per step per GPU;
 V ~ CN(0,1) * diag(4, 2, 1, 0.5) in complex64 (seed 0); step s on rank g uses
@@ -11,7 +12,7 @@ direction seed 1 + s * world + g.  Metric: candidate*n evaluations per
 second (S * n per step), whole job.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--mode bf16|fp32]
-                  [--workload scale|exact|maxcut|batched|learned]
+                  [--workload scale|exact|maxcut|batched|learned|rank1|hybrid] [--sampler uniform|null]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (same metric, unit and config).
@@ -25,9 +26,12 @@ The other workloads print one line each for the remaining paths:
            2^17 BF16 candidates, FP64 rescore, exact cut count
   batched  512 instances, n log-uniform in [64, 8192], r in 2..6,
            K in {2, 3, 4, 8}: one graph-captured persistent launch
+           (--sampler null: null-vector directions instead of uniform ones)
   learned  the learned proposal at a larger training set
-  rank1    SBM n = 10^6: rank-1 Laplacian truncation, exact rank-1 sweep
-           (Algorithm 1) and the best exact cut along it
+  rank1    SBM n = 10^6: rank-2 Laplacian truncation, the two-eigenvector
+           rounding vector q = u1 + i u2, exact rank-1 sweep (Algorithm 1)
+           and the best exact cut along it
+  hybrid   rank1, then greedy local search from the sweep's best-cut state
 """
 from __future__ import annotations
 
