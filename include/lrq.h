@@ -176,6 +176,10 @@ int lrq_sample_score(const void* V, int64_t n, int r, int K, void* C, int genera
  *   best_out : 1 int64 (device): idx[t*] of the best candidate.
  *   best_f_out : 1 double (device): its f.
  *   1 <= m <= 4096; K in [2, 64]; r in [1, 8].
+ *   ws       : lrq_rescore_workspace_size(n, r, m) bytes of device memory,
+ *              owned by the caller: the per-chunk partial sums, m x chunks x
+ *              16 doubles, chunks = the larger of about four blocks of 16
+ *              candidates per SM and ceil(n / 65536), at most 65535.
  * ------------------------------------------------------------------------ */
 int lrq_rescore_workspace_size(int64_t n, int r, int m, size_t* bytes /* host */);
 int lrq_rescore(const void* V, int64_t n, int r, int K, const void* C, int64_t S, const int64_t* idx,
