@@ -26,10 +26,18 @@ of an MMA queue, a pending copy).  The checker raises ProtocolError on
   holding the wrong tiles), or a buffer overwritten before its last reader
   has consumed it.
 
+`fail_prob` > 0 also exercises the failure path: a wait that is not yet
+satisfied may give up (a bounded wait running out), exactly as the kernel's
+waits do, and then the warp carries `bad` to the rendezvous, which every warp
+leaves together (bar.red.or), or sets the CTA's abort flag, which makes every
+other unsatisfied wait give up at once.  The checker then also requires that
+no MMA or copy is outstanding when the last warp reaches the teardown (TMEM is
+freed and the CTA exits there).
+
 `mutation` plants one known mistake in the protocol (the checker must catch
 it): "refill_early" refills a stage one tile too soon, "no_a2_wait" stores A2
 without waiting for the previous GEMM2, "gemm2_early" issues GEMM2 before the
-rendezvous.
+rendezvous, "no_drain" lets warp 0 skip its drain.
 """
 from __future__ import annotations
 
@@ -93,8 +101,12 @@ def make_items(rng, n_items, max_tiles):
 class Worker:
     """One worker of the kernel; `items` is the number of tiles of each item."""
 
-    def __init__(self, items, nst, flush, seed, mutation=None):
+    def __init__(self, items, nst, flush, seed, mutation=None, fail_prob=0.0, async_weight=1.0, slow_mma0=False):
         self.rng = random.Random(seed)
+        self.async_weight = async_weight  # < 1: MMAs and copies lag behind the warps
+        self.slow_mma0 = slow_mma0  # warp 0's MMAs far slower than everything else
+        self.fail_prob = fail_prob
+        self.abort = False
         self.nst = nst
         self.F = flush
         self.mut = mutation
@@ -113,7 +125,8 @@ class Worker:
         # named barrier (rendezvous) state
         self.bar_gen = 0
         self.bar_count = 0
-        self.bar_waiting = set()
+        self.bar_or = False
+        self.bar_result = {}  # generation -> OR of the warps' flags
         # data
         self.stage = [None] * nst  # (tile, landed)
         self.dirs = [None] * 2  # (item, landed)
@@ -154,9 +167,9 @@ class Worker:
         has_next = g + 1 < self.T
         return first, item_end, last, has_next
 
-    def _wait(self, who, bar, k):
+    def _wait(self, who, bar, k, may_fail=True):
         bar.start_wait(who, k)
-        return ("wait", bar, k)
+        return ("wait", bar, k, may_fail)
 
     # ------------------------------------------------------------- data paths
     def _tma_stage(self, t):
@@ -214,6 +227,8 @@ class Worker:
 
     # ------------------------------------------------------------ warp program
     def _rounding_warp(self, w):
+        # Every wait is `ok = yield ("wait", bar, k)`: True once the phase has
+        # completed, False when it gives up (timeout or abort flag).
         nst = self.nst
         T = self.T
         lg = la = cg = ca = 0
@@ -225,28 +240,37 @@ class Worker:
                 self._tma_stage(lg)
                 lg += 1
         if w == 0 and T > 0:  # GEMM1(0) once its operands have landed
-            yield self._wait(w, self.a1_full[0], 0)
+            ok = yield self._wait(w, self.a1_full[0], 0)
             ca += 1
-            yield self._wait(w, self.full[0], 0)
-            cg += 1
-            self.mma_q[0].append(("gemm1", 0))
-            self.mma_q[0].append(("commit", self.d1_full))
+            if ok:
+                ok = yield self._wait(w, self.full[0], 0)
+                cg += 1
+            if ok:
+                self.mma_q[0].append(("gemm1", 0))
+                self.mma_q[0].append(("commit", self.d1_full))
+            else:
+                self.abort = True
         pos = 0
         pe = 0
+        bad = False
         for g in range(T):
             first, item_end, last, has_next = self._flags(g, pos)
-            yield self._wait(w, self.d1_full, g)
-            if self.d1 != g:
-                raise ProtocolError("warp %d reads D1 holding tile %r, wants %d" % (w, self.d1, g))
-            self.d1_read.setdefault(g, set()).add(w)
-            if g > 0 and self.mut != "no_a2_wait":
-                yield self._wait(w, self.a2_free, g - 1)
-            if g > 0 and (g - 1) not in self.g2_done:
-                raise ProtocolError("warp %d overwrites A2 before GEMM2(%d) read it" % (w, g - 1))
-            self.a2[w] = g
-            if w == 2 and self.mut == "gemm2_early":
-                self._issue_gemm2(g, first, last)
-            yield ("rendezvous",)
+            if not bad:
+                bad = not (yield self._wait(w, self.d1_full, g))
+            if not bad:
+                if self.d1 != g:
+                    raise ProtocolError("warp %d reads D1 holding tile %r, wants %d" % (w, self.d1, g))
+                self.d1_read.setdefault(g, set()).add(w)
+                if g > 0 and self.mut != "no_a2_wait":
+                    bad = not (yield self._wait(w, self.a2_free, g - 1))
+                if not bad:
+                    if g > 0 and (g - 1) not in self.g2_done:
+                        raise ProtocolError("warp %d overwrites A2 before GEMM2(%d) read it" % (w, g - 1))
+                    self.a2[w] = g
+                    if w == 2 and self.mut == "gemm2_early":
+                        self._issue_gemm2(g, first, last)
+            if (yield ("rendezvous", bad)):
+                break  # every warp leaves here together
             if w == 1:
                 limit = g + nst if self.mut == "refill_early" else g - 1 + nst
                 while lg <= limit and lg < T:
@@ -256,35 +280,44 @@ class Worker:
                     self._tma_dirs(la)
                     la += 1
             if w == 0 and has_next:
+                ok = True
                 if item_end:
-                    yield self._wait(w, self.a1_full[ca % 2], ca // 2)
+                    ok = yield self._wait(w, self.a1_full[ca % 2], ca // 2)
                     ca += 1
-                yield self._wait(w, self.full[cg % nst], cg // nst)
-                cg += 1
-                self.mma_q[0].append(("gemm1", g + 1))
-                self.mma_q[0].append(("commit", self.d1_full))
+                if ok:
+                    ok = yield self._wait(w, self.full[cg % nst], cg // nst)
+                    cg += 1
+                if ok:
+                    self.mma_q[0].append(("gemm1", g + 1))
+                    self.mma_q[0].append(("commit", self.d1_full))
+                else:
+                    self.abort = True
             if w == 2 and self.mut != "gemm2_early":
                 self._issue_gemm2(g, first, last)
             if last:
-                yield self._wait(w, self.d2_ready, pe)
+                bad = not (yield self._wait(w, self.d2_ready, pe))
+                if not bad:
+                    p = self.period_of[g]
+                    if self.d2 is None or self.d2[0] != p or self.d2[1] != self.period_tiles[p]:
+                        raise ProtocolError("warp %d folds period %d from D2 holding %r" % (w, p, self.d2))
+                    self.folded.setdefault(p, set()).add(w)
                 pe += 1
-                p = self.period_of[g]
-                if self.d2 is None or self.d2[0] != p or self.d2[1] != self.period_tiles[p]:
-                    raise ProtocolError("warp %d folds period %d from D2 holding %r" % (w, p, self.d2))
-                self.folded.setdefault(p, set()).add(w)
             pos = 0 if last else pos + 1
-        # drain
-        if w == 0:
+        if bad:
+            self.abort = True
+        # drain: the MMAs of warps 0 and 2 and the loader's copies complete
+        # before TMEM is freed (these waits never give up early)
+        if w == 0 and self.mut != "no_drain":
             self.mma_q[0].append(("commit", self.drain))
-            yield self._wait(w, self.drain, 0)
+            yield self._wait(w, self.drain, 0, may_fail=False)
         if w == 2:
             self.mma_q[2].append(("commit", self.drain2))
-            yield self._wait(w, self.drain2, 0)
+            yield self._wait(w, self.drain2, 0, may_fail=False)
         if w == 1:
             for t in range(max(0, lg - nst), lg):
-                yield self._wait(w, self.full[t % nst], t // nst)
+                yield self._wait(w, self.full[t % nst], t // nst, may_fail=False)
             for t in range(max(0, la - 2), la):
-                yield self._wait(w, self.a1_full[t % 2], t // 2)
+                yield self._wait(w, self.a1_full[t % 2], t // 2, may_fail=False)
 
     def _issue_gemm2(self, g, first, last):
         self.mma_q[2].append(("gemm2", g, first))
@@ -300,32 +333,43 @@ class Worker:
                 continue
             req = self.blocked.get(w)
             if req is None:
-                agents.append(("warp", w))
-            elif req[0] == "wait" and req[1].ready(req[2]):
-                agents.append(("warp", w))
-            elif req[0] == "rendezvous" and self.bar_gen > req[1]:
-                agents.append(("warp", w))
+                agents.append(("warp", w, None))
+            elif req[0] == "wait":
+                bar, k, may_fail = req[1], req[2], req[3]
+                if bar.ready(k):
+                    agents.append(("warp", w, True))
+                elif may_fail and self.abort:
+                    agents.append(("warp", w, False))  # the abort flag: give up at once
+                elif may_fail and self.fail_prob > 0 and self.rng.random() < self.fail_prob:
+                    agents.append(("warp", w, False))  # the bounded wait runs out
+            elif req[0] == "rendezvous" and req[1] in self.bar_result:
+                agents.append(("warp", w, self.bar_result[req[1]]))
         for q in (0, 2):
             if self.mma_q[q]:
-                agents.append(("mma", q))
+                agents.append(("mma", q, None))
         for idx in range(len(self.tma)):
-            agents.append(("tma", idx))
+            agents.append(("tma", idx, None))
+        if self.slow_mma0 and self.mma_q[0]:
+            agents.append(("tick", None, None))  # time passes, nothing completes
         return agents
 
-    def _step_warp(self, w):
+    def _step_warp(self, w, value):
         req = self.blocked.pop(w, None)
         if req is not None and req[0] == "wait":
             req[1].end_wait(w)
         try:
-            nxt = next(self.gens[w])
+            nxt = self.gens[w].send(value) if req is not None else next(self.gens[w])
         except StopIteration:
             self.finished.add(w)
             return
         if nxt[0] == "rendezvous":
-            self.bar_count += 1
             gen = self.bar_gen
+            self.bar_or = self.bar_or or bool(nxt[1])
+            self.bar_count += 1
             if self.bar_count == 4:
+                self.bar_result[gen] = self.bar_or
                 self.bar_count = 0
+                self.bar_or = False
                 self.bar_gen += 1
             self.blocked[w] = ("rendezvous", gen)
         else:
@@ -350,16 +394,24 @@ class Worker:
 
     def run(self, max_steps=200000):
         for _ in range(max_steps):
-            if len(self.finished) == 4 and not self.tma and not self.mma_q[0] and not self.mma_q[2]:
+            if len(self.finished) == 4:
+                # the teardown: TMEM is freed and the CTA exits
+                if self.tma or self.mma_q[0] or self.mma_q[2]:
+                    raise ProtocolError("teardown with work in flight: %d copies, MMA queues %r"
+                                        % (len(self.tma), {q: len(v) for q, v in self.mma_q.items()}))
                 return
             agents = self._enabled()
             if not agents:
                 raise ProtocolError("deadlock: warps %r blocked on %r" % (
                     sorted(set(range(4)) - self.finished),
                     {w: (r[1].name, r[2]) if r[0] == "wait" else r for w, r in self.blocked.items()}))
-            kind, a = agents[self.rng.randrange(len(agents))]
+            weights = [1.0 if ag[0] == "warp" else
+                       (0.002 if self.slow_mma0 and ag[:2] == ("mma", 0) else self.async_weight) for ag in agents]
+            kind, a, value = self.rng.choices(agents, weights)[0]
+            if kind == "tick":
+                continue
             if kind == "warp":
-                self._step_warp(a)
+                self._step_warp(a, value)
             elif kind == "mma":
                 self._step_mma(a)
             else:
@@ -367,6 +419,9 @@ class Worker:
         raise ProtocolError("no progress within %d steps" % max_steps)
 
 
-def check(items, nst, flush, seed, mutation=None):
-    """Run one random schedule of a worker over `items`; raises ProtocolError."""
-    Worker(items, nst, flush, seed, mutation).run()
+def check(items, nst, flush, seed, mutation=None, fail_prob=0.0, async_weight=1.0, slow_mma0=False):
+    """Run one random schedule of a worker over `items`; raises ProtocolError.
+    Returns the worker (its `abort` flag says whether a wait gave up)."""
+    wk = Worker(items, nst, flush, seed, mutation, fail_prob, async_weight, slow_mma0)
+    wk.run()
+    return wk

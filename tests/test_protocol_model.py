@@ -1,7 +1,9 @@
 """The per-worker synchronisation protocol of the tensor-core scoring kernel,
 model-checked on random schedules (tests/protocol_model.py mirrors the
 kernel's program step for step): no deadlock, no parity wait that could
-alias, no data hazard -- and each planted mistake is caught."""
+alias, no data hazard, and on the failure path (bounded waits running out)
+every warp leaves together with nothing in flight at the teardown -- and
+each planted mistake is caught."""
 import random
 
 import pytest
@@ -28,14 +30,39 @@ def test_protocol_holds_on_random_schedules(n_items, max_tiles, nst, flush):
         check(items, nst, flush, seed=rng.randrange(1 << 30))
 
 
-@pytest.mark.parametrize("mutation", ["refill_early", "no_a2_wait", "gemm2_early"])
-def test_planted_mistakes_are_caught(mutation):
+@pytest.mark.parametrize("async_weight", [1.0, 0.05])
+@pytest.mark.parametrize("fail_prob", [0.002, 0.05])
+def test_failure_path_leaves_together_and_drains(fail_prob, async_weight):
+    # bounded waits that run out (at random unsatisfied waits): every warp
+    # leaves at the same rendezvous, and nothing is in flight at the teardown
+    rng = random.Random(int(fail_prob * 1000) + int(async_weight * 100))
+    aborted = 0
+    for trial in range(150):
+        items = make_items(rng, 3, 5)
+        wk = check(items, 3, 2, seed=rng.randrange(1 << 30), fail_prob=fail_prob, async_weight=async_weight)
+        aborted += wk.abort
+    assert aborted > 0
+
+
+def test_failure_path_with_slow_mma():
+    rng = random.Random(21)
+    for trial in range(150):
+        check(make_items(rng, 3, 6), 3, 2, seed=rng.randrange(1 << 30), fail_prob=0.05, slow_mma0=True)
+
+
+@pytest.mark.parametrize("mutation,opts", [
+    ("refill_early", {}),
+    ("no_a2_wait", {}),
+    ("gemm2_early", {}),
+    ("no_drain", {"fail_prob": 0.05, "slow_mma0": True}),
+])
+def test_planted_mistakes_are_caught(mutation, opts):
     rng = random.Random(7)
     caught = 0
     for trial in range(200):
         items = make_items(rng, 3, 6)
         try:
-            check(items, 3, 2, seed=rng.randrange(1 << 30), mutation=mutation)
+            check(items, 3, 2, seed=rng.randrange(1 << 30), mutation=mutation, **opts)
         except ProtocolError:
             caught += 1
     assert caught > 0
