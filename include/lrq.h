@@ -58,7 +58,8 @@ typedef enum {
 
 typedef enum {
   LRQ_MODE_FP32 = 0,     /* CUDA-core FP32 scoring                                      */
-  LRQ_MODE_BF16_TC = 1   /* tcgen05 tensor-core scoring: F16 signs, FP8 x2 class sums, FP32 accumulate */
+  LRQ_MODE_TC = 1,       /* tcgen05 tensor-core scoring: F16 signs, FP8 x2 class sums, FP32 accumulate */
+  LRQ_MODE_BF16_TC = 1   /* the same mode under its first name (its operands were BF16 then) */
 } lrq_mode;
 
 /* Human-readable name of a status code (static string, never NULL). */

@@ -26,7 +26,8 @@ LRQ_ENOCONV = 5
 LRQ_EWORKSPACE = 6
 
 LRQ_MODE_FP32 = 0
-LRQ_MODE_BF16_TC = 1
+LRQ_MODE_TC = 1  # tensor-core mode: F16 signs, FP8 class sums
+LRQ_MODE_BF16_TC = LRQ_MODE_TC  # its first name
 
 _lock = threading.Lock()
 _lib = None
