@@ -30,6 +30,13 @@ def test_protocol_holds_on_random_schedules(n_items, max_tiles, nst, flush):
         check(items, nst, flush, seed=rng.randrange(1 << 30))
 
 
+def test_worker_without_items():
+    # a worker the grid has no item for still commits and waits its drains
+    for seed in range(20):
+        check([], 3, 2, seed=seed)
+        check([], 8, 64, seed=seed, fail_prob=0.05)
+
+
 @pytest.mark.parametrize("async_weight", [1.0, 0.05])
 @pytest.mark.parametrize("fail_prob", [0.002, 0.05])
 def test_failure_path_leaves_together_and_drains(fail_prob, async_weight):
