@@ -470,7 +470,7 @@ def check_status(dev_status: torch.Tensor, where: str = "device"):
         raise LrqError(s, where, lrq_status_string(s))
 
 
-def sample_score(V, K, C=None, S=None, seed=0, mode=LRQ_MODE_BF16_TC, top_m=64, want_scores=False,
+def sample_score(V, K, C=None, S=None, seed=0, mode=LRQ_MODE_TC, top_m=64, want_scores=False,
                  ws=None, dev_status=None, stream=None):
     """Score S directions (given in C, or drawn from `seed` into a new C).
     Returns dict(C, top_idx, top_f, scores, dev_status)."""
