@@ -70,8 +70,10 @@ def _config(mode: str, world: int):
 # ncu capture of the launch after the L2 flush: 72.44 MB read + 137.84 MB
 # written (the FP64 partials, S x 2r doubles per coordinate chunk, dominate
 # the writes; part of them is still in L2 when the kernel ends).
-# The command that measured it is in profiles/score_tc_kernel_n2e20_S2e16_dram.md;
-# it must be taken again whenever the kernel changes.
+# Measured with
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
+#       -k regex:score_tc -s 1 -c 1 python bench.py --steps 1 --warmup 1 --no-cpu-baseline --no-learned
+# (one pass); it must be taken again whenever the kernel changes.
 SCALE_TRAFFIC_BYTES = 72.44e6 + 137.84e6
 
 

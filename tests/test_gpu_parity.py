@@ -1,13 +1,13 @@
 """GPU parity: the CUDA path through the C ABI against the FP64 oracle on the
 same seeded inputs.
 
-Tolerances (stated here, derived in the design doc):
+Tolerances (each derived from the arithmetic of the path it bounds):
 * FP32 scoring: f within 1e-5 relative of the oracle.
 * FP64 re-scoring: f within 1e-9 relative; codes equal the oracle's except
   where the oracle's own angle margin to a boundary is below 1e-9 rad (a tie
   in FP64 arithmetic).
 * Tensor-core scoring: per candidate, |sqrt(f) - sqrt(f_oracle)| within
-  the error bound of _bf16_bound (decision flips only where the oracle's
+  the error bound of _tc_bound (decision flips only where the oracle's
   margin is inside the F16 projection error, plus the hi + lo E4M3
   rounding of the per-class sums' operand); median relative error below 3e-3 for
   n >= 1000.  The winner is decided after the FP64 re-scoring above.
@@ -117,8 +117,8 @@ def test_rescore_rejects_out_of_range_index(lrq):
 # ---------------------------------------------------------------------------
 # tensor-core scoring (tcgen05 + TMEM + TMA)
 # ---------------------------------------------------------------------------
-def _bf16_bound(V, K, C):
-    """Per-candidate bound on |sqrt(f_bf16) - sqrt(f)| for the BF16 mode.
+def _tc_bound(V, K, C):
+    """Per-candidate bound on |sqrt(f_tc) - sqrt(f)| for the tensor-core mode.
 
     GEMM1 scales each row and direction by a power of two (no effect on the
     signs), rounds both operands to F16 (unit roundoff 2^-11) and accumulates
@@ -157,7 +157,7 @@ def _check_bf16(lrq, n, r, K, S, top_m, seed=0):
     out = _score(lrq, V, K, C, BF16, top_m)
     f = out["scores"].cpu().numpy().astype(np.float64)
     ref = O.score(V, K, C)
-    bound = _bf16_bound(V, K, C) + 1e-5 * np.sqrt(ref)
+    bound = _tc_bound(V, K, C) + 1e-5 * np.sqrt(ref)
     dev = np.abs(np.sqrt(f) - np.sqrt(ref))
     assert np.all(dev <= bound), (np.max(dev / bound), np.argmax(dev / bound))
     rel = np.abs(f - ref) / ref
@@ -209,7 +209,7 @@ def test_score_bf16_heavy_tailed_rows(lrq, K):
     out = _score(lrq, V, K, C, BF16, 8)
     f = out["scores"].cpu().numpy().astype(np.float64)
     ref = O.score(V, K, C)
-    bound = _bf16_bound(V, K, C) + 1e-5 * np.sqrt(ref)
+    bound = _tc_bound(V, K, C) + 1e-5 * np.sqrt(ref)
     dev = np.abs(np.sqrt(f) - np.sqrt(ref))
     assert np.all(dev <= bound), (np.max(dev / bound), np.argmax(dev / bound))
     assert np.median(np.abs(f - ref) / ref) < 3e-3

@@ -1,5 +1,5 @@
 """The error bound the GPU parity tests allow the tensor-core scoring mode
-(test_gpu_parity._bf16_bound), checked against a numpy emulation of that
+(test_gpu_parity._tc_bound), checked against a numpy emulation of that
 mode's arithmetic (tests/tc_emulator.py: F16 projections with F16
 accumulation, sign decisions, hi + lo E4M3 class sums in FP32): the
 emulated scores stay inside the bound, including on rows spread over many
@@ -10,7 +10,7 @@ import pytest
 import oracle as O
 import tc_emulator as E
 from paper_2602_20376_gb300 import inputs as I
-from test_gpu_parity import _bf16_bound
+from test_gpu_parity import _tc_bound
 
 
 def test_e4m3_rounding():
@@ -32,7 +32,7 @@ def test_emulated_scores_within_the_bound(n, r, K, S, seed):
     C = I.directions(S, r, seed=seed + 100)
     f = E.score(V, K, C)
     ref = O.score(V, K, C)
-    bound = _bf16_bound(V, K, C) + 1e-5 * np.sqrt(ref)
+    bound = _tc_bound(V, K, C) + 1e-5 * np.sqrt(ref)
     dev = np.abs(np.sqrt(f) - np.sqrt(ref))
     assert np.all(dev <= bound), (np.max(dev / bound), np.argmax(dev / bound))
     assert np.max(dev / bound) > 1e-4  # the bound is not vacuous
@@ -47,7 +47,7 @@ def test_emulated_heavy_tailed_rows_within_the_bound(K):
     C = I.directions(32, 4, seed=10)
     f = E.score(V, K, C)
     ref = O.score(V, K, C)
-    bound = _bf16_bound(V, K, C) + 1e-5 * np.sqrt(ref)
+    bound = _tc_bound(V, K, C) + 1e-5 * np.sqrt(ref)
     assert np.all(np.abs(np.sqrt(f) - np.sqrt(ref)) <= bound)
 
 
@@ -60,6 +60,6 @@ def test_k3_middle_line_needs_one_scale_per_coordinate():
     V = (V * (10.0 ** rng.uniform(-10, 0, size=64))[:, None]).astype(np.complex64)
     C = I.directions(32, 4, seed=10)
     ref = O.score(V, 3, C)
-    bound = _bf16_bound(V, 3, C) + 1e-5 * np.sqrt(ref)
+    bound = _tc_bound(V, 3, C) + 1e-5 * np.sqrt(ref)
     f = E.score(V, 3, C, per_line_scale=True)
     assert np.any(np.abs(np.sqrt(f) - np.sqrt(ref)) > bound)
