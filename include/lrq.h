@@ -470,7 +470,8 @@ int lrq_enumerate(const void* V, int64_t n, int r, int K, double budget, uint8_t
  *   row-major (in x out).  X: B x F; H1, H2: B x 256 (written by forward,
  *   read by backward); O: B x 160.  backward: dO (B x 160) -> grads (same
  *   layout as params), scratch: 2 B x 256 floats.  bf16 != 0 rounds every
- *   GEMM operand to bfloat16 (products accumulate in FP32).
+ *   GEMM operand to bfloat16 (products accumulate in FP32).  1 <= B <=
+ *   2097120 (LRQ_EUNSUPPORTED above).
  * lrq_vmf_nll: O (B x 160): per component m, outputs 10m..10m+7 give
  *   mu_m = u / ||u||, 10m+8 gives kappa_m = softplus, 10m+9 the mixture
  *   logit.  targets: B x T x 8 unit vectors.  loss_out (1 double, device):

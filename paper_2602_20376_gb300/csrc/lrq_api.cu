@@ -52,6 +52,10 @@ int cuda_check(cudaError_t e, const char* what) {
   return fail(LRQ_ECUDA, std::string(what) + ": " + cudaGetErrorString(e));
 }
 
+// The MLP's GEMMs tile the batch rows 32 at a time on the grid's y axis
+// (at most 65535 blocks).
+constexpr int kMaxMlpBatch = 65535 * 32;
+
 int num_sms_current() {
   static std::mutex mu;
   static int cache[64] = {0};
@@ -372,6 +376,7 @@ int lrq_proposal_features(const void* V, int B, int64_t n, int r, const double* 
 int lrq_mlp_forward(const float* params, int F, int B, const float* X, float* H1, float* H2, float* O, int bf16,
                     void* stream) {
   if (F < 1 || B < 1) return fail(LRQ_EINVAL, "bad sizes");
+  if (B > kMaxMlpBatch) return fail(LRQ_EUNSUPPORTED, "at most 2097120 rows per MLP call");
   if (!params || !X || !H1 || !H2 || !O) return fail(LRQ_EINVAL, "NULL pointer argument");
   return launch_mlp_forward(params, F, B, X, H1, H2, O, bf16 ? 1 : 0, static_cast<cudaStream_t>(stream));
 }
@@ -379,6 +384,7 @@ int lrq_mlp_forward(const float* params, int F, int B, const float* X, float* H1
 int lrq_mlp_backward(const float* params, int F, int B, const float* X, const float* H1, const float* H2,
                      const float* dO, float* grads, float* scratch, int bf16, void* stream) {
   if (F < 1 || B < 1) return fail(LRQ_EINVAL, "bad sizes");
+  if (B > kMaxMlpBatch) return fail(LRQ_EUNSUPPORTED, "at most 2097120 rows per MLP call");
   if (!params || !X || !H1 || !H2 || !dO || !grads || !scratch) return fail(LRQ_EINVAL, "NULL pointer argument");
   return launch_mlp_backward(params, F, B, X, H1, H2, dO, grads, scratch, bf16 ? 1 : 0,
                              static_cast<cudaStream_t>(stream));

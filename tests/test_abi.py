@@ -95,6 +95,15 @@ def test_workspace_queries(lib):
         lrq.lrq_sample_score_workspace_size(1 << 20, 4, 9, 1 << 16, lrq.LRQ_MODE_BF16_TC, 64)
 
 
+def test_mlp_batch_limit(lib):
+    # the MLP's GEMMs put the batch rows on the grid's y axis, 32 per block
+    P = ctypes.c_void_p
+    dummy = P(256)
+    args = (dummy, 24, 65535 * 32 + 1, dummy, dummy, dummy, dummy, 0, None)
+    assert lib.lrq_mlp_forward(*args) == 2  # LRQ_EUNSUPPORTED
+    assert lib.lrq_mlp_backward(dummy, 24, 65535 * 32 + 1, dummy, dummy, dummy, dummy, dummy, dummy, 0, None) == 2
+
+
 def test_rescore_scratch_sizes(lib):
     # the re-scoring scratch is m x chunks x 16 doubles with at most 65536
     # coordinates per chunk: m = 64 fits the no-alloc entry point's fixed
