@@ -33,27 +33,41 @@
 // significant bits (like BF16).  hi and lo are separate output columns
 // (N = 2 x 8, or 2 x 16 for r > 4); the epilogue adds them and divides by s.
 // An FP8 MMA reduces 32 entries where a BF16 one reduces 16, so GEMM2 takes
-// half the MMA instructions (N is the problem's 2r outputs, so the MMAs are
-// small and the kernel is bounded by each worker's per-tile chain of waits,
-// issues and rounding, not by arithmetic).  D2 accumulates in TMEM (FP32) for
-// at most `flush` tiles, then is folded into FP32 two-sum registers
-// (error-free) and written as FP64 partials per coordinate chunk.
+// half the MMA instructions.  D2 accumulates in TMEM (FP32) over an
+// accumulation period of at most 2048 coordinates, then is folded into FP32
+// two-sum registers (error-free) and written as FP64 partials per coordinate
+// chunk.
 //
-// Pipeline (one CTA per SM, persistent over (chunk, candidate tile) items):
-// NW independent workers per CTA, each a warpgroup (one thread per candidate
-// of the 128-candidate tile) with its own stage ring and TMEM slice (D1
-// projections, A2 indicator words, D2 accumulator).  Per tile, after the
-// warpgroup has turned D1 into indicator words in A2 and met at a barrier,
-// its warp 0 issues GEMM1 of the next tile and its warp 2 GEMM2 of this one,
-// each from the whole converged warp through one elected lane (measured:
-// about a third of the cost of issuing from a lone active lane).  Separate
-// commits (D1 ready; A2 free) let the two run side by side; the rounding
-// threads wait for "A2 free" only just before they overwrite A2.  One lane of
-// warp 1 keeps the stage ring full: a stage is free once both GEMMs of its
-// tile are known complete; each packed tile -- GEMM1 rows and GEMM2 rows -- is
-// one TMA box.  The workers of a CTA interleave on the tensor core.  Every
-// wait is bounded; on expiry the kernel records LRQ_ETIMEOUT, drains its
-// in-flight copies and MMAs, frees TMEM and returns.
+// Pipeline (one CTA per SM, persistent over (chunk, candidate tile) items,
+// every role a warp or warpgroup of its own, all hand-offs through
+// mbarriers):
+//   TMA warp      fills a ring of NS stages (one packed coordinate tile each:
+//                 GEMM1 rows | GEMM2 rows | indicator magnitudes, one box)
+//                 and two direction buffers (one per item);
+//   GEMM1 warp    issues tile g's projections into the D1 buffer g % ND of a
+//                 ring of ND buffers in tensor memory, ahead of the rounding;
+//   rounding      two warpgroups, one thread per candidate row; warpgroup
+//                 g % 2 takes tile g: loads D1, releases the buffer at once,
+//                 turns the projections into indicator words and stores them
+//                 into its own A2 buffer;
+//   GEMM2 warps   one per rounding warpgroup (small MMAs cost their issuing
+//                 thread tens of cycles each, so two threads issue them):
+//                 GEMM2 warp w issues warpgroup w's tiles from A2[w] into
+//                 warpgroup w's accumulator D2[w][p % 2], p the warpgroup's
+//                 accumulation period (at most 2048 coordinates of one item);
+//   fold          a warpgroup that owns the two-sum partials: per item it
+//                 reads period i of warpgroup 0, then period i of warpgroup
+//                 1, for i = 0, 1, ..., releases each accumulator, and writes
+//                 the item's FP64 partials at its end.
+// The rounding warpgroups, which do all the per-evaluation work, never wait
+// for an MMA they have just asked for: D1 of their next tile was issued while
+// they rounded the previous ones, and their A2 buffer was released by a GEMM2
+// issued a tile earlier.  Every wait is an mbarrier try_wait loop (try_wait
+// blocks in hardware until the phase completes or a time limit passes) and
+// is bounded; on expiry the kernel records LRQ_ETIMEOUT, every role leaves
+// its loop, in-flight
+// copies and MMAs are drained, TMEM is freed and the CTA returns.  The
+// protocol is model-checked on the CPU (tests/protocol_model.py).
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
@@ -70,18 +84,18 @@
 namespace lrq {
 
 constexpr int kTcM = 128;
-constexpr int kTcStages = 8;
-constexpr int kTcFlush = 64;
+constexpr int kTcMaxStages = 24;
+constexpr int kTcPeriodCoords = 2048;  // coordinates per FP32 accumulation period
 constexpr long long kWaitLimit = 2000000000LL;
+constexpr int kTcThreads = 512;  // 16 warps: 2 rounding warpgroups, TMA, GEMM1, 2 x GEMM2, fold warpgroup
+constexpr int kWarpTma = 8, kWarpG1 = 9, kWarpG2 = 10, kWarpFold0 = 12;  // GEMM2 warps 10 and 11
 
-// Tile shape per alphabet and rank class (KCH = 1 for r <= 4, 2 above).  A
-// CTA runs NW independent workers; each worker is one warpgroup (128
-// threads, one per candidate of the tile) and owns a TMEM slice of WCOLS
-// columns:
-//   D1 : N1 = BKG * R columns    GEMM1 projections of one tile
-//   A2 : KD2 / 4 columns         GEMM2 indicator operand (4 FP8 per column)
-//   D2 : N2 = 2 * NOUT columns   GEMM2 accumulator, hi | lo
-// NW * WCOLS <= 512.  R is the number of coordinates per tile.
+// Tile shape per alphabet and rank class (KCH = 1 for r <= 4, 2 above).  R is
+// the number of coordinates per tile.  Tensor memory (512 columns of 128
+// lanes) holds
+//   D1 : ND buffers of N1 = BKG * R columns   GEMM1 projections (F16, one per column)
+//   A2 : 2 buffers of KD2 / 4 columns         GEMM2 indicator operand (4 FP8 per column), one per warpgroup
+//   D2 : 2 x 2 buffers of N2 = 2 * NOUT cols  GEMM2 accumulators, hi | lo, two per warpgroup
 template <int K, int KCH>
 struct TcShape {
   static constexpr int BK = (K % 2 == 0) ? K / 2 : K;
@@ -90,27 +104,31 @@ struct TcShape {
   // CUDA cores
   static constexpr int BKG = (K == 3) ? 2 : BK;
   static constexpr int G = (K % 2 == 0) ? K / 2 : K - 1;
-  static constexpr int R = K == 2 ? 64 : K == 7 ? 16 : 32;
+  static constexpr int R = K == 2 ? 128 : (K == 3 || K == 4) ? 64 : K == 7 ? 16 : 32;
   static constexpr int ROWS = R;  // coordinates per tile (packing granularity)
   static constexpr int N1 = BKG * R;   // GEMM1 N
   static constexpr int KD2 = G * R;    // GEMM2 reduction length per tile
   static constexpr int A2COLS = KD2 / 4;
   static constexpr int NOUT = KCH == 1 ? 8 : 16;  // real outputs per candidate (>= 2r)
   static constexpr int N2 = 2 * NOUT;             // GEMM2 N: hi and lo halves
-  static constexpr int WCOLS = N1 + A2COLS + N2;
-  static constexpr int NW = (512 / WCOLS) < 5 ? (512 / WCOLS) : 5;
-  static constexpr int D1_OFF = 0, A2_OFF = N1, D2_OFF = N1 + A2COLS;
-  static_assert(NW >= 1 && NW * WCOLS <= 512, "TMEM budget");
+  static constexpr int ND = (3 * N1 + 2 * A2COLS + 4 * N2 <= 512) ? 3 : 2;
+  static constexpr int D1_OFF = 0;
+  static constexpr int A2_OFF = ND * N1;
+  static constexpr int D2_OFF = A2_OFF + 2 * A2COLS;
+  static constexpr int TMEM_COLS = D2_OFF + 4 * N2;
+  static_assert(TMEM_COLS <= 512, "TMEM budget");
   static_assert(N1 % 16 == 0 && N1 <= 256, "GEMM1 N");
   static_assert(KD2 % 32 == 0, "GEMM2 K (FP8 MMAs reduce 32 entries)");
-  static_assert(R % 16 == 0, "rows are processed 16 at a time");
+  static_assert(R % 16 == 0 && R <= 128, "rows are processed 16 at a time; magnitudes fit one 256-byte row");
   static_assert(A2COLS % 8 == 0, "indicator words are stored 8 columns at a time");
-  static constexpr int THREADS = 128 * NW;
+  // coordinates per tensor-memory load: 32 (x16 packed loads) unless the
+  // lines of 32 coordinates would not fit the rounding thread's registers
+  static constexpr int RC = (R >= 32 && BKG * 16 <= 64) ? 32 : 16;
+  // a warpgroup's tiles per accumulation period
+  static constexpr int FLUSH = kTcPeriodCoords / R;
   // boundary line whose projections fill GEMM1 row block b
   static constexpr __host__ __device__ int line(int b) { return (K == 3 && b == 1) ? 2 : b; }
 };
-
-constexpr int align1k(int x) { return (x + 1023) / 1024 * 1024; }
 
 template <int K, int KCH>
 struct TcLayout {
@@ -119,32 +137,31 @@ struct TcLayout {
   static constexpr int B2ROWS = Sh::KD2 / 16 * N2R;       // 16-byte rows of B2 per tile
   static constexpr int B1_BYTES = Sh::N1 * 16 * KCH;
   static constexpr int B2_BYTES = B2ROWS * 16;
+  static constexpr int MAG_BYTES = 256;                   // R indicator-magnitude bytes, padded
   static_assert(B1_BYTES % 256 == 0 && B2_BYTES % 256 == 0, "tiles are whole 256-byte TMA rows");
-  // one packed tile = GEMM1 rows | GEMM2 rows, contiguous: one TMA box
-  static constexpr int TILE_BYTES = B1_BYTES + B2_BYTES;
-  static_assert(TILE_BYTES / 256 <= 256, "TMA box height");
+  // one packed tile = GEMM1 rows | GEMM2 rows | magnitudes, contiguous: one TMA box
   static constexpr int B1_OFF_IN_STAGE = 0;
   static constexpr int B2_OFF_IN_STAGE = B1_BYTES;
-  static constexpr int STAGE_BYTES = align1k(TILE_BYTES);
+  static constexpr int MAG_OFF_IN_STAGE = B1_BYTES + B2_BYTES;
+  static constexpr int TILE_BYTES = B1_BYTES + B2_BYTES + MAG_BYTES;
+  static_assert(TILE_BYTES / 256 <= 256, "TMA box height");
+  static constexpr int STAGE_BYTES = TILE_BYTES;          // a multiple of 256: TMA destinations stay aligned
   static constexpr uint32_t STAGE_TX = TILE_BYTES;
   static constexpr int A1_BYTES = kTcM * 16 * KCH;
-  static constexpr int ACC_BYTES = kTcM * 16 * 8;         // two-sum partials, 128 x 16 x (hi, lo)
   static constexpr int ZERO_BYTES = 4096;
-  static constexpr int WFIXED = align1k(2 * A1_BYTES) + ACC_BYTES;
-  static constexpr int NST_FIT = (200 * 1024 - ZERO_BYTES - 4096 - Sh::NW * WFIXED) / (Sh::NW * STAGE_BYTES);
-  static constexpr int NST = NST_FIT < kTcStages ? NST_FIT : kTcStages;  // stages per worker
-  static_assert(NST >= 3, "pipeline depth");
-  static constexpr int WSMEM = NST * STAGE_BYTES + WFIXED;  // per worker: stages | A1 x 2 | ACC
-  static constexpr int W_A1 = NST * STAGE_BYTES;
-  static constexpr int W_ACC = W_A1 + align1k(2 * A1_BYTES);
-  static constexpr int ZERO_OFF = Sh::NW * WSMEM;
+  static constexpr int NBARS = 2 * kTcMaxStages + 2 + 2 + 2 * 3 + 2 + 2 + 4 + 4 + 3;
+  static constexpr int FIXED = 2 * A1_BYTES + ZERO_BYTES + NBARS * 8 + 64;
+  // at least 120 KB of shared memory, so that two CTAs never share an SM
+  // (each holds all 512 TMEM columns); the stage ring takes what is left
+  static constexpr int NS_FIT = (120 * 1024 - FIXED) / STAGE_BYTES;
+  static constexpr int NS = NS_FIT < kTcMaxStages ? NS_FIT : kTcMaxStages;
+  static_assert(NS >= 4, "pipeline depth");
+  static constexpr int DIRS_OFF = NS * STAGE_BYTES;
+  // the zero region lies above every operand: the descriptors' K-direction
+  // byte offsets (LBO) to it are positive
+  static constexpr int ZERO_OFF = DIRS_OFF + 2 * A1_BYTES;
   static constexpr int BAR_OFF = ZERO_OFF + ZERO_BYTES;
-  // per worker: full per stage, A1 full x 2, D1-full, D2-ready, drain of the
-  // GEMM1 warp, A2-free, drain of the GEMM2 warp
-  static constexpr int WBARS = NST + 7;
-  static constexpr int USED = BAR_OFF + Sh::NW * WBARS * 8 + 16;
-  // at least 120 KB so that two CTAs never share an SM (each holds all 512
-  // TMEM columns)
+  static constexpr int USED = BAR_OFF + NBARS * 8 + 64;
   static constexpr int TOTAL = USED < 120 * 1024 ? 120 * 1024 : USED;
   static_assert(Sh::N1 * 16 <= ZERO_BYTES && kTcM * 16 <= ZERO_BYTES, "zero pad");
   static_assert(TOTAL <= 227 * 1024, "shared memory");
@@ -157,7 +174,6 @@ struct TcParams {
   int64_t num_items;
   int64_t S_pad;
   int r;
-  int flush;
 };
 
 __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) {
@@ -166,83 +182,151 @@ __device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& e) 
   e = (a - (s - bb)) + (b - bb);
 }
 
-// Every lane of the warp polls the barrier and the warp agrees on the outcome
-// (measured: cheaper than one lane polling while the rest of its warp waits).
+// Every lane of the warp polls and the warp agrees on the outcome.  A
+// try_wait blocks in hardware for a while before it reports an incomplete
+// phase (measured: faster here than a try_wait with a suspend-time hint).
 __device__ __forceinline__ bool warp_wait(uint64_t* bar, uint32_t parity, volatile int* abort) {
   const bool ok = ptx::mbar_wait(bar, parity, abort, kWaitLimit);
   return __all_sync(0xffffffffu, ok);
 }
 
-// The worker's sequence of tiles: items gw, gw + workers, ... and the tiles of
-// each item in order.
-struct TcCursor {
-  int64_t item;
-  int j, ntile;
-  int64_t ic;     // items passed
-  int64_t chunk;  // coordinate chunk of the item
-  int64_t ct;     // candidate tile of the item
-  int64_t t0;     // first coordinate tile of the chunk
+// Position in a ring of N slots: slot index and the parity of the current
+// lap (the phase parity a wait for this slot's current use expects).
+template <int N>
+struct Ring {
+  uint32_t idx = 0, ph = 0;
+  __device__ __forceinline__ void next() {
+    if (++idx == N) {
+      idx = 0;
+      ph ^= 1u;
+    }
+  }
+  __device__ __forceinline__ void next2() {  // two slots on (N >= 2)
+    idx += 2;
+    if (idx >= N) {
+      idx -= N;
+      ph ^= 1u;
+    }
+  }
+  __device__ __forceinline__ void set(int64_t g) {  // the slot of use g
+    idx = static_cast<uint32_t>(g % N);
+    ph = static_cast<uint32_t>((g / N) & 1);
+  }
 };
 
-// The item's chunk, candidate tile and tile range, computed once per item
-// (64-bit divisions are kept off the per-tile path).
-__device__ __forceinline__ TcCursor tc_start(const TcParams& prm, int64_t item, int64_t ic) {
-  TcCursor c;
-  c.item = item;
-  c.j = 0;
-  c.ic = ic;
-  c.chunk = item / prm.c_tiles;
-  c.ct = item - c.chunk * prm.c_tiles;
+// Polling with a growing sleep between polls, for the warps off the critical
+// path (copies, folds): they give their issue slots to the rounding warps.
+__device__ __forceinline__ bool warp_wait_lazy(uint64_t* bar, uint32_t parity, volatile int* abort) {
+  bool ok = ptx::mbar_try_wait(bar, parity);
+  if (!__all_sync(0xffffffffu, ok)) {
+    const long long t0 = clock64();
+    uint32_t ns = 64;
+    for (;;) {
+      __nanosleep(ns);
+      if (ptx::mbar_try_wait(bar, parity)) {
+        ok = true;
+        break;
+      }
+      if (*abort || clock64() - t0 > kWaitLimit) {
+        ok = false;
+        break;
+      }
+      ns = ns < 1024 ? 2 * ns : 1024;
+    }
+  }
+  return __all_sync(0xffffffffu, ok);
+}
+
+// Own tiles of warpgroup w in an item whose first tile is the CTA's tile
+// g_base: j = j0, j0 + 2, ... < ntile.
+__device__ __forceinline__ int own_first(int64_t g_base, int w) { return static_cast<int>((w - (g_base & 1)) & 1); }
+
+// The CTA's items are blockIdx.x, blockIdx.x + gridDim.x, ...; item it covers
+// coordinate chunk it / c_tiles (tiles t0 .. t0 + ntile - 1) against candidate
+// tile it % c_tiles.
+struct TcItem {
+  int64_t chunk, ct, t0;
+  int ntile;
+};
+
+__device__ __forceinline__ TcItem tc_item(const TcParams& prm, int64_t it) {
+  TcItem c;
+  c.chunk = it / prm.c_tiles;
+  c.ct = it - c.chunk * prm.c_tiles;
   c.t0 = c.chunk * prm.tiles_per_chunk;
-  c.ntile = item < prm.num_items ? static_cast<int>(min(prm.n_tiles, c.t0 + prm.tiles_per_chunk) - c.t0) : 0;
+  c.ntile = static_cast<int>(min(prm.n_tiles, c.t0 + prm.tiles_per_chunk) - c.t0);
   return c;
 }
 
-__device__ __forceinline__ void tc_advance(const TcParams& prm, int64_t workers, TcCursor& c) {
-  if (++c.j == c.ntile) c = tc_start(prm, c.item + workers, c.ic + 1);
-}
-
 template <int K, int KCH>
-__global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
+__global__ void __launch_bounds__(kTcThreads, 1)
     score_tc_kernel(const __grid_constant__ CUtensorMap tm_vt, const __grid_constant__ CUtensorMap tm_ct,
-                    TcParams prm, const float* __restrict__ scale, const uint32_t* __restrict__ iw,
-                    double* __restrict__ partial, int32_t* status) {
+                    TcParams prm, const float* __restrict__ scale, double* __restrict__ partial,
+                    int32_t* status) {
   using Sh = TcShape<K, KCH>;
   using L = TcLayout<K, KCH>;
   constexpr int R = Sh::R;
   constexpr int BK = Sh::BK;
   constexpr int BKG = Sh::BKG;
   constexpr int G = Sh::G;
-  constexpr int NW = Sh::NW;
-  constexpr int NST = L::NST;
+  constexpr int ND = Sh::ND;
+  constexpr int NS = L::NS;
   constexpr int NOUT = Sh::NOUT;
+  constexpr int F = Sh::FLUSH;
   constexpr int CW = R / 4;  // indicator words per class per tile
+  constexpr int RC = Sh::RC;
 
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5;
   const int lane = threadIdx.x & 31;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::BAR_OFF + NW * L::WBARS * 8);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
+  uint64_t* sfull = bars;                     // [NS]  stage landed (TMA)
+  uint64_t* sempty = sfull + kTcMaxStages;    // [NS]  both GEMMs of the stage's tile done
+  uint64_t* dfull = sempty + kTcMaxStages;    // [2]   direction buffer landed
+  uint64_t* dempty = dfull + 2;               // [2]   every GEMM1 of the buffer's item done
+  uint64_t* d1full = dempty + 2;              // [3]   D1 buffer holds its tile's projections
+  uint64_t* d1empty = d1full + 3;             // [3]   every rounding warp has loaded it (4 arrivals)
+  uint64_t* a2full = d1empty + 3;             // [2]   A2 buffer written (4 arrivals)
+  uint64_t* a2empty = a2full + 2;             // [2]   GEMM2 that read it done
+  uint64_t* d2full = a2empty + 2;             // [2][2] accumulation period of warpgroup w complete
+  uint64_t* d2empty = d2full + 4;             // [2][2] folded (4 arrivals)
+  uint64_t* drain = d2empty + 4;              // [3]   teardown of the GEMM1 / GEMM2 warps
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::BAR_OFF + L::NBARS * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NW * L::WBARS; ++i) ptx::mbar_init(reinterpret_cast<uint64_t*>(smem + L::BAR_OFF) + i, 1);
+    for (int i = 0; i < NS; ++i) {
+      ptx::mbar_init(&sfull[i], 1);
+      ptx::mbar_init(&sempty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      ptx::mbar_init(&dfull[i], 1);
+      ptx::mbar_init(&dempty[i], 1);
+      ptx::mbar_init(&a2full[i], 4);
+      ptx::mbar_init(&a2empty[i], 1);
+    }
+    for (int i = 0; i < 4; ++i) {
+      ptx::mbar_init(&d2full[i], 1);
+      ptx::mbar_init(&d2empty[i], 4);
+    }
+    for (int i = 0; i < 3; ++i) ptx::mbar_init(&drain[i], 1);
+    for (int i = 0; i < 3; ++i) {
+      ptx::mbar_init(&d1full[i], 1);
+      ptx::mbar_init(&d1empty[i], 4);
+    }
     *abort_flag = 0;
     ptx::fence_mbar_init();
   }
   {
     uint4* z = reinterpret_cast<uint4*>(smem + L::ZERO_OFF);
     for (int i = threadIdx.x; i < L::ZERO_BYTES / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
-    for (int w = 0; w < NW; ++w) {
-      uint4* acc = reinterpret_cast<uint4*>(smem + w * L::WSMEM + L::W_ACC);
-      for (int i = threadIdx.x; i < L::ACC_BYTES / 16; i += blockDim.x) acc[i] = make_uint4(0u, 0u, 0u, 0u);
-    }
   }
   ptx::fence_proxy_async_smem();
-  if (warp == 0 && lane == 0) {
+  if (warp == kWarpTma && lane == 0) {
     ptx::tma_prefetch_desc(&tm_vt);
     ptx::tma_prefetch_desc(&tm_ct);
   }
-  if (warp == 1) {
+  if (warp == 0) {
     ptx::tmem_alloc(tmem_slot, 512);
     ptx::tmem_relinquish();
   }
@@ -251,284 +335,320 @@ __global__ void __launch_bounds__(TcShape<K, KCH>::THREADS, 1)
   ptx::tc_fence_after();
   const uint32_t tmem = *tmem_slot;
   const uint32_t smem_base = ptx::smem_u32(smem);
-  const float inv_s = scale[1];
+  const int64_t grid = gridDim.x;
+  const int64_t first_item = blockIdx.x;
 
-  const int F = prm.flush;
-  const int64_t workers = static_cast<int64_t>(gridDim.x) * NW;
-  const int w = warp >> 2;                                        // worker
-  const int64_t gw = static_cast<int64_t>(blockIdx.x) * NW + w;  // global worker id
-  uint8_t* wsm = smem + w * L::WSMEM;
-  const uint32_t wsm_s = smem_base + w * L::WSMEM;
-  uint64_t* wb = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF) + w * L::WBARS;
-  uint64_t* full_b = wb;
-  uint64_t* a1_full = wb + NST;  // [2]
-  uint64_t* d1_full = a1_full + 2;
-  uint64_t* d2_ready = a1_full + 3;
-  uint64_t* drain_bar = a1_full + 4;
-  uint64_t* a2_free = a1_full + 5;
-  uint64_t* drain2 = a1_full + 6;
-
-  // Thread `row` owns candidate `row` of every tile.  Per tile g:
-  //   wait D1(g) -> round its R coordinates into indicator words -> wait until
-  //   GEMM2(g-1) has released A2 -> store them into A2 -> one warpgroup
-  //   rendezvous -> warp 0 issues GEMM1(g+1) behind d1_full while warp 2
-  //   issues GEMM2(g) behind a2_free (and d2_ready at the end of a period);
-  //   both issue from the converged warp through one elected lane, and every
-  //   wait is polled by whole warps -> every `flush` tiles fold D2 into the
-  //   two-sum partials.  After the rendezvous the loader (one lane of warp 1)
-  //   refills the stages freed by tile g-1.
-  const int qtr = warp & 3;         // TMEM lane quarter
-  const int row = qtr * 32 + lane;  // candidate row within the tile
-  const bool loader = (qtr == 1 && lane == 0);  // issues the worker's TMA copies
-  const uint32_t lane_base = static_cast<uint32_t>(qtr * 32) << 16;
-  const uint32_t tw = tmem + w * Sh::WCOLS;  // this worker's TMEM slice
-  constexpr uint32_t idesc1 = ptx::idesc_f16_f16(kTcM, Sh::N1);
-  constexpr uint32_t idesc2 = ptx::idesc_e4m3_f32(kTcM, Sh::N2);
-  constexpr uint32_t lbo_b2 = L::N2R * 16;
-  float2* acc = reinterpret_cast<float2*>(wsm + L::W_ACC) + row * 16;  // (hi, lo) per component
-
-  TcCursor cc = tc_start(prm, gw, 0);           // consumer: the tile being rounded
-  TcCursor lc = cc;                             // loader: the next tile to load
-  int64_t lg = 0, cg = 0;                       // tiles loaded / stages waited for
-  int64_t la = 0, ca = 0;                       // direction tiles loaded / waited for
-
-  // loader helpers: copies into the stage ring and the direction buffers
-  auto load_tile = [&]() {
-    const uint32_t s = static_cast<uint32_t>(lg % NST);
-    uint8_t* st = wsm + s * L::STAGE_BYTES;
-    const int64_t t = lc.t0 + lc.j;
-    ptx::mbar_arrive_expect_tx(&full_b[s], L::STAGE_TX);
-    ptx::tma_load_2d(st, &tm_vt, 0, static_cast<int>(t * (L::TILE_BYTES / 256)), &full_b[s]);
-    ++lg;
-    tc_advance(prm, workers, lc);
-  };
-  auto load_dirs = [&]() {  // directions of the worker's la-th item, if it exists
-    const int64_t it = gw + la * workers;
-    if (it >= prm.num_items) return;
-    const uint32_t b = static_cast<uint32_t>(la & 1);
-    ptx::mbar_arrive_expect_tx(&a1_full[b], L::A1_BYTES);
-    ptx::tma_load_2d(wsm + L::W_A1 + b * L::A1_BYTES, &tm_ct, 0,
-                     static_cast<int>((it % prm.c_tiles) * (L::A1_BYTES / 256)), &a1_full[b]);  // once per item
-    ++la;
-  };
-  auto wait_stage = [&]() -> bool {  // the stage of tile cg (warp 0)
-    const bool ok = warp_wait(&full_b[cg % NST], static_cast<uint32_t>((cg / NST) & 1), abort_flag);
-    ++cg;
-    return ok;
-  };
-  auto wait_dirs = [&]() -> bool {  // the direction buffer of item ca (warp 0)
-    const bool ok = warp_wait(&a1_full[ca & 1], static_cast<uint32_t>((ca >> 1) & 1), abort_flag);
-    ++ca;
-    return ok;
-  };
-  auto gemm1 = [&](uint32_t stage, uint32_t ab) {
-    constexpr bool two_chunks = (KCH == 2);
-    const uint32_t a1 = wsm_s + L::W_A1 + ab * L::A1_BYTES;
-    const uint32_t lbo_a1 = two_chunks ? kTcM * 16u : (smem_base + L::ZERO_OFF - a1);
-    const uint32_t b1 = wsm_s + stage * L::STAGE_BYTES + L::B1_OFF_IN_STAGE;
-    const uint32_t lbo_b1 = two_chunks ? Sh::N1 * 16u : (smem_base + L::ZERO_OFF - b1);
-    ptx::mma_f16_ss_elect(tw + Sh::D1_OFF, ptx::smem_desc(a1, lbo_a1, 128), ptx::smem_desc(b1, lbo_b1, 128), idesc1,
-                          0u);
-    ptx::mma_commit_elect(d1_full);
-  };
-
-  uint32_t g = 0, pe = 0;
-  int pos = 0;       // tile position within the accumulation period
-  bool bad = false;  // this thread saw a wait give up (carried to the next barrier)
-  if (cc.item < prm.num_items && loader) {
-    // prologue: directions of the first two items, the first NST tiles
-    load_dirs();
-    load_dirs();
-    while (lg < NST && lc.item < prm.num_items) load_tile();
-  }
-  if (cc.item < prm.num_items && qtr == 0) {
-    // GEMM1(0) once its operands have landed
-    const bool ok = wait_dirs() && wait_stage();
-    if (ok) {
-      ptx::tc_fence_after();
-      gemm1(0u, 0u);
-    } else if (lane == 0) {
-      *abort_flag = 1;
-    }
-  }
-  while (cc.item < prm.num_items) {
-    const bool first = pos == 0;
-    const bool item_end = (cc.j == cc.ntile - 1);
-    const bool last = (pos == F - 1) || item_end;
-    const bool has_next = !item_end || cc.item + workers < prm.num_items;
-    // indicator magnitudes 2^(g - e_i) of the tile's coordinates (E4M3 bytes),
-    // read while D1 is on its way
-    uint32_t mag[CW];
-    {
-      const uint4* iwt = reinterpret_cast<const uint4*>(iw + (cc.t0 + cc.j) * CW);
-#pragma unroll
-      for (int c = 0; c < CW / 4; ++c) {
-        const uint4 v4 = __ldg(iwt + c);
-        mag[4 * c] = v4.x;
-        mag[4 * c + 1] = v4.y;
-        mag[4 * c + 2] = v4.z;
-        mag[4 * c + 3] = v4.w;
+  if (warp == kWarpTma) {
+    // ------------------------------------------------------------ TMA warp
+    Ring<NS> st;
+    int64_t loads = 0, dloads = 0;
+    bool ok = true;
+    for (int64_t it = first_item, k = 0; it < prm.num_items && ok; it += grid, ++k) {
+      const TcItem c = tc_item(prm, it);
+      const uint32_t b = static_cast<uint32_t>(k & 1);
+      if (k >= 2) ok = warp_wait_lazy(&dempty[b], static_cast<uint32_t>(((k - 2) >> 1) & 1), abort_flag);
+      if (!ok) break;
+      if (lane == 0) {
+        ptx::mbar_arrive_expect_tx(&dfull[b], L::A1_BYTES);
+        ptx::tma_load_2d(smem + L::DIRS_OFF + b * L::A1_BYTES, &tm_ct, 0,
+                         static_cast<int>(c.ct * (L::A1_BYTES / 256)), &dfull[b]);
       }
-    }
-    bad = bad || !warp_wait(d1_full, g & 1u, abort_flag);
-    // ---- round the projections of tile g into indicator words in A2
-    if (!bad) {
-      ptx::tc_fence_after();
-      uint32_t wv[G * CW];
-      // D1 holds F16 projections, one per column; a packed load gives two
-      // coordinates per register, so one byte permute gathers the signs of
-      // four coordinates
-      constexpr int RC = R < 32 ? R : 32;  // coordinates per load
-#pragma unroll
-      for (int ch = 0; ch < R / RC; ++ch) {
-        uint32_t pl[BKG][RC / 2];
-#pragma unroll
-        for (int b = 0; b < BKG; ++b) {
-          const uint32_t ta = tw + lane_base + Sh::D1_OFF + b * R + ch * RC;
-          if constexpr (RC == 32)
-            ptx::tmem_ld_x16_pack16(ta, *reinterpret_cast<uint32_t(*)[16]>(pl[b]));
-          else
-            ptx::tmem_ld_x8_pack16(ta, *reinterpret_cast<uint32_t(*)[8]>(pl[b]));
+      ++dloads;
+      for (int j = 0; j < c.ntile; ++j) {
+        if (loads >= NS) ok = warp_wait_lazy(&sempty[st.idx], st.ph ^ 1u, abort_flag);
+        if (!ok) break;
+        if (lane == 0) {
+          ptx::mbar_arrive_expect_tx(&sfull[st.idx], L::STAGE_TX);
+          ptx::tma_load_2d(smem + st.idx * L::STAGE_BYTES, &tm_vt, 0,
+                           static_cast<int>((c.t0 + j) * (L::TILE_BYTES / 256)), &sfull[st.idx]);
         }
-        ptx::tmem_wait_ld();
-#pragma unroll
-        for (int p = 0; p < RC / 4; ++p) {
-          uint32_t nm[BK];
-          if constexpr (K == 3) {
-            // p_1 = -(p_0 + p_2): the three boundary directions sum to zero, so
-            // p_1 < 0 exactly where p_0 + p_2 > 0
-            const uint32_t sum_neg = ptx::prmt(ptx::hadd2(pl[0][2 * p], pl[1][2 * p]),
-                                               ptx::hadd2(pl[0][2 * p + 1], pl[1][2 * p + 1]), 0xFDB9u);
-            nm[0] = ptx::prmt(pl[0][2 * p], pl[0][2 * p + 1], 0xFDB9u);
-            nm[1] = ~sum_neg;
-            nm[2] = ptx::prmt(pl[1][2 * p], pl[1][2 * p + 1], 0xFDB9u);
-          } else {
-#pragma unroll
-            for (int m = 0; m < BK; ++m) nm[m] = ptx::prmt(pl[m][2 * p], pl[m][2 * p + 1], 0xFDB9u);
-          }
-          const int wi = ch * (RC / 4) + p;
-#pragma unroll
-          for (int gc = 0; gc < G; ++gc) {
-            if constexpr (K % 2 == 1)
-              wv[gc * CW + wi] = ~nm[gc] & nm[gc + 1] & mag[wi];  // p_{k-1} > 0 and p_k < 0
-            else
-              wv[gc * CW + wi] = (nm[gc] & 0x80808080u) | mag[wi];  // sign(p_m) as +-1
-          }
-        }
+        ++loads;
+        st.next();
       }
-      // GEMM2(g-1) has released A2
-      if (g > 0) bad = !warp_wait(a2_free, (g - 1) & 1u, abort_flag);
-      if (!bad) {
+    }
+    if (!ok) *abort_flag = 1;
+    // drain: the copies still in flight land before shared memory is released
+    volatile int never = 0;
+    for (int64_t t = loads > NS ? loads - NS : 0; t < loads; ++t)
+      ptx::mbar_wait_sleep(&sfull[t % NS], static_cast<uint32_t>((t / NS) & 1), &never, kWaitLimit);
+    for (int64_t t = dloads > 2 ? dloads - 2 : 0; t < dloads; ++t)
+      ptx::mbar_wait_sleep(&dfull[t & 1], static_cast<uint32_t>((t >> 1) & 1), &never, kWaitLimit);
+  } else if (warp == kWarpG1) {
+    // ---------------------------------------------------------- GEMM1 warp
+    constexpr uint32_t idesc1 = ptx::idesc_f16_f16(kTcM, Sh::N1);
+    Ring<NS> st;
+    Ring<ND> d1;
+    int64_t g = 0;
+    bool ok = true;
+    for (int64_t it = first_item, k = 0; it < prm.num_items && ok; it += grid, ++k) {
+      const TcItem c = tc_item(prm, it);
+      const uint32_t b = static_cast<uint32_t>(k & 1);
+      ok = warp_wait(&dfull[b], static_cast<uint32_t>((k >> 1) & 1), abort_flag);
+      if (!ok) break;
+      const uint32_t a1 = smem_base + L::DIRS_OFF + b * L::A1_BYTES;
+      const uint32_t lbo_a1 = KCH == 2 ? kTcM * 16u : (smem_base + L::ZERO_OFF - a1);
+      const uint64_t adesc = ptx::smem_desc(a1, lbo_a1, 128);
+      for (int j = 0; j < c.ntile; ++j, ++g) {
+        ok = warp_wait(&sfull[st.idx], st.ph, abort_flag);
+        if (ok && g >= ND) ok = warp_wait(&d1empty[d1.idx], d1.ph ^ 1u, abort_flag);
+        if (!ok) break;
         ptx::tc_fence_after();
-#pragma unroll
-        for (int c = 0; c < Sh::A2COLS / 8; ++c)
-          ptx::tmem_st_x8(tw + lane_base + Sh::A2_OFF + c * 8, *reinterpret_cast<const uint32_t(*)[8]>(&wv[c * 8]));
-        ptx::tmem_wait_st();
+        const uint32_t b1 = smem_base + st.idx * L::STAGE_BYTES + L::B1_OFF_IN_STAGE;
+        const uint32_t lbo_b1 = KCH == 2 ? Sh::N1 * 16u : (smem_base + L::ZERO_OFF - b1);
+        ptx::mma_f16_ss_elect(tmem + Sh::D1_OFF + d1.idx * Sh::N1, adesc, ptx::smem_desc(b1, lbo_b1, 128), idesc1,
+                              0u);
+        ptx::mma_commit_elect(&d1full[d1.idx]);
+        st.next();
+        d1.next();
       }
+      if (!ok) break;
+      ptx::mma_commit_elect(&dempty[b]);
     }
-    ptx::tc_fence_before();
-    // D1 read and A2 written by the whole warpgroup; all leave together on failure
-    if (ptx::named_barrier_or(1 + w, 128, bad)) break;
-    // ---- the loader: GEMM1(g) is done (D1(g) was seen) and so is GEMM2(g-1)
-    // (every warp saw a2_free before storing A2): the stages up to tile g-1
-    // are free, and at the end of an item its direction buffer
-    if (loader) {
-      while (lg <= static_cast<int64_t>(g) - 1 + NST && lc.item < prm.num_items) load_tile();
-      if (item_end) load_dirs();
-    }
-    // ---- warp 0: GEMM1(g+1) into D1
-    if (qtr == 0) {
-      ptx::tc_fence_after();
-      bool ok = true;
-      if (has_next) {
-        ok = item_end ? wait_dirs() : true;
-        ok = ok && wait_stage();
-        if (ok) gemm1((g + 1) % NST, static_cast<uint32_t>((cc.ic + (item_end ? 1 : 0)) & 1));
-      }
-      if (!ok && lane == 0) *abort_flag = 1;
-    }
-    // ---- warp 2: GEMM2(g) from A2 and the tile's stage into D2
-    if (qtr == 2) {
-      ptx::tc_fence_after();
-      const uint32_t b2 = wsm_s + (g % NST) * L::STAGE_BYTES + L::B2_OFF_IN_STAGE;
-#pragma unroll
-      for (int q = 0; q < Sh::KD2 / 32; ++q)
-        ptx::mma_e4m3_ts_elect(tw + Sh::D2_OFF, tw + Sh::A2_OFF + q * 8,
-                               ptx::smem_desc(b2 + q * 2 * lbo_b2, lbo_b2, 128), idesc2, (q > 0 || !first) ? 1u : 0u);
-      if (last) ptx::mma_commit_elect(d2_ready);
-      ptx::mma_commit_elect(a2_free);
-    }
-    // ---- fold the period's accumulator into the two-sum partials
-    if (last) {
-      bad = !warp_wait(d2_ready, pe & 1u, abort_flag);
-      if (!bad) {
+    if (!ok) *abort_flag = 1;
+    volatile int never = 0;
+    ptx::mma_commit_elect(&drain[0]);
+    warp_wait(&drain[0], 0u, &never);
+  } else if (warp == kWarpG2 || warp == kWarpG2 + 1) {
+    // ---------------------------------------------------------- GEMM2 warps
+    const int w = warp - kWarpG2;  // the rounding warpgroup whose tiles this warp issues
+    constexpr uint32_t idesc2 = ptx::idesc_e4m3_f32(kTcM, Sh::N2);
+    constexpr uint32_t lbo_b2 = L::N2R * 16;
+    const uint32_t a2 = tmem + Sh::A2_OFF + w * Sh::A2COLS;
+    const uint32_t d2 = tmem + Sh::D2_OFF + 2 * w * Sh::N2;
+    Ring<NS> st;
+    int64_t g_base = 0, p = 0;  // the CTA's first tile of the item; this warpgroup's periods
+    bool ok = true;
+    for (int64_t it = first_item; it < prm.num_items && ok; it += grid) {
+      const TcItem c = tc_item(prm, it);
+      int j = own_first(g_base, w);
+      st.set(g_base + j);
+      int pos = 0;
+      for (; j < c.ntile; j += 2, st.next2()) {
+        const int64_t g = g_base + j;
+        const bool first = pos == 0;
+        const bool last = (pos == F - 1) || (j + 2 >= c.ntile);
+        const uint32_t pb = static_cast<uint32_t>(p & 1);
+        if (first && p >= 2)
+          ok = warp_wait(&d2empty[2 * w + pb], static_cast<uint32_t>(((p >> 1) - 1) & 1), abort_flag);
+        if (ok) ok = warp_wait(&a2full[w], static_cast<uint32_t>((g >> 1) & 1), abort_flag);
+        if (!ok) break;
         ptx::tc_fence_after();
-        uint32_t dh[16], dl[16];
-        if constexpr (NOUT == 8) {
-          ptx::tmem_ld_x16(tw + lane_base + Sh::D2_OFF, dh);
-          ptx::tmem_wait_ld();
+        const uint32_t b2 = smem_base + st.idx * L::STAGE_BYTES + L::B2_OFF_IN_STAGE;
 #pragma unroll
-          for (int jj = 0; jj < 8; ++jj) dl[jj] = dh[8 + jj];
+        for (int q = 0; q < Sh::KD2 / 32; ++q)
+          ptx::mma_e4m3_ts_elect(d2 + pb * Sh::N2, a2 + q * 8, ptx::smem_desc(b2 + q * 2 * lbo_b2, lbo_b2, 128), idesc2,
+                                 (q > 0 || !first) ? 1u : 0u);
+        ptx::mma_commit_elect(&a2empty[w]);
+        ptx::mma_commit_elect(&sempty[st.idx]);
+        if (last) {
+          ptx::mma_commit_elect(&d2full[2 * w + pb]);
+          ++p;
+          pos = 0;
         } else {
-          ptx::tmem_ld_x16(tw + lane_base + Sh::D2_OFF, dh);
-          ptx::tmem_ld_x16(tw + lane_base + Sh::D2_OFF + 16, dl);
-          ptx::tmem_wait_ld();
+          ++pos;
         }
-        ptx::tc_fence_before();
-        const int r2 = 2 * prm.r;
-        double* out = partial + (cc.chunk * prm.S_pad + cc.ct * kTcM + row) * r2;
+      }
+      g_base += c.ntile;
+    }
+    if (!ok) *abort_flag = 1;
+    volatile int never = 0;
+    ptx::mma_commit_elect(&drain[1 + w]);
+    warp_wait(&drain[1 + w], 0u, &never);
+  } else if (warp >= kWarpFold0) {
+    // --------------------------------------------------------- fold warpgroup
+    const int q = warp & 3;
+    const int row = q * 32 + lane;
+    const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+    const float inv_s = scale[1];
+    const int r2 = 2 * prm.r;
+    float hi[NOUT], lo[NOUT];
 #pragma unroll
-        for (int jj = 0; jj < NOUT; ++jj) {
-          if (jj < r2) {
-            float2 hl = acc[jj];
-            float s, er;
-            two_sum_f(hl.x, __uint_as_float(dh[jj]), s, er);
-            hl.x = s;
-            hl.y += er;
-            two_sum_f(hl.x, __uint_as_float(dl[jj]), s, er);
-            hl.x = s;
-            hl.y += er;
-            if (item_end) {
-              out[jj] = (static_cast<double>(hl.x) + static_cast<double>(hl.y)) * static_cast<double>(inv_s);
-              hl = make_float2(0.f, 0.f);
+    for (int jj = 0; jj < NOUT; ++jj) hi[jj] = lo[jj] = 0.f;
+    int64_t g_base = 0;
+    int64_t pw[2] = {0, 0};  // periods folded per warpgroup
+    bool ok = true;
+    for (int64_t it = first_item; it < prm.num_items && ok; it += grid) {
+      const TcItem c = tc_item(prm, it);
+      // the item's periods per warpgroup: its own tiles, F at a time
+      int nper[2];
+#pragma unroll
+      for (int w = 0; w < 2; ++w) {
+        const int own = (c.ntile - own_first(g_base, w) + 1) / 2;
+        nper[w] = (own + F - 1) / F;
+      }
+      const int imax = nper[0] > nper[1] ? nper[0] : nper[1];
+      for (int i = 0; i < imax && ok; ++i) {
+#pragma unroll
+        for (int w = 0; w < 2; ++w) {
+          if (i >= nper[w] || !ok) continue;
+          const uint32_t pb = static_cast<uint32_t>(pw[w] & 1);
+          ok = warp_wait_lazy(&d2full[2 * w + pb], static_cast<uint32_t>((pw[w] >> 1) & 1), abort_flag);
+          if (!ok) break;
+          ptx::tc_fence_after();
+          uint32_t dh[NOUT], dl[NOUT];
+          const uint32_t ta = tmem + lane_base + Sh::D2_OFF + (2 * w + pb) * Sh::N2;
+          if constexpr (NOUT == 8) {
+            uint32_t v[16];
+            ptx::tmem_ld_x16(ta, v);
+            ptx::tmem_wait_ld();
+#pragma unroll
+            for (int jj = 0; jj < 8; ++jj) {
+              dh[jj] = v[jj];
+              dl[jj] = v[8 + jj];
             }
-            acc[jj] = hl;
+          } else {
+            ptx::tmem_ld_x16(ta, dh);
+            ptx::tmem_ld_x16(ta + 16, dl);
+            ptx::tmem_wait_ld();
+          }
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&d2empty[2 * w + pb]);
+          ++pw[w];
+#pragma unroll
+          for (int jj = 0; jj < NOUT; ++jj) {
+            float s, er;
+            two_sum_f(hi[jj], __uint_as_float(dh[jj]), s, er);
+            hi[jj] = s;
+            lo[jj] += er;
+            two_sum_f(hi[jj], __uint_as_float(dl[jj]), s, er);
+            hi[jj] = s;
+            lo[jj] += er;
           }
         }
       }
-      ++pe;
+      if (!ok) break;
+      // the item's chunk partial sums
+      double* out = partial + (c.chunk * prm.S_pad + c.ct * kTcM + row) * r2;
+#pragma unroll
+      for (int jj = 0; jj < NOUT; ++jj) {
+        if (jj < r2) out[jj] = (static_cast<double>(hi[jj]) + static_cast<double>(lo[jj])) * static_cast<double>(inv_s);
+        hi[jj] = lo[jj] = 0.f;
+      }
+      g_base += c.ntile;
     }
-    // ---- advance
-    pos = last ? 0 : pos + 1;
-    ++g;
-    tc_advance(prm, workers, cc);
-  }
-  if (bad || *abort_flag) {
-    *abort_flag = 1;
-    dev_fail(status, LRQ_ETIMEOUT);
-  }
-  // drain: the MMAs of warps 0 and 2 and the loader's copies complete before
-  // TMEM and shared memory are released (a stage or direction buffer is
-  // refilled only after its previous copy was consumed, so only the last NST
-  // tile copies and the last two direction copies can be outstanding)
-  if (qtr == 0 || qtr == 2) {
-    volatile int never = 0;
-    uint64_t* db = qtr == 0 ? drain_bar : drain2;
-    ptx::mma_commit_elect(db);
-    warp_wait(db, 0u, &never);
-  }
-  if (loader) {
-    volatile int never = 0;
-    for (int64_t t = lg > NST ? lg - NST : 0; t < lg; ++t)
-      ptx::mbar_wait(&full_b[t % NST], static_cast<uint32_t>((t / NST) & 1), &never, kWaitLimit);
-    for (int64_t t = la > 2 ? la - 2 : 0; t < la; ++t)
-      ptx::mbar_wait(&a1_full[t & 1], static_cast<uint32_t>((t >> 1) & 1), &never, kWaitLimit);
+    if (!ok) *abort_flag = 1;
+  } else if (warp < 8) {
+    // ----------------------------------------------------- rounding warpgroups
+    const int wg = warp >> 2;
+    const int q = warp & 3;
+    const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
+    const uint32_t a2_tmem = tmem + lane_base + Sh::A2_OFF + wg * Sh::A2COLS;
+    // load every chunk's projections before rounding when they fit the
+    // registers (one load latency per tile and the earliest release of D1)
+    constexpr int NCH = R / RC;
+    constexpr bool ALL_LOADS_FIRST = BKG * NCH * (RC / 2) <= 64;
+    Ring<NS> st;
+    Ring<ND> d1;
+    uint32_t a2ph = 0;  // parity of this warpgroup's A2 buffer uses
+    int64_t g_base = 0;
+    bool ok = true;
+    for (int64_t it = first_item; it < prm.num_items && ok; it += grid) {
+      const TcItem c = tc_item(prm, it);
+      int j = own_first(g_base, wg);
+      st.set(g_base + j);
+      d1.set(g_base + j);
+      for (; j < c.ntile; j += 2, st.next2(), d1.next2()) {
+        const int64_t g = g_base + j;
+        // the stage (for the indicator magnitudes) and D1 of tile g
+        ok = warp_wait(&sfull[st.idx], st.ph, abort_flag) && warp_wait(&d1full[d1.idx], d1.ph, abort_flag);
+        if (!ok) break;
+        ptx::tc_fence_after();
+        const uint4* magp = reinterpret_cast<const uint4*>(smem + st.idx * L::STAGE_BYTES + L::MAG_OFF_IN_STAGE);
+        const uint32_t d1_tmem = tmem + lane_base + Sh::D1_OFF + d1.idx * Sh::N1;
+        uint32_t wv[G * CW];
+        // D1 holds F16 projections, one per column; a packed load gives two
+        // coordinates per register, so one byte permute gathers the signs of
+        // four coordinates
+        uint32_t pl[ALL_LOADS_FIRST ? NCH : 1][BKG][RC / 2];
+        auto load_chunk = [&](int ch, uint32_t (&dst)[BKG][RC / 2]) {
+#pragma unroll
+          for (int b = 0; b < BKG; ++b) {
+            const uint32_t ta = d1_tmem + b * R + ch * RC;
+            if constexpr (RC == 32)
+              ptx::tmem_ld_x16_pack16(ta, *reinterpret_cast<uint32_t(*)[16]>(dst[b]));
+            else
+              ptx::tmem_ld_x8_pack16(ta, *reinterpret_cast<uint32_t(*)[8]>(dst[b]));
+          }
+        };
+        auto release_d1 = [&]() {  // every projection of the tile is in registers
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&d1empty[d1.idx]);
+        };
+        if constexpr (ALL_LOADS_FIRST) {
+#pragma unroll
+          for (int ch = 0; ch < NCH; ++ch) load_chunk(ch, pl[ch]);
+          ptx::tmem_wait_ld();
+          release_d1();
+        }
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+          const int pi = ALL_LOADS_FIRST ? ch : 0;
+          if constexpr (!ALL_LOADS_FIRST) {
+            load_chunk(ch, pl[0]);
+            ptx::tmem_wait_ld();
+            if (ch == NCH - 1) release_d1();
+          }
+          uint32_t mag[RC / 4];
+#pragma unroll
+          for (int v = 0; v < RC / 16; ++v) {
+            const uint4 m4 = magp[ch * (RC / 16) + v];
+            mag[4 * v] = m4.x;
+            mag[4 * v + 1] = m4.y;
+            mag[4 * v + 2] = m4.z;
+            mag[4 * v + 3] = m4.w;
+          }
+#pragma unroll
+          for (int pq = 0; pq < RC / 4; ++pq) {
+            uint32_t nm[BK];
+            if constexpr (K == 3) {
+              // p_1 = -(p_0 + p_2): the three boundary directions sum to zero, so
+              // p_1 < 0 exactly where p_0 + p_2 > 0
+              const uint32_t sum_neg = ptx::prmt(ptx::hadd2(pl[pi][0][2 * pq], pl[pi][1][2 * pq]),
+                                                 ptx::hadd2(pl[pi][0][2 * pq + 1], pl[pi][1][2 * pq + 1]), 0xFDB9u);
+              nm[0] = ptx::prmt(pl[pi][0][2 * pq], pl[pi][0][2 * pq + 1], 0xFDB9u);
+              nm[1] = ~sum_neg;
+              nm[2] = ptx::prmt(pl[pi][1][2 * pq], pl[pi][1][2 * pq + 1], 0xFDB9u);
+            } else {
+#pragma unroll
+              for (int m = 0; m < BK; ++m) nm[m] = ptx::prmt(pl[pi][m][2 * pq], pl[pi][m][2 * pq + 1], 0xFDB9u);
+            }
+            const int wi = ch * (RC / 4) + pq;
+#pragma unroll
+            for (int gc = 0; gc < G; ++gc) {
+              if constexpr (K % 2 == 1)
+                wv[gc * CW + wi] = ~nm[gc] & nm[gc + 1] & mag[pq];  // p_{k-1} > 0 and p_k < 0
+              else
+                wv[gc * CW + wi] = (nm[gc] & 0x80808080u) | mag[pq];  // sign(p_m) as +-1
+            }
+          }
+        }
+        // the GEMM2 that read this warpgroup's A2 buffer last (its previous tile) is done
+        if (g >= 2) ok = warp_wait(&a2empty[wg], a2ph ^ 1u, abort_flag);
+        if (!ok) break;
+        ptx::tc_fence_after();
+#pragma unroll
+        for (int cc = 0; cc < Sh::A2COLS / 8; ++cc)
+          ptx::tmem_st_x8(a2_tmem + cc * 8, *reinterpret_cast<const uint32_t(*)[8]>(&wv[cc * 8]));
+        ptx::tmem_wait_st();
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&a2full[wg]);
+        a2ph ^= 1u;
+      }
+      g_base += c.ntile;
+    }
+    if (!ok) *abort_flag = 1;
   }
   // ------------------------------------------------------------ teardown
+  if (threadIdx.x == 0) {
+    __threadfence_block();
+  }
   ptx::tc_fence_before();
   __syncthreads();
-  if (warp == 1) {
-    __syncwarp();
+  if (threadIdx.x == 0 && *abort_flag) dev_fail(status, LRQ_ETIMEOUT);
+  if (warp == 0) {
     ptx::tc_fence_after();
     ptx::tmem_dealloc(tmem, 512);
   }
@@ -681,8 +801,15 @@ __global__ void pack_b2_kernel(const float2* __restrict__ V, int64_t n, int r, i
 
 // Indicator magnitudes 2^(g - e_i) as E4M3 bytes, four coordinates per word
 // (lowest coordinate in the lowest byte), R / 4 words per tile; 0 past n.
+// Written twice: into `iw` (read back by the GEMM2 row packing) and into the
+// magnitude row of each packed tile (read by the scoring kernel's rounding
+// threads from the tile's stage).
+template <int K, int KCH>
 __global__ void pack_indicator_scale_kernel(const float2* __restrict__ V, int64_t n, int r, int64_t words,
-                                            const float* __restrict__ scale, uint32_t* __restrict__ iw) {
+                                            const float* __restrict__ scale, uint32_t* __restrict__ iw,
+                                            uint8_t* __restrict__ tiles) {
+  using Sh = TcShape<K, KCH>;
+  using L = TcLayout<K, KCH>;
   const int64_t q = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (q >= words) return;
   const int g = b2_global_exp(scale);
@@ -696,6 +823,9 @@ __global__ void pack_indicator_scale_kernel(const float2* __restrict__ V, int64_
     w |= code << (8 * c);
   }
   iw[q] = w;
+  const int64_t t = q / (Sh::ROWS / 4);
+  const int wi = static_cast<int>(q % (Sh::ROWS / 4));
+  *reinterpret_cast<uint32_t*>(tiles + t * L::TILE_BYTES + L::MAG_OFF_IN_STAGE + 4 * wi) = w;
 }
 
 // directions: candidate tile ct, chunk ch, row s: slots [Re c, Im c, 0...]
@@ -764,8 +894,8 @@ static int pack_impl(const ScorePlan& p, const Alphabet& a, const float2* V, con
   count_launch(2);
   // the per-coordinate exponents first: the GEMM2 rows read them back
   const int64_t words = p.n_tiles * (Sh::ROWS / 4);
-  pack_indicator_scale_kernel<<<static_cast<unsigned>(ceil_div(words, 256)), 256, 0, st>>>(V, p.n, p.r, words, scale,
-                                                                                          iw);
+  pack_indicator_scale_kernel<K, KCH><<<static_cast<unsigned>(ceil_div(words, 256)), 256, 0, st>>>(
+      V, p.n, p.r, words, scale, iw, static_cast<uint8_t*>(tiles));
   int64_t nb = p.n_tiles * L::B2ROWS;
   pack_b2_kernel<K, KCH><<<static_cast<unsigned>(ceil_div(nb, 256)), 256, 0, st>>>(
       V, p.n, p.r, p.n_tiles, tb, scale, reinterpret_cast<const uint8_t*>(iw), static_cast<uint8_t*>(tiles));
@@ -821,9 +951,8 @@ static int make_rows_map(CUtensorMap* map, const void* base, size_t total_bytes,
 }
 
 template <int K, int KCH>
-static int score_impl(const ScorePlan& p, const void* tiles, const void* ct, const float* scale,
-                      const uint32_t* iw, double* partial, int32_t* status, cudaStream_t st) {
-  using Sh = TcShape<K, KCH>;
+static int score_impl(const ScorePlan& p, const void* tiles, const void* ct, const float* scale, double* partial,
+                      int32_t* status, cudaStream_t st) {
   using L = TcLayout<K, KCH>;
   CUtensorMap m_vt, m_ct;
   int e;
@@ -842,9 +971,8 @@ static int score_impl(const ScorePlan& p, const void* tiles, const void* ct, con
   prm.num_items = p.c_tiles * p.nsplit;
   prm.S_pad = p.c_tiles * kTcM;
   prm.r = p.r;
-  prm.flush = kTcFlush;
-  int grid = static_cast<int>(std::min<int64_t>(ceil_div(prm.num_items, Sh::NW), num_sms_current()));
-  score_tc_kernel<K, KCH><<<grid, Sh::THREADS, L::TOTAL, st>>>(m_vt, m_ct, prm, scale, iw, partial, status);
+  int grid = static_cast<int>(std::min<int64_t>(prm.num_items, num_sms_current()));
+  score_tc_kernel<K, KCH><<<grid, kTcThreads, L::TOTAL, st>>>(m_vt, m_ct, prm, scale, partial, status);
   count_launch();
   return cuda_check(cudaGetLastError(), "score_tc_kernel");
 }
@@ -871,10 +999,9 @@ int tc_rows_per_tile(int K) {
 }
 
 int tc_workers_per_cta(int K, int r) {
-  const bool two = r > 4;
-#define LRQ_NW(k, c) TcShape<k, c>::NW
-  LRQ_TC_SHAPE_SWITCH(LRQ_NW);
-#undef LRQ_NW
+  (void)K;
+  (void)r;
+  return 1;  // one pipeline per CTA
 }
 
 size_t tc_bytes_tiles(int K, int r, int64_t n_tiles) {
@@ -916,8 +1043,8 @@ int launch_tc_pack(const ScorePlan& p, const Alphabet& a, const float2* V, const
 int launch_score_tc(const ScorePlan& p, const Alphabet& a, const void* tiles, const void* ct, const void* scale,
                     const void* iw, double* partial, int32_t* status, cudaStream_t st) {
   (void)a;
-  LRQ_TC_DISPATCH(score_impl, p, tiles, ct, static_cast<const float*>(scale), static_cast<const uint32_t*>(iw),
-                  partial, status, st);
+  (void)iw;  // the magnitudes travel inside the packed tiles
+  LRQ_TC_DISPATCH(score_impl, p, tiles, ct, static_cast<const float*>(scale), partial, status, st);
 }
 
 }  // namespace lrq

@@ -123,11 +123,14 @@ int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_
     p->rows_per_tile = tc_rows_per_tile(K);
     p->n_tiles = ceil_div(n, p->rows_per_tile);
     // coordinate chunks: balance (chunk, candidate tile) items over the
-    // workers (num_sms CTAs x workers per CTA)
+    // workers (num_sms CTAs x workers per CTA); of the splits within 1% of
+    // the best balance take the fewest chunks (each chunk writes S x 2r FP64
+    // partial sums)
     const int64_t workers = static_cast<int64_t>(num_sms) * tc_workers_per_cta(K, r);
-    int best_ns = 1;
+    double eff_of[65];
     double best_eff = -1.0;
-    for (int ns = 1; ns <= 64 && ns <= p->n_tiles; ++ns) {
+    const int ns_max = static_cast<int>(std::min<int64_t>(64, p->n_tiles));
+    for (int ns = 1; ns <= ns_max; ++ns) {
       int64_t tpc = ceil_div(p->n_tiles, ns);
       int64_t ns_eff = ceil_div(p->n_tiles, tpc);
       int64_t items = p->c_tiles * ns_eff;
@@ -135,11 +138,11 @@ int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_
       double eff = static_cast<double>(items) / static_cast<double>(waves * workers);
       // a longer chunk amortises the pipeline fill of an item
       eff *= static_cast<double>(tpc) / static_cast<double>(tpc + 2);
-      if (eff > best_eff + 1e-3) {
-        best_eff = eff;
-        best_ns = ns;
-      }
+      eff_of[ns] = eff;
+      best_eff = std::max(best_eff, eff);
     }
+    int best_ns = 1;
+    while (best_ns < ns_max && eff_of[best_ns] < best_eff - 0.01) ++best_ns;
     p->tiles_per_chunk = ceil_div(p->n_tiles, best_ns);
     p->nsplit = static_cast<int>(ceil_div(p->n_tiles, p->tiles_per_chunk));
     p->npart = p->nsplit;

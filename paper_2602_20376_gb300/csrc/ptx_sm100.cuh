@@ -60,6 +60,39 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   }
 }
 
+// try_wait with a suspend-time hint: a thread whose phase has not completed
+// sleeps until it does or until about `hint_ns` nanoseconds have passed, so a
+// waiting warp takes (almost) no issue slots from the warps beside it.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded sleeping wait: like mbar_wait, with the thread suspended between
+// polls.  Gives up when `abort` becomes non-zero or after `limit` cycles.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity, volatile int* abort,
+                                                long long limit) {
+  if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+  long long t0 = clock64();
+  for (;;) {
+    if (mbar_try_wait_sleep(bar, parity, 20000u)) return true;
+    if (*abort) return false;
+    if (clock64() - t0 > limit) return false;
+  }
+}
+
+// One arrival (release semantics at CTA scope) on an mbarrier.
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 // Barrier among `count` threads that also ORs a predicate over them: every
 // participant gets the same answer (used to leave a loop together).
 __device__ __forceinline__ bool named_barrier_or(int id, int count, bool pred) {

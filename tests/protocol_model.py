@@ -1,17 +1,29 @@
-"""Executable model of the per-worker synchronisation protocol of score_tc_kernel.
+"""Executable model of the synchronisation protocol of score_tc_kernel.
 
 Test infrastructure (plain Python, no GPU).  The model mirrors, step for step,
-the program one worker of the tensor-core scoring kernel runs:
+the programs the warps of one CTA of the tensor-core scoring kernel run:
 
-* four rounding warps; warp 0 also issues GEMM1, warp 2 GEMM2, and one lane
-  of warp 1 (the loader) issues the TMA copies;
-* the tcgen05 operations (MMAs and commits) of warps 0 and 2, which execute
-  in issue order per issuing warp and in any order across the two warps; a
-  commit arrives on its mbarrier once every earlier operation of its warp
-  has executed;
+* the TMA warp, which fills a ring of NS coordinate-tile stages and two
+  direction buffers;
+* the GEMM1 warp, which issues the projections of tile g into the D1 buffer
+  g % ND (a ring of ND buffers in tensor memory);
+* two rounding warpgroups (four warps each): warpgroup g % 2 loads D1 of tile
+  g, releases the buffer, rounds, and stores the indicator operand into its
+  own A2 buffer;
+* two GEMM2 warps: GEMM2 warp w issues the per-class sums of warpgroup w's
+  tiles from A2[w] into warpgroup w's accumulator D2[w][p % 2], p the index
+  of the tile's accumulation period among warpgroup w's periods (a period is
+  at most F of the warpgroup's tiles of one item);
+* the fold warpgroup (four warps), which reads the accumulators at the end of
+  each period -- per item, period i of warpgroup 0, then period i of
+  warpgroup 1, for i = 0, 1, ... -- and releases them;
+* the tcgen05 operations (MMAs and commits) of the two issuing warps, which
+  execute in issue order per warp and in any order across the warps; a commit
+  arrives on its mbarrier once every earlier operation of its warp has
+  executed;
 * the TMA copies, which complete in any order;
 * the mbarriers (arrival count, transaction bytes, completed phases) with
-  their parity waits, and the warpgroup rendezvous.
+  their parity waits.
 
 A seeded random scheduler runs one enabled agent at a time (a warp, the head
 of an MMA queue, a pending copy).  The checker raises ProtocolError on
@@ -21,23 +33,28 @@ of an MMA queue, a pending copy).  The checker raises ProtocolError on
   has already completed phase k + 1 (mbarrier.try_wait.parity cannot tell
   phase k from phase k + 2, so such a wait would block or pass on the wrong
   phase);
-* a data hazard: an operand read before the data it needs was written
-  (D1 of the wrong tile, a stage or direction buffer not yet landed, A2 or D2
+* an arrival that would count towards the wrong phase (more arrivals than
+  the barrier's count while a phase is open is caught as a phase completing
+  early, which the data checks then see);
+* a data hazard: an operand read before the data it needs was written (D1 of
+  the wrong tile, a stage or direction buffer not yet landed, A2 or D2
   holding the wrong tiles), or a buffer overwritten before its last reader
   has consumed it.
 
 `fail_prob` > 0 also exercises the failure path: a wait that is not yet
 satisfied may give up (a bounded wait running out), exactly as the kernel's
-waits do, and then the warp carries `bad` to the rendezvous, which every warp
-leaves together (bar.red.or), or sets the CTA's abort flag, which makes every
-other unsatisfied wait give up at once.  The checker then also requires that
-no MMA or copy is outstanding when the last warp reaches the teardown (TMEM is
-freed and the CTA exits there).
+waits do; the warp then sets the CTA's abort flag, which makes every other
+unsatisfied wait give up at once, and leaves its loop.  The checker then also
+requires that no MMA or copy is outstanding when the last warp reaches the
+teardown (TMEM is freed and the CTA exits there).
 
 `mutation` plants one known mistake in the protocol (the checker must catch
 it): "refill_early" refills a stage one tile too soon, "no_a2_wait" stores A2
-without waiting for the previous GEMM2, "gemm2_early" issues GEMM2 before the
-rendezvous, "no_drain" lets warp 0 skip its drain.
+without waiting for the GEMM2 that read it last, "no_d1_wait" issues GEMM1
+without waiting for the D1 buffer to be released, "release_early" releases D1
+before loading it, "no_d2_wait" starts a period without waiting for the fold
+of the period that used the accumulator before, "no_drain" lets the GEMM1
+warp skip its drain.
 """
 from __future__ import annotations
 
@@ -98,241 +115,284 @@ def make_items(rng, n_items, max_tiles):
     return [rng.randint(1, max_tiles) for _ in range(n_items)]
 
 
-class Worker:
-    """One worker of the kernel; `items` is the number of tiles of each item."""
+class Cta:
+    """One CTA of the kernel; `items` is the number of tiles of each item."""
 
-    def __init__(self, items, nst, flush, seed, mutation=None, fail_prob=0.0, async_weight=1.0, slow_mma0=False):
+    def __init__(self, items, ns, nd, flush, seed, mutation=None, fail_prob=0.0, async_weight=1.0,
+                 slow_mma=False):
         self.rng = random.Random(seed)
         self.async_weight = async_weight  # < 1: MMAs and copies lag behind the warps
-        self.slow_mma0 = slow_mma0  # warp 0's MMAs far slower than everything else
+        self.slow_mma = slow_mma  # the GEMM1 warp's MMAs far slower than everything else
         self.fail_prob = fail_prob
         self.abort = False
-        self.nst = nst
+        self.ns = ns
+        self.nd = nd
         self.F = flush
         self.mut = mutation
-        # the worker's tile sequence: (item, j, ntile)
+        self.items = list(items)
+        # the CTA's tile sequence: (item, j, ntile)
         self.tiles = [(i, j, nt) for i, nt in enumerate(items) for j in range(nt)]
         self.T = len(self.tiles)
         self.n_items = len(items)
-        # barriers
-        self.full = [Barrier("full[%d]" % s) for s in range(nst)]
-        self.a1_full = [Barrier("a1_full[%d]" % b) for b in range(2)]
-        self.d1_full = Barrier("d1_full")
-        self.d2_ready = Barrier("d2_ready")
-        self.a2_free = Barrier("a2_free")
-        self.drain = Barrier("drain")
-        self.drain2 = Barrier("drain2")
-        # named barrier (rendezvous) state
-        self.bar_gen = 0
-        self.bar_count = 0
-        self.bar_or = False
-        self.bar_result = {}  # generation -> OR of the warps' flags
-        # data
-        self.stage = [None] * nst  # (tile, landed)
-        self.dirs = [None] * 2  # (item, landed)
-        self.d1 = None
-        self.d1_read = {}  # tile -> set of warps
-        self.a2 = [None] * 4  # tile per lane quarter
-        self.d2 = None  # (period, set of tiles)
-        self.folded = {}  # period -> set of warps
-        self.g1_done = set()
-        self.g2_done = set()
-        self.g1_of_item_done = {}  # item -> tiles whose GEMM1 executed
-        # async work
-        self.mma_q = {0: [], 2: []}
-        self.tma = []  # pending copies
-        # periods: tile -> period index, period -> tiles
+        # accumulation periods of each warpgroup: its tiles of an item, F at a
+        # time; tile -> (warpgroup, period), first / last tile of a period
         self.period_of = {}
         self.period_tiles = {}
-        pos, p = 0, 0
-        for g, (i, j, nt) in enumerate(self.tiles):
-            self.period_of[g] = p
-            self.period_tiles.setdefault(p, set()).add(g)
-            last = pos == flush - 1 or j == nt - 1
-            if last:
-                p += 1
-                pos = 0
-            else:
-                pos += 1
+        self.first = {}
+        self.last = {}
+        self.item_periods = []  # per item: [periods of warpgroup 0, periods of warpgroup 1]
+        pcount = [0, 0]
+        g = 0
+        for i, nt in enumerate(items):
+            own = [[g + j for j in range(nt) if (g + j) % 2 == w] for w in range(2)]
+            per_item = [[], []]
+            for w in range(2):
+                for a in range(0, len(own[w]), flush):
+                    chunk = own[w][a:a + flush]
+                    p = pcount[w]
+                    pcount[w] += 1
+                    per_item[w].append(p)
+                    self.period_tiles[(w, p)] = set(chunk)
+                    for t in chunk:
+                        self.period_of[t] = (w, p)
+                        self.first[t] = t == chunk[0]
+                        self.last[t] = t == chunk[-1]
+            self.item_periods.append(per_item)
+            g += nt
+        # barriers
+        self.sfull = [Barrier("sfull[%d]" % s) for s in range(ns)]
+        self.sempty = [Barrier("sempty[%d]" % s) for s in range(ns)]
+        self.dfull = [Barrier("dfull[%d]" % b) for b in range(2)]
+        self.dempty = [Barrier("dempty[%d]" % b) for b in range(2)]
+        self.d1full = [Barrier("d1full[%d]" % d) for d in range(nd)]
+        self.d1empty = [Barrier("d1empty[%d]" % d, 4) for d in range(nd)]
+        self.a2full = [Barrier("a2full[%d]" % b, 4) for b in range(2)]
+        self.a2empty = [Barrier("a2empty[%d]" % b) for b in range(2)]
+        self.d2full = [[Barrier("d2full[%d][%d]" % (w, b)) for b in range(2)] for w in range(2)]
+        self.d2empty = [[Barrier("d2empty[%d][%d]" % (w, b), 4) for b in range(2)] for w in range(2)]
+        self.drain1 = Barrier("drain1")
+        self.drain2 = [Barrier("drain2[%d]" % w) for w in range(2)]
+        # data
+        self.stage = [None] * ns  # (tile, landed)
+        self.dirs = [None] * 2  # (item, landed)
+        self.d1 = [None] * nd  # tile whose projections the buffer holds
+        self.d1_read = {}  # tile -> set of warps that loaded it
+        self.a2 = [[None] * 4 for _ in range(2)]  # per buffer, per lane quarter: tile
+        self.d2 = [[None] * 2 for _ in range(2)]  # per warpgroup, buffer: (period, set of tiles)
+        self.folded = {}  # (warpgroup, period) -> set of fold warps
+        self.g1_done = set()
+        self.g2_done = set()
+        self.g1_of_item_done = {}
+        # async work
+        self.mma_q = {"g1": [], "g2_0": [], "g2_1": []}
+        self.tma = []  # pending copies
+        self.progs = {"tma": self._tma_warp(), "g1": self._gemm1_warp(),
+                      "g2_0": self._gemm2_warp(0), "g2_1": self._gemm2_warp(1)}
+        for wg in range(2):
+            for q in range(4):
+                self.progs[("r", wg, q)] = self._rounding_warp(wg, q)
+        for q in range(4):
+            self.progs[("f", q)] = self._fold_warp(q)
         self.finished = set()
-        self.gens = {w: self._rounding_warp(w) for w in range(4)}
-        self.blocked = {}  # warp -> predicate that must hold to resume
-
-    # ---------------------------------------------------------------- helpers
-    def _flags(self, g, pos):
-        i, j, nt = self.tiles[g]
-        first = pos == 0
-        item_end = j == nt - 1
-        last = pos == self.F - 1 or item_end
-        has_next = g + 1 < self.T
-        return first, item_end, last, has_next
+        self.blocked = {}
 
     def _wait(self, who, bar, k, may_fail=True):
         bar.start_wait(who, k)
         return ("wait", bar, k, may_fail)
 
-    # ------------------------------------------------------------- data paths
-    def _tma_stage(self, t):
-        s = t % self.nst
-        old = t - self.nst
-        if old >= 0 and not (old in self.g1_done and old in self.g2_done):
-            raise ProtocolError("stage %d refilled with tile %d before both GEMMs of tile %d executed" % (s, t, old))
-        bar = self.full[s]
-        bar.expect_tx(1)
-        bar.arrive()
-        self.tma.append(("stage", s, t, bar))
-
-    def _tma_dirs(self, item):
-        b = item % 2
-        old = item - 2
-        if old >= 0:
-            n_old = sum(1 for (i, _, _) in self.tiles if i == old)
-            if len(self.g1_of_item_done.get(old, ())) != n_old:
+    # ------------------------------------------------------------ programs
+    def _tma_warp(self):
+        ns = self.ns
+        lg = 0
+        ok = True
+        issued_dirs = 0
+        for k in range(self.n_items):
+            if k >= 2:
+                ok = yield self._wait("tma", self.dempty[k % 2], (k - 2) // 2)
+                if not ok:
+                    break
+            old = k - 2
+            if old >= 0 and len(self.g1_of_item_done.get(old, ())) != self.items[old]:
                 raise ProtocolError("direction buffer %d refilled with item %d before item %d's GEMM1s executed"
-                                    % (b, item, old))
-        bar = self.a1_full[b]
-        bar.expect_tx(1)
-        bar.arrive()
-        self.tma.append(("dirs", b, item, bar))
+                                    % (k % 2, k, old))
+            self.dfull[k % 2].expect_tx(1)
+            self.dfull[k % 2].arrive()
+            self.tma.append(("dirs", k % 2, k, self.dfull[k % 2]))
+            issued_dirs += 1
+            for j in range(self.items[k]):
+                g = lg
+                s = g % ns
+                if g >= ns:
+                    k_wait = g // ns - 1
+                    if self.mut == "refill_early":
+                        k_wait -= 1
+                    if k_wait >= 0:
+                        ok = yield self._wait("tma", self.sempty[s], k_wait)
+                        if not ok:
+                            break
+                    old = g - ns
+                    if not (old in self.g1_done and old in self.g2_done):
+                        raise ProtocolError("stage %d refilled with tile %d before both GEMMs of tile %d executed"
+                                            % (s, g, old))
+                self.sfull[s].expect_tx(1)
+                self.sfull[s].arrive()
+                self.tma.append(("stage", s, g, self.sfull[s]))
+                lg += 1
+            if not ok:
+                break
+        if not ok:
+            self.abort = True
+        # drain: the copies still in flight land before the teardown
+        for t in range(max(0, lg - ns), lg):
+            yield self._wait("tma", self.sfull[t % ns], t // ns, may_fail=False)
+        for t in range(max(0, issued_dirs - 2), issued_dirs):
+            yield self._wait("tma", self.dfull[t % 2], t // 2, may_fail=False)
 
+    def _gemm1_warp(self):
+        ns, nd = self.ns, self.nd
+        g = 0
+        ok = True
+        for k in range(self.n_items):
+            ok = yield self._wait("g1", self.dfull[k % 2], k // 2)
+            if not ok:
+                break
+            for j in range(self.items[k]):
+                ok = yield self._wait("g1", self.sfull[g % ns], g // ns)
+                if ok and g >= nd and self.mut != "no_d1_wait":
+                    ok = yield self._wait("g1", self.d1empty[g % nd], g // nd - 1)
+                if not ok:
+                    break
+                self.mma_q["g1"].append(("gemm1", g))
+                self.mma_q["g1"].append(("commit", self.d1full[g % nd]))
+                g += 1
+            if not ok:
+                break
+            self.mma_q["g1"].append(("commit", self.dempty[k % 2]))
+        if not ok:
+            self.abort = True
+        if self.mut != "no_drain":
+            self.mma_q["g1"].append(("commit", self.drain1))
+            yield self._wait("g1", self.drain1, 0, may_fail=False)
+
+    def _gemm2_warp(self, w):
+        who = "g2_%d" % w
+        q = self.mma_q[who]
+        ok = True
+        for g in range(w, self.T, 2):
+            pw, p = self.period_of[g]
+            if self.first[g] and p >= 2 and self.mut != "no_d2_wait":
+                ok = yield self._wait(who, self.d2empty[w][p % 2], p // 2 - 1)
+                if not ok:
+                    break
+            ok = yield self._wait(who, self.a2full[w], g // 2)
+            if not ok:
+                break
+            q.append(("gemm2", g))
+            q.append(("commit", self.a2empty[w]))
+            q.append(("commit", self.sempty[g % self.ns]))
+            if self.last[g]:
+                q.append(("commit", self.d2full[w][p % 2]))
+        if not ok:
+            self.abort = True
+        q.append(("commit", self.drain2[w]))
+        yield self._wait(who, self.drain2[w], 0, may_fail=False)
+
+    def _rounding_warp(self, wg, q):
+        who = ("r", wg, q)
+        nd = self.nd
+        ok = True
+        for g in range(wg, self.T, 2):
+            d = g % nd
+            if self.mut == "release_early":
+                self.d1empty[d].arrive()
+            ok = yield self._wait(who, self.d1full[d], g // nd)
+            if not ok:
+                break
+            if self.d1[d] != g:
+                raise ProtocolError("%r reads D1[%d] holding tile %r, wants %d" % (who, d, self.d1[d], g))
+            self.d1_read.setdefault(g, set()).add(who)
+            if self.mut != "release_early":
+                self.d1empty[d].arrive()
+            yield ("step",)  # the rounding itself
+            if g >= 2 and self.mut != "no_a2_wait":
+                ok = yield self._wait(who, self.a2empty[wg], g // 2 - 1)
+                if not ok:
+                    break
+            if g >= 2 and (g - 2) not in self.g2_done:
+                raise ProtocolError("%r overwrites A2[%d] before GEMM2(%d) read it" % (who, wg, g - 2))
+            self.a2[wg][q] = g
+            self.a2full[wg].arrive()
+        if not ok:
+            self.abort = True
+
+    def _fold_warp(self, q):
+        who = ("f", q)
+        ok = True
+        for per_item in self.item_periods:
+            for i in range(max(len(per_item[0]), len(per_item[1]))):
+                for w in range(2):
+                    if i >= len(per_item[w]):
+                        continue
+                    p = per_item[w][i]
+                    ok = yield self._wait(who, self.d2full[w][p % 2], p // 2)
+                    if not ok:
+                        break
+                    cur = self.d2[w][p % 2]
+                    if cur is None or cur[0] != p or cur[1] != self.period_tiles[(w, p)]:
+                        raise ProtocolError("%r folds period %d of warpgroup %d from D2 holding %r" % (who, p, w, cur))
+                    self.folded.setdefault((w, p), set()).add(who)
+                    self.d2empty[w][p % 2].arrive()
+                if not ok:
+                    break
+            if not ok:
+                break
+        if not ok:
+            self.abort = True
+
+    # ----------------------------------------------------------- async ops
     def _exec_gemm1(self, t):
-        s = t % self.nst
+        s = t % self.ns
         item = self.tiles[t][0]
+        d = t % self.nd
         if self.stage[s] != (t, True):
             raise ProtocolError("GEMM1(%d) reads stage %d holding %r" % (t, s, self.stage[s]))
         if self.dirs[item % 2] != (item, True):
             raise ProtocolError("GEMM1(%d) reads directions %r, wants item %d" % (t, self.dirs[item % 2], item))
-        if t > 0 and len(self.d1_read.get(t - 1, ())) != 4:
-            raise ProtocolError("GEMM1(%d) overwrites D1 before every warp read D1(%d)" % (t, t - 1))
-        self.d1 = t
+        old = t - self.nd
+        if old >= 0 and len(self.d1_read.get(old, ())) != 4:
+            raise ProtocolError("GEMM1(%d) overwrites D1[%d] before every warp read D1(%d)" % (t, d, old))
+        self.d1[d] = t
         self.g1_done.add(t)
         self.g1_of_item_done.setdefault(item, set()).add(t)
 
-    def _exec_gemm2(self, t, first):
-        s = t % self.nst
+    def _exec_gemm2(self, t):
+        s = t % self.ns
+        b = t % 2
         if self.stage[s] != (t, True):
             raise ProtocolError("GEMM2(%d) reads stage %d holding %r" % (t, s, self.stage[s]))
-        if self.a2 != [t] * 4:
-            raise ProtocolError("GEMM2(%d) reads A2 holding tiles %r" % (t, self.a2))
-        p = self.period_of[t]
-        if first:
-            if p > 0 and len(self.folded.get(p - 1, ())) != 4:
-                raise ProtocolError("GEMM2(%d) starts period %d before period %d was folded" % (t, p, p - 1))
-            self.d2 = (p, {t})
+        if self.a2[b] != [t] * 4:
+            raise ProtocolError("GEMM2(%d) reads A2[%d] holding tiles %r" % (t, b, self.a2[b]))
+        w, p = self.period_of[t]
+        if self.first[t]:
+            if p >= 2 and len(self.folded.get((w, p - 2), ())) != 4:
+                raise ProtocolError("GEMM2(%d) starts period %d of warpgroup %d before period %d was folded"
+                                    % (t, p, w, p - 2))
+            self.d2[w][p % 2] = (p, {t})
         else:
-            if self.d2 is None or self.d2[0] != p:
-                raise ProtocolError("GEMM2(%d) accumulates into D2 of period %r" % (t, self.d2))
-            self.d2[1].add(t)
+            cur = self.d2[w][p % 2]
+            if cur is None or cur[0] != p:
+                raise ProtocolError("GEMM2(%d) accumulates into D2 of period %r" % (t, cur))
+            cur[1].add(t)
         self.g2_done.add(t)
 
-    # ------------------------------------------------------------ warp program
-    def _rounding_warp(self, w):
-        # Every wait is `ok = yield ("wait", bar, k)`: True once the phase has
-        # completed, False when it gives up (timeout or abort flag).
-        nst = self.nst
-        T = self.T
-        lg = la = cg = ca = 0
-        if w == 1 and T > 0:  # loader prologue
-            for item in range(min(2, self.n_items)):
-                self._tma_dirs(item)
-                la += 1
-            while lg < nst and lg < T:
-                self._tma_stage(lg)
-                lg += 1
-        if w == 0 and T > 0:  # GEMM1(0) once its operands have landed
-            ok = yield self._wait(w, self.a1_full[0], 0)
-            ca += 1
-            if ok:
-                ok = yield self._wait(w, self.full[0], 0)
-                cg += 1
-            if ok:
-                self.mma_q[0].append(("gemm1", 0))
-                self.mma_q[0].append(("commit", self.d1_full))
-            else:
-                self.abort = True
-        pos = 0
-        pe = 0
-        bad = False
-        for g in range(T):
-            first, item_end, last, has_next = self._flags(g, pos)
-            if not bad:
-                bad = not (yield self._wait(w, self.d1_full, g))
-            if not bad:
-                if self.d1 != g:
-                    raise ProtocolError("warp %d reads D1 holding tile %r, wants %d" % (w, self.d1, g))
-                self.d1_read.setdefault(g, set()).add(w)
-                if g > 0 and self.mut != "no_a2_wait":
-                    bad = not (yield self._wait(w, self.a2_free, g - 1))
-                if not bad:
-                    if g > 0 and (g - 1) not in self.g2_done:
-                        raise ProtocolError("warp %d overwrites A2 before GEMM2(%d) read it" % (w, g - 1))
-                    self.a2[w] = g
-                    if w == 2 and self.mut == "gemm2_early":
-                        self._issue_gemm2(g, first, last)
-            if (yield ("rendezvous", bad)):
-                break  # every warp leaves here together
-            if w == 1:
-                limit = g + nst if self.mut == "refill_early" else g - 1 + nst
-                while lg <= limit and lg < T:
-                    self._tma_stage(lg)
-                    lg += 1
-                if item_end and la < self.n_items:
-                    self._tma_dirs(la)
-                    la += 1
-            if w == 0 and has_next:
-                ok = True
-                if item_end:
-                    ok = yield self._wait(w, self.a1_full[ca % 2], ca // 2)
-                    ca += 1
-                if ok:
-                    ok = yield self._wait(w, self.full[cg % nst], cg // nst)
-                    cg += 1
-                if ok:
-                    self.mma_q[0].append(("gemm1", g + 1))
-                    self.mma_q[0].append(("commit", self.d1_full))
-                else:
-                    self.abort = True
-            if w == 2 and self.mut != "gemm2_early":
-                self._issue_gemm2(g, first, last)
-            if last:
-                bad = not (yield self._wait(w, self.d2_ready, pe))
-                if not bad:
-                    p = self.period_of[g]
-                    if self.d2 is None or self.d2[0] != p or self.d2[1] != self.period_tiles[p]:
-                        raise ProtocolError("warp %d folds period %d from D2 holding %r" % (w, p, self.d2))
-                    self.folded.setdefault(p, set()).add(w)
-                pe += 1
-            pos = 0 if last else pos + 1
-        if bad:
-            self.abort = True
-        # drain: the MMAs of warps 0 and 2 and the loader's copies complete
-        # before TMEM is freed (these waits never give up early)
-        if w == 0 and self.mut != "no_drain":
-            self.mma_q[0].append(("commit", self.drain))
-            yield self._wait(w, self.drain, 0, may_fail=False)
-        if w == 2:
-            self.mma_q[2].append(("commit", self.drain2))
-            yield self._wait(w, self.drain2, 0, may_fail=False)
-        if w == 1:
-            for t in range(max(0, lg - nst), lg):
-                yield self._wait(w, self.full[t % nst], t // nst, may_fail=False)
-            for t in range(max(0, la - 2), la):
-                yield self._wait(w, self.a1_full[t % 2], t // 2, may_fail=False)
-
-    def _issue_gemm2(self, g, first, last):
-        self.mma_q[2].append(("gemm2", g, first))
-        if last:
-            self.mma_q[2].append(("commit", self.d2_ready))
-        self.mma_q[2].append(("commit", self.a2_free))
-
-    # --------------------------------------------------------------- scheduler
+    # ----------------------------------------------------------- scheduler
     def _enabled(self):
         agents = []
-        for w in range(4):
+        for w in self.progs:
             if w in self.finished:
                 continue
             req = self.blocked.get(w)
-            if req is None:
+            if req is None or req[0] == "step":
                 agents.append(("warp", w, None))
             elif req[0] == "wait":
                 bar, k, may_fail = req[1], req[2], req[3]
@@ -342,15 +402,13 @@ class Worker:
                     agents.append(("warp", w, False))  # the abort flag: give up at once
                 elif may_fail and self.fail_prob > 0 and self.rng.random() < self.fail_prob:
                     agents.append(("warp", w, False))  # the bounded wait runs out
-            elif req[0] == "rendezvous" and req[1] in self.bar_result:
-                agents.append(("warp", w, self.bar_result[req[1]]))
-        for q in (0, 2):
+        for q in self.mma_q:
             if self.mma_q[q]:
                 agents.append(("mma", q, None))
         for idx in range(len(self.tma)):
             agents.append(("tma", idx, None))
-        if self.slow_mma0 and self.mma_q[0]:
-            agents.append(("tick", None, None))  # time passes, nothing completes
+        if self.slow_mma and self.mma_q["g1"]:
+            agents.append(("tick", None, None))
         return agents
 
     def _step_warp(self, w, value):
@@ -358,29 +416,18 @@ class Worker:
         if req is not None and req[0] == "wait":
             req[1].end_wait(w)
         try:
-            nxt = self.gens[w].send(value) if req is not None else next(self.gens[w])
+            nxt = self.progs[w].send(value) if req is not None else next(self.progs[w])
         except StopIteration:
             self.finished.add(w)
             return
-        if nxt[0] == "rendezvous":
-            gen = self.bar_gen
-            self.bar_or = self.bar_or or bool(nxt[1])
-            self.bar_count += 1
-            if self.bar_count == 4:
-                self.bar_result[gen] = self.bar_or
-                self.bar_count = 0
-                self.bar_or = False
-                self.bar_gen += 1
-            self.blocked[w] = ("rendezvous", gen)
-        else:
-            self.blocked[w] = nxt
+        self.blocked[w] = nxt
 
     def _step_mma(self, q):
         op = self.mma_q[q].pop(0)
         if op[0] == "gemm1":
             self._exec_gemm1(op[1])
         elif op[0] == "gemm2":
-            self._exec_gemm2(op[1], op[2])
+            self._exec_gemm2(op[1])
         else:  # commit: every earlier operation of this warp has executed
             op[1].arrive()
 
@@ -392,21 +439,23 @@ class Worker:
             self.dirs[slot] = (content, True)
         bar.complete_tx(1)
 
-    def run(self, max_steps=200000):
+    def run(self, max_steps=400000):
         for _ in range(max_steps):
-            if len(self.finished) == 4:
-                # the teardown: TMEM is freed and the CTA exits
-                if self.tma or self.mma_q[0] or self.mma_q[2]:
+            if len(self.finished) == len(self.progs):
+                if self.tma or any(self.mma_q.values()):
                     raise ProtocolError("teardown with work in flight: %d copies, MMA queues %r"
                                         % (len(self.tma), {q: len(v) for q, v in self.mma_q.items()}))
+                if not self.abort and len(self.g2_done) != self.T:
+                    raise ProtocolError("finished with %d of %d tiles scored" % (len(self.g2_done), self.T))
                 return
             agents = self._enabled()
             if not agents:
                 raise ProtocolError("deadlock: warps %r blocked on %r" % (
-                    sorted(set(range(4)) - self.finished),
-                    {w: (r[1].name, r[2]) if r[0] == "wait" else r for w, r in self.blocked.items()}))
+                    sorted((str(w) for w in self.progs if w not in self.finished)),
+                    {str(w): (r[1].name, r[2]) if r[0] == "wait" else r for w, r in self.blocked.items()}))
             weights = [1.0 if ag[0] == "warp" else
-                       (0.002 if self.slow_mma0 and ag[:2] == ("mma", 0) else self.async_weight) for ag in agents]
+                       (0.002 if self.slow_mma and ag[:2] == ("mma", "g1") else self.async_weight)
+                       for ag in agents]
             kind, a, value = self.rng.choices(agents, weights)[0]
             if kind == "tick":
                 continue
@@ -419,9 +468,9 @@ class Worker:
         raise ProtocolError("no progress within %d steps" % max_steps)
 
 
-def check(items, nst, flush, seed, mutation=None, fail_prob=0.0, async_weight=1.0, slow_mma0=False):
-    """Run one random schedule of a worker over `items`; raises ProtocolError.
-    Returns the worker (its `abort` flag says whether a wait gave up)."""
-    wk = Worker(items, nst, flush, seed, mutation, fail_prob, async_weight, slow_mma0)
-    wk.run()
-    return wk
+def check(items, ns, nd, flush, seed, mutation=None, fail_prob=0.0, async_weight=1.0, slow_mma=False):
+    """Run one random schedule of a CTA over `items`; raises ProtocolError.
+    Returns the CTA (its `abort` flag says whether a wait gave up)."""
+    cta = Cta(items, ns, nd, flush, seed, mutation, fail_prob, async_weight, slow_mma)
+    cta.run()
+    return cta
