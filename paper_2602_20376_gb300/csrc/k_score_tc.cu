@@ -44,21 +44,28 @@
 //   TMA warp      fills a ring of NS stages (one packed coordinate tile each:
 //                 GEMM1 rows | GEMM2 rows | indicator magnitudes, one box)
 //                 and two direction buffers (one per item);
-//   GEMM1 warp    issues tile g's projections into the D1 buffer g % ND of a
-//                 ring of ND buffers in tensor memory, ahead of the rounding;
-//   rounding      two warpgroups, one thread per candidate row; warpgroup
-//                 g % 2 takes tile g: loads D1, releases the buffer at once,
-//                 turns the projections into indicator words and stores them
-//                 into its own A2 buffer;
-//   GEMM2 warps   one per rounding warpgroup (small MMAs cost their issuing
-//                 thread tens of cycles each, so two threads issue them):
-//                 GEMM2 warp w issues warpgroup w's tiles from A2[w] into
-//                 warpgroup w's accumulator D2[w][p % 2], p the warpgroup's
+//   GEMM1 warp    for every tile g: waits for the tile's stage and for D1
+//                 buffer g % ND (a ring of ND buffers in tensor memory),
+//                 arrives on the buffer's barrier (telling the rounding warps
+//                 that the stage has landed) and issues the projections; the
+//                 buffer's barrier completes on that arrival and the MMA.  It
+//                 runs ahead of the rounding as far as the ring allows, and
+//                 polls its two barriers together (every mbarrier wait costs
+//                 ~100 cycles even when its phase has completed);
+//   GEMM2 warps   two streams (one thread issues a small FP8 MMA only every
+//                 ~32 cycles): stream g % 2 issues tile g from A2[g % 3]
+//                 into its accumulator D2[v][p % NB2], p the stream's
 //                 accumulation period (at most 2048 coordinates of one item);
+//   rounding      three warpgroups, one thread per candidate row; warpgroup
+//                 g % 3 takes tile g: one wait, reads the indicator
+//                 magnitudes from the tile's stage, loads D1, releases the
+//                 buffer at once, turns the projections into indicator words
+//                 and stores them into its own A2 buffer (three warpgroups
+//                 hide the latency of their waits);
 //   fold          a warpgroup that owns the two-sum partials: per item it
-//                 reads period i of warpgroup 0, then period i of warpgroup
-//                 1, for i = 0, 1, ..., releases each accumulator, and writes
-//                 the item's FP64 partials at its end.
+//                 reads period i of stream 0, then period i of stream 1, for
+//                 i = 0, 1, ..., releases each accumulator, and writes the
+//                 item's FP64 partials at its end.
 // The rounding warpgroups, which do all the per-evaluation work, never wait
 // for an MMA they have just asked for: D1 of their next tile was issued while
 // they rounded the previous ones, and their A2 buffer was released by a GEMM2
@@ -87,15 +94,16 @@ constexpr int kTcM = 128;
 constexpr int kTcMaxStages = 24;
 constexpr int kTcPeriodCoords = 2048;  // coordinates per FP32 accumulation period
 constexpr long long kWaitLimit = 2000000000LL;
-constexpr int kTcThreads = 512;  // 16 warps: 2 rounding warpgroups, TMA, GEMM1, 2 x GEMM2, fold warpgroup
-constexpr int kWarpTma = 8, kWarpG1 = 9, kWarpG2 = 10, kWarpFold0 = 12;  // GEMM2 warps 10 and 11
+constexpr int kTcNwg = 3;         // rounding warpgroups
+constexpr int kTcThreads = 640;  // 20 warps: 3 rounding warpgroups, fold warpgroup, TMA, GEMM1, 2 x GEMM2
+constexpr int kWarpFold0 = 12, kWarpTma = 16, kWarpG1 = 17, kWarpG2 = 18;  // GEMM2 streams: warps 18 and 19
 
 // Tile shape per alphabet and rank class (KCH = 1 for r <= 4, 2 above).  R is
 // the number of coordinates per tile.  Tensor memory (512 columns of 128
 // lanes) holds
-//   D1 : ND buffers of N1 = BKG * R columns   GEMM1 projections (F16, one per column)
-//   A2 : 2 buffers of KD2 / 4 columns         GEMM2 indicator operand (4 FP8 per column), one per warpgroup
-//   D2 : 2 x 2 buffers of N2 = 2 * NOUT cols  GEMM2 accumulators, hi | lo, two per warpgroup
+//   D1 : ND buffers of N1 = BKG * R columns     GEMM1 projections (F16, one per column)
+//   A2 : 3 buffers of KD2 / 4 columns           GEMM2 indicator operand (4 FP8 per column), one per warpgroup
+//   D2 : 2 x NB2 buffers of N2 = 2 * NOUT cols  GEMM2 accumulators, hi | lo, NB2 per stream
 template <int K, int KCH>
 struct TcShape {
   static constexpr int BK = (K % 2 == 0) ? K / 2 : K;
@@ -111,11 +119,14 @@ struct TcShape {
   static constexpr int A2COLS = KD2 / 4;
   static constexpr int NOUT = KCH == 1 ? 8 : 16;  // real outputs per candidate (>= 2r)
   static constexpr int N2 = 2 * NOUT;             // GEMM2 N: hi and lo halves
-  static constexpr int ND = (3 * N1 + 2 * A2COLS + 4 * N2 <= 512) ? 3 : 2;
+  // D1 buffers and accumulators per stream: the deepest that fit, D1 first
+  static constexpr int cols(int nd, int nb2) { return nd * N1 + kTcNwg * A2COLS + 2 * nb2 * N2; }
+  static constexpr int ND = cols(3, 1) <= 512 ? 3 : 2;
+  static constexpr int NB2 = cols(ND, 2) <= 512 ? 2 : 1;
   static constexpr int D1_OFF = 0;
   static constexpr int A2_OFF = ND * N1;
-  static constexpr int D2_OFF = A2_OFF + 2 * A2COLS;
-  static constexpr int TMEM_COLS = D2_OFF + 4 * N2;
+  static constexpr int D2_OFF = A2_OFF + kTcNwg * A2COLS;
+  static constexpr int TMEM_COLS = D2_OFF + 2 * NB2 * N2;
   static_assert(TMEM_COLS <= 512, "TMEM budget");
   static_assert(N1 % 16 == 0 && N1 <= 256, "GEMM1 N");
   static_assert(KD2 % 32 == 0, "GEMM2 K (FP8 MMAs reduce 32 entries)");
@@ -149,7 +160,7 @@ struct TcLayout {
   static constexpr uint32_t STAGE_TX = TILE_BYTES;
   static constexpr int A1_BYTES = kTcM * 16 * KCH;
   static constexpr int ZERO_BYTES = 4096;
-  static constexpr int NBARS = 2 * kTcMaxStages + 2 + 2 + 2 * 3 + 2 + 2 + 4 + 4 + 3;
+  static constexpr int NBARS = 2 * kTcMaxStages + 2 + 2 + 2 * 3 + 2 * kTcNwg + 4 + 4 + 3;
   static constexpr int FIXED = 2 * A1_BYTES + ZERO_BYTES + NBARS * 8 + 64;
   // at least 120 KB of shared memory, so that two CTAs never share an SM
   // (each holds all 512 TMEM columns); the stage ring takes what is left
@@ -201,11 +212,15 @@ struct Ring {
       ph ^= 1u;
     }
   }
-  __device__ __forceinline__ void next2() {  // two slots on (N >= 2)
-    idx += 2;
-    if (idx >= N) {
-      idx -= N;
-      ph ^= 1u;
+  template <int D>
+  __device__ __forceinline__ void step() {  // D slots on
+    idx += D;
+#pragma unroll
+    for (int i = 0; i < (D + N - 1) / N; ++i) {
+      if (idx >= N) {
+        idx -= N;
+        ph ^= 1u;
+      }
     }
   }
   __device__ __forceinline__ void set(int64_t g) {  // the slot of use g
@@ -214,32 +229,30 @@ struct Ring {
   }
 };
 
-// Polling with a growing sleep between polls, for the warps off the critical
-// path (copies, folds): they give their issue slots to the rounding warps.
-__device__ __forceinline__ bool warp_wait_lazy(uint64_t* bar, uint32_t parity, volatile int* abort) {
-  bool ok = ptx::mbar_try_wait(bar, parity);
-  if (!__all_sync(0xffffffffu, ok)) {
-    const long long t0 = clock64();
-    uint32_t ns = 64;
-    for (;;) {
-      __nanosleep(ns);
-      if (ptx::mbar_try_wait(bar, parity)) {
-        ok = true;
-        break;
-      }
-      if (*abort || clock64() - t0 > kWaitLimit) {
-        ok = false;
-        break;
-      }
-      ns = ns < 1024 ? 2 * ns : 1024;
-    }
-  }
-  return __all_sync(0xffffffffu, ok);
+// Two barriers: both polled at once first, so that the latencies of two
+// complete phases overlap; `use2` false skips the second.
+__device__ __forceinline__ bool warp_wait2(uint64_t* bar1, uint32_t par1, uint64_t* bar2, uint32_t par2, bool use2,
+                                           volatile int* abort) {
+  uint32_t both;
+  asm volatile(
+      "{\n\t.reg .pred p, q;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 q, [%3], %4;\n\t"
+      "and.pred p, p, q;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(both)
+      : "r"(ptx::smem_u32(bar1)), "r"(par1), "r"(ptx::smem_u32(use2 ? bar2 : bar1)), "r"(use2 ? par2 : par1)
+      : "memory");
+  if (__all_sync(0xffffffffu, both != 0)) return true;
+  return warp_wait(bar1, par1, abort) && (!use2 || warp_wait(bar2, par2, abort));
 }
 
-// Own tiles of warpgroup w in an item whose first tile is the CTA's tile
-// g_base: j = j0, j0 + 2, ... < ntile.
-__device__ __forceinline__ int own_first(int64_t g_base, int w) { return static_cast<int>((w - (g_base & 1)) & 1); }
+// The tiles of an item (whose first tile is the CTA's tile g_base) that fall
+// to member w of a round robin of M: j = j0, j0 + M, ... < ntile.
+template <int M>
+__device__ __forceinline__ int own_first(int64_t g_base, int w) {
+  return static_cast<int>((w - static_cast<int>(g_base % M) + M) % M);
+}
 
 // The CTA's items are blockIdx.x, blockIdx.x + gridDim.x, ...; item it covers
 // coordinate chunk it / c_tiles (tiles t0 .. t0 + ntile - 1) against candidate
@@ -259,7 +272,7 @@ __device__ __forceinline__ TcItem tc_item(const TcParams& prm, int64_t it) {
 }
 
 template <int K, int KCH>
-__global__ void __launch_bounds__(kTcThreads, 1)
+__global__ void __maxnreg__(96)
     score_tc_kernel(const __grid_constant__ CUtensorMap tm_vt, const __grid_constant__ CUtensorMap tm_ct,
                     TcParams prm, const float* __restrict__ scale, double* __restrict__ partial,
                     int32_t* status) {
@@ -284,13 +297,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
   uint64_t* sempty = sfull + kTcMaxStages;    // [NS]  both GEMMs of the stage's tile done
   uint64_t* dfull = sempty + kTcMaxStages;    // [2]   direction buffer landed
   uint64_t* dempty = dfull + 2;               // [2]   every GEMM1 of the buffer's item done
-  uint64_t* d1full = dempty + 2;              // [3]   D1 buffer holds its tile's projections
+  uint64_t* d1full = dempty + 2;              // [3]   D1 buffer holds its tile, stage landed (MMA + arrival)
   uint64_t* d1empty = d1full + 3;             // [3]   every rounding warp has loaded it (4 arrivals)
-  uint64_t* a2full = d1empty + 3;             // [2]   A2 buffer written (4 arrivals)
-  uint64_t* a2empty = a2full + 2;             // [2]   GEMM2 that read it done
-  uint64_t* d2full = a2empty + 2;             // [2][2] accumulation period of warpgroup w complete
+  uint64_t* a2full = d1empty + 3;             // [3]   A2 buffer written (4 arrivals)
+  uint64_t* a2empty = a2full + kTcNwg;        // [3]   GEMM2 that read it done
+  uint64_t* d2full = a2empty + kTcNwg;        // [2][2] accumulation period of stream v complete
   uint64_t* d2empty = d2full + 4;             // [2][2] folded (4 arrivals)
-  uint64_t* drain = d2empty + 4;              // [3]   teardown of the GEMM1 / GEMM2 warps
+  uint64_t* drain = d2empty + 4;              // [3]   teardown of the GEMM2 / GEMM1 warps
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::BAR_OFF + L::NBARS * 8);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
 
@@ -302,6 +315,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int i = 0; i < 2; ++i) {
       ptx::mbar_init(&dfull[i], 1);
       ptx::mbar_init(&dempty[i], 1);
+    }
+    for (int i = 0; i < kTcNwg; ++i) {
       ptx::mbar_init(&a2full[i], 4);
       ptx::mbar_init(&a2empty[i], 1);
     }
@@ -311,7 +326,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     for (int i = 0; i < 3; ++i) ptx::mbar_init(&drain[i], 1);
     for (int i = 0; i < 3; ++i) {
-      ptx::mbar_init(&d1full[i], 1);
+      ptx::mbar_init(&d1full[i], 2);
       ptx::mbar_init(&d1empty[i], 4);
     }
     *abort_flag = 0;
@@ -346,7 +361,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     for (int64_t it = first_item, k = 0; it < prm.num_items && ok; it += grid, ++k) {
       const TcItem c = tc_item(prm, it);
       const uint32_t b = static_cast<uint32_t>(k & 1);
-      if (k >= 2) ok = warp_wait_lazy(&dempty[b], static_cast<uint32_t>(((k - 2) >> 1) & 1), abort_flag);
+      if (k >= 2) ok = warp_wait(&dempty[b], static_cast<uint32_t>(((k - 2) >> 1) & 1), abort_flag);
       if (!ok) break;
       if (lane == 0) {
         ptx::mbar_arrive_expect_tx(&dfull[b], L::A1_BYTES);
@@ -355,7 +370,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       }
       ++dloads;
       for (int j = 0; j < c.ntile; ++j) {
-        if (loads >= NS) ok = warp_wait_lazy(&sempty[st.idx], st.ph ^ 1u, abort_flag);
+        if (loads >= NS) ok = warp_wait(&sempty[st.idx], st.ph ^ 1u, abort_flag);
         if (!ok) break;
         if (lane == 0) {
           ptx::mbar_arrive_expect_tx(&sfull[st.idx], L::STAGE_TX);
@@ -389,9 +404,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       const uint32_t lbo_a1 = KCH == 2 ? kTcM * 16u : (smem_base + L::ZERO_OFF - a1);
       const uint64_t adesc = ptx::smem_desc(a1, lbo_a1, 128);
       for (int j = 0; j < c.ntile; ++j, ++g) {
-        ok = warp_wait(&sfull[st.idx], st.ph, abort_flag);
-        if (ok && g >= ND) ok = warp_wait(&d1empty[d1.idx], d1.ph ^ 1u, abort_flag);
+        // the tile's stage has landed and its D1 buffer is free (both
+        // barriers polled together: their latencies overlap)
+        ok = warp_wait2(&sfull[st.idx], st.ph, &d1empty[d1.idx], d1.ph ^ 1u, g >= ND, abort_flag);
         if (!ok) break;
+        // one arrival of the buffer's barrier (the MMA's commit is the
+        // other): the rounding warps read the magnitudes from the stage
+        if (lane == 0) ptx::mbar_arrive(&d1full[d1.idx]);
         ptx::tc_fence_after();
         const uint32_t b1 = smem_base + st.idx * L::STAGE_BYTES + L::B1_OFF_IN_STAGE;
         const uint32_t lbo_b1 = KCH == 2 ? Sh::N1 * 16u : (smem_base + L::ZERO_OFF - b1);
@@ -406,42 +425,44 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (!ok) *abort_flag = 1;
     volatile int never = 0;
-    ptx::mma_commit_elect(&drain[0]);
-    warp_wait(&drain[0], 0u, &never);
+    ptx::mma_commit_elect(&drain[2]);
+    warp_wait(&drain[2], 0u, &never);
   } else if (warp == kWarpG2 || warp == kWarpG2 + 1) {
     // ---------------------------------------------------------- GEMM2 warps
-    const int w = warp - kWarpG2;  // the rounding warpgroup whose tiles this warp issues
+    const int v = warp - kWarpG2;  // stream: the tiles g with g % 2 == v
+    constexpr int NB2 = Sh::NB2;
     constexpr uint32_t idesc2 = ptx::idesc_e4m3_f32(kTcM, Sh::N2);
     constexpr uint32_t lbo_b2 = L::N2R * 16;
-    const uint32_t a2 = tmem + Sh::A2_OFF + w * Sh::A2COLS;
-    const uint32_t d2 = tmem + Sh::D2_OFF + 2 * w * Sh::N2;
+    const uint32_t d2 = tmem + Sh::D2_OFF + v * NB2 * Sh::N2;
     Ring<NS> st;
-    int64_t g_base = 0, p = 0;  // the CTA's first tile of the item; this warpgroup's periods
+    Ring<kTcNwg> a2;            // the A2 buffer (warpgroup) of the tile and the parity of its use
+    int64_t g_base = 0, p = 0;  // the CTA's first tile of the item; this stream's periods
     bool ok = true;
     for (int64_t it = first_item; it < prm.num_items && ok; it += grid) {
       const TcItem c = tc_item(prm, it);
-      int j = own_first(g_base, w);
+      int j = own_first<2>(g_base, v);
       st.set(g_base + j);
+      a2.set(g_base + j);
       int pos = 0;
-      for (; j < c.ntile; j += 2, st.next2()) {
-        const int64_t g = g_base + j;
+      for (; j < c.ntile; j += 2, st.template step<2>(), a2.template step<2>()) {
         const bool first = pos == 0;
         const bool last = (pos == F - 1) || (j + 2 >= c.ntile);
-        const uint32_t pb = static_cast<uint32_t>(p & 1);
-        if (first && p >= 2)
-          ok = warp_wait(&d2empty[2 * w + pb], static_cast<uint32_t>(((p >> 1) - 1) & 1), abort_flag);
-        if (ok) ok = warp_wait(&a2full[w], static_cast<uint32_t>((g >> 1) & 1), abort_flag);
+        const uint32_t pb = static_cast<uint32_t>(p % NB2);
+        if (first && p >= NB2)
+          ok = warp_wait(&d2empty[v * 2 + pb], static_cast<uint32_t>(((p / NB2) - 1) & 1), abort_flag);
+        if (ok) ok = warp_wait(&a2full[a2.idx], a2.ph, abort_flag);
         if (!ok) break;
         ptx::tc_fence_after();
         const uint32_t b2 = smem_base + st.idx * L::STAGE_BYTES + L::B2_OFF_IN_STAGE;
+        const uint32_t a2t = tmem + Sh::A2_OFF + a2.idx * Sh::A2COLS;
 #pragma unroll
         for (int q = 0; q < Sh::KD2 / 32; ++q)
-          ptx::mma_e4m3_ts_elect(d2 + pb * Sh::N2, a2 + q * 8, ptx::smem_desc(b2 + q * 2 * lbo_b2, lbo_b2, 128), idesc2,
-                                 (q > 0 || !first) ? 1u : 0u);
-        ptx::mma_commit_elect(&a2empty[w]);
+          ptx::mma_e4m3_ts_elect(d2 + pb * Sh::N2, a2t + q * 8, ptx::smem_desc(b2 + q * 2 * lbo_b2, lbo_b2, 128),
+                                 idesc2, (q > 0 || !first) ? 1u : 0u);
+        ptx::mma_commit_elect(&a2empty[a2.idx]);
         ptx::mma_commit_elect(&sempty[st.idx]);
         if (last) {
-          ptx::mma_commit_elect(&d2full[2 * w + pb]);
+          ptx::mma_commit_elect(&d2full[v * 2 + pb]);
           ++p;
           pos = 0;
         } else {
@@ -452,8 +473,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     }
     if (!ok) *abort_flag = 1;
     volatile int never = 0;
-    ptx::mma_commit_elect(&drain[1 + w]);
-    warp_wait(&drain[1 + w], 0u, &never);
+    ptx::mma_commit_elect(&drain[v]);
+    warp_wait(&drain[v], 0u, &never);
   } else if (warp >= kWarpFold0) {
     // --------------------------------------------------------- fold warpgroup
     const int q = warp & 3;
@@ -464,16 +485,17 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     float hi[NOUT], lo[NOUT];
 #pragma unroll
     for (int jj = 0; jj < NOUT; ++jj) hi[jj] = lo[jj] = 0.f;
+    constexpr int NB2 = Sh::NB2;
     int64_t g_base = 0;
-    int64_t pw[2] = {0, 0};  // periods folded per warpgroup
+    int64_t pw[2] = {0, 0};  // periods folded per stream
     bool ok = true;
     for (int64_t it = first_item; it < prm.num_items && ok; it += grid) {
       const TcItem c = tc_item(prm, it);
-      // the item's periods per warpgroup: its own tiles, F at a time
+      // the item's periods per stream: its tiles, F at a time
       int nper[2];
 #pragma unroll
       for (int w = 0; w < 2; ++w) {
-        const int own = (c.ntile - own_first(g_base, w) + 1) / 2;
+        const int own = (c.ntile - own_first<2>(g_base, w) + 1) / 2;
         nper[w] = (own + F - 1) / F;
       }
       const int imax = nper[0] > nper[1] ? nper[0] : nper[1];
@@ -481,12 +503,12 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 #pragma unroll
         for (int w = 0; w < 2; ++w) {
           if (i >= nper[w] || !ok) continue;
-          const uint32_t pb = static_cast<uint32_t>(pw[w] & 1);
-          ok = warp_wait_lazy(&d2full[2 * w + pb], static_cast<uint32_t>((pw[w] >> 1) & 1), abort_flag);
+          const uint32_t pb = static_cast<uint32_t>(pw[w] % NB2);
+          ok = warp_wait(&d2full[2 * w + pb], static_cast<uint32_t>((pw[w] / NB2) & 1), abort_flag);
           if (!ok) break;
           ptx::tc_fence_after();
           uint32_t dh[NOUT], dl[NOUT];
-          const uint32_t ta = tmem + lane_base + Sh::D2_OFF + (2 * w + pb) * Sh::N2;
+          const uint32_t ta = tmem + lane_base + Sh::D2_OFF + (w * NB2 + pb) * Sh::N2;
           if constexpr (NOUT == 8) {
             uint32_t v[16];
             ptx::tmem_ld_x16(ta, v);
@@ -528,76 +550,64 @@ __global__ void __launch_bounds__(kTcThreads, 1)
       g_base += c.ntile;
     }
     if (!ok) *abort_flag = 1;
-  } else if (warp < 8) {
+  } else if (warp < 4 * kTcNwg) {
     // ----------------------------------------------------- rounding warpgroups
     const int wg = warp >> 2;
     const int q = warp & 3;
     const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
     const uint32_t a2_tmem = tmem + lane_base + Sh::A2_OFF + wg * Sh::A2COLS;
-    // load every chunk's projections before rounding when they fit the
-    // registers (one load latency per tile and the earliest release of D1)
     constexpr int NCH = R / RC;
-    constexpr bool ALL_LOADS_FIRST = BKG * NCH * (RC / 2) <= 64;
-    Ring<NS> st;
     Ring<ND> d1;
+    Ring<NS> st;
     uint32_t a2ph = 0;  // parity of this warpgroup's A2 buffer uses
     int64_t g_base = 0;
     bool ok = true;
     for (int64_t it = first_item; it < prm.num_items && ok; it += grid) {
       const TcItem c = tc_item(prm, it);
-      int j = own_first(g_base, wg);
-      st.set(g_base + j);
+      int j = own_first<kTcNwg>(g_base, wg);
       d1.set(g_base + j);
-      for (; j < c.ntile; j += 2, st.next2(), d1.next2()) {
+      st.set(g_base + j);
+      for (; j < c.ntile; j += kTcNwg, d1.template step<kTcNwg>(), st.template step<kTcNwg>()) {
         const int64_t g = g_base + j;
-        // the stage (for the indicator magnitudes) and D1 of tile g
-        ok = warp_wait(&sfull[st.idx], st.ph, abort_flag) && warp_wait(&d1full[d1.idx], d1.ph, abort_flag);
+        // D1 of tile g; its completion also says that the tile's stage has
+        // landed (the GEMM1 warp saw the stage's barrier before arriving)
+        ok = warp_wait(&d1full[d1.idx], d1.ph, abort_flag);
         if (!ok) break;
         ptx::tc_fence_after();
-        const uint4* magp = reinterpret_cast<const uint4*>(smem + st.idx * L::STAGE_BYTES + L::MAG_OFF_IN_STAGE);
+        uint32_t mag[CW];
+        {
+          const uint4* mp = reinterpret_cast<const uint4*>(smem + st.idx * L::STAGE_BYTES + L::MAG_OFF_IN_STAGE);
+#pragma unroll
+          for (int v4 = 0; v4 < CW / 4; ++v4) {
+            const uint4 m4 = mp[v4];
+            mag[4 * v4] = m4.x;
+            mag[4 * v4 + 1] = m4.y;
+            mag[4 * v4 + 2] = m4.z;
+            mag[4 * v4 + 3] = m4.w;
+          }
+        }
         const uint32_t d1_tmem = tmem + lane_base + Sh::D1_OFF + d1.idx * Sh::N1;
         uint32_t wv[G * CW];
         // D1 holds F16 projections, one per column; a packed load gives two
         // coordinates per register, so one byte permute gathers the signs of
         // four coordinates
-        uint32_t pl[ALL_LOADS_FIRST ? NCH : 1][BKG][RC / 2];
-        auto load_chunk = [&](int ch, uint32_t (&dst)[BKG][RC / 2]) {
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+          uint32_t pl[BKG][RC / 2];
 #pragma unroll
           for (int b = 0; b < BKG; ++b) {
             const uint32_t ta = d1_tmem + b * R + ch * RC;
             if constexpr (RC == 32)
-              ptx::tmem_ld_x16_pack16(ta, *reinterpret_cast<uint32_t(*)[16]>(dst[b]));
+              ptx::tmem_ld_x16_pack16(ta, *reinterpret_cast<uint32_t(*)[16]>(pl[b]));
             else
-              ptx::tmem_ld_x8_pack16(ta, *reinterpret_cast<uint32_t(*)[8]>(dst[b]));
+              ptx::tmem_ld_x8_pack16(ta, *reinterpret_cast<uint32_t(*)[8]>(pl[b]));
           }
-        };
-        auto release_d1 = [&]() {  // every projection of the tile is in registers
-          ptx::tc_fence_before();
-          __syncwarp();
-          if (lane == 0) ptx::mbar_arrive(&d1empty[d1.idx]);
-        };
-        if constexpr (ALL_LOADS_FIRST) {
-#pragma unroll
-          for (int ch = 0; ch < NCH; ++ch) load_chunk(ch, pl[ch]);
           ptx::tmem_wait_ld();
-          release_d1();
-        }
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) {
-          const int pi = ALL_LOADS_FIRST ? ch : 0;
-          if constexpr (!ALL_LOADS_FIRST) {
-            load_chunk(ch, pl[0]);
-            ptx::tmem_wait_ld();
-            if (ch == NCH - 1) release_d1();
-          }
-          uint32_t mag[RC / 4];
-#pragma unroll
-          for (int v = 0; v < RC / 16; ++v) {
-            const uint4 m4 = magp[ch * (RC / 16) + v];
-            mag[4 * v] = m4.x;
-            mag[4 * v + 1] = m4.y;
-            mag[4 * v + 2] = m4.z;
-            mag[4 * v + 3] = m4.w;
+          if (ch == NCH - 1) {
+            // every projection of the tile is in registers: release D1
+            ptx::tc_fence_before();
+            __syncwarp();
+            if (lane == 0) ptx::mbar_arrive(&d1empty[d1.idx]);
           }
 #pragma unroll
           for (int pq = 0; pq < RC / 4; ++pq) {
@@ -605,27 +615,27 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             if constexpr (K == 3) {
               // p_1 = -(p_0 + p_2): the three boundary directions sum to zero, so
               // p_1 < 0 exactly where p_0 + p_2 > 0
-              const uint32_t sum_neg = ptx::prmt(ptx::hadd2(pl[pi][0][2 * pq], pl[pi][1][2 * pq]),
-                                                 ptx::hadd2(pl[pi][0][2 * pq + 1], pl[pi][1][2 * pq + 1]), 0xFDB9u);
-              nm[0] = ptx::prmt(pl[pi][0][2 * pq], pl[pi][0][2 * pq + 1], 0xFDB9u);
+              const uint32_t sum_neg = ptx::prmt(ptx::hadd2(pl[0][2 * pq], pl[1][2 * pq]),
+                                                 ptx::hadd2(pl[0][2 * pq + 1], pl[1][2 * pq + 1]), 0xFDB9u);
+              nm[0] = ptx::prmt(pl[0][2 * pq], pl[0][2 * pq + 1], 0xFDB9u);
               nm[1] = ~sum_neg;
-              nm[2] = ptx::prmt(pl[pi][1][2 * pq], pl[pi][1][2 * pq + 1], 0xFDB9u);
+              nm[2] = ptx::prmt(pl[1][2 * pq], pl[1][2 * pq + 1], 0xFDB9u);
             } else {
 #pragma unroll
-              for (int m = 0; m < BK; ++m) nm[m] = ptx::prmt(pl[pi][m][2 * pq], pl[pi][m][2 * pq + 1], 0xFDB9u);
+              for (int m = 0; m < BK; ++m) nm[m] = ptx::prmt(pl[m][2 * pq], pl[m][2 * pq + 1], 0xFDB9u);
             }
             const int wi = ch * (RC / 4) + pq;
 #pragma unroll
             for (int gc = 0; gc < G; ++gc) {
               if constexpr (K % 2 == 1)
-                wv[gc * CW + wi] = ~nm[gc] & nm[gc + 1] & mag[pq];  // p_{k-1} > 0 and p_k < 0
+                wv[gc * CW + wi] = ~nm[gc] & nm[gc + 1] & mag[wi];  // p_{k-1} > 0 and p_k < 0
               else
-                wv[gc * CW + wi] = (nm[gc] & 0x80808080u) | mag[pq];  // sign(p_m) as +-1
+                wv[gc * CW + wi] = (nm[gc] & 0x80808080u) | mag[wi];  // sign(p_m) as +-1
             }
           }
         }
         // the GEMM2 that read this warpgroup's A2 buffer last (its previous tile) is done
-        if (g >= 2) ok = warp_wait(&a2empty[wg], a2ph ^ 1u, abort_flag);
+        if (g >= kTcNwg) ok = warp_wait(&a2empty[wg], a2ph ^ 1u, abort_flag);
         if (!ok) break;
         ptx::tc_fence_after();
 #pragma unroll

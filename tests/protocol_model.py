@@ -5,19 +5,26 @@ the programs the warps of one CTA of the tensor-core scoring kernel run:
 
 * the TMA warp, which fills a ring of NS coordinate-tile stages and two
   direction buffers;
-* the GEMM1 warp, which issues the projections of tile g into the D1 buffer
-  g % ND (a ring of ND buffers in tensor memory);
-* two rounding warpgroups (four warps each): warpgroup g % 2 loads D1 of tile
-  g, releases the buffer, rounds, and stores the indicator operand into its
-  own A2 buffer;
-* two GEMM2 warps: GEMM2 warp w issues the per-class sums of warpgroup w's
-  tiles from A2[w] into warpgroup w's accumulator D2[w][p % 2], p the index
-  of the tile's accumulation period among warpgroup w's periods (a period is
-  at most F of the warpgroup's tiles of one item);
+* the GEMM1 warp, which for every tile g waits for the tile's stage and for
+  D1 buffer g % ND (a ring of ND buffers in tensor memory) to be released,
+  arrives on the buffer's barrier (which tells the rounding warps that the
+  stage has landed) and issues the projections into the buffer (the barrier
+  completes on that arrival plus the MMA's commit); it waits for each item's
+  directions and commits their release after the item's last GEMM1;
+* two GEMM2 warps (streams): GEMM2 warp v takes the tiles g with
+  g % 2 == v;
+* NWG rounding warpgroups (four warps each): warpgroup g % NWG waits for D1
+  of tile g, reads the indicator magnitudes from the tile's stage, loads D1,
+  releases the buffer, rounds, and stores the indicator operand into its own
+  A2 buffer;
+* GEMM2 of tile g (MMA warp g % 2) reads A2[g % NWG] and accumulates into
+  the stream's accumulator D2[v][p % NB2], p the index of the tile's
+  accumulation period among stream v's periods (a period is at most F of the
+  stream's tiles of one item);
 * the fold warpgroup (four warps), which reads the accumulators at the end of
-  each period -- per item, period i of warpgroup 0, then period i of
-  warpgroup 1, for i = 0, 1, ... -- and releases them;
-* the tcgen05 operations (MMAs and commits) of the two issuing warps, which
+  each period -- per item, period i of stream 0, then period i of stream 1,
+  for i = 0, 1, ... -- and releases them;
+* the tcgen05 operations (MMAs and commits) of the issuing warps, which
   execute in issue order per warp and in any order across the warps; a commit
   arrives on its mbarrier once every earlier operation of its warp has
   executed;
@@ -119,7 +126,7 @@ class Cta:
     """One CTA of the kernel; `items` is the number of tiles of each item."""
 
     def __init__(self, items, ns, nd, flush, seed, mutation=None, fail_prob=0.0, async_weight=1.0,
-                 slow_mma=False):
+                 slow_mma=False, nwg=3, nb2=1):
         self.rng = random.Random(seed)
         self.async_weight = async_weight  # < 1: MMAs and copies lag behind the warps
         self.slow_mma = slow_mma  # the GEMM1 warp's MMAs far slower than everything else
@@ -128,19 +135,21 @@ class Cta:
         self.ns = ns
         self.nd = nd
         self.F = flush
+        self.nwg = nwg
+        self.nb2 = nb2
         self.mut = mutation
         self.items = list(items)
         # the CTA's tile sequence: (item, j, ntile)
         self.tiles = [(i, j, nt) for i, nt in enumerate(items) for j in range(nt)]
         self.T = len(self.tiles)
         self.n_items = len(items)
-        # accumulation periods of each warpgroup: its tiles of an item, F at a
-        # time; tile -> (warpgroup, period), first / last tile of a period
+        # accumulation periods of each GEMM2 stream: its tiles of an item, F at
+        # a time; tile -> (stream, period), first / last tile of a period
         self.period_of = {}
         self.period_tiles = {}
         self.first = {}
         self.last = {}
-        self.item_periods = []  # per item: [periods of warpgroup 0, periods of warpgroup 1]
+        self.item_periods = []  # per item: [periods of stream 0, periods of stream 1]
         pcount = [0, 0]
         g = 0
         for i, nt in enumerate(items):
@@ -164,22 +173,24 @@ class Cta:
         self.sempty = [Barrier("sempty[%d]" % s) for s in range(ns)]
         self.dfull = [Barrier("dfull[%d]" % b) for b in range(2)]
         self.dempty = [Barrier("dempty[%d]" % b) for b in range(2)]
-        self.d1full = [Barrier("d1full[%d]" % d) for d in range(nd)]
+        self.d1full = [Barrier("d1full[%d]" % d, 2) for d in range(nd)]
         self.d1empty = [Barrier("d1empty[%d]" % d, 4) for d in range(nd)]
-        self.a2full = [Barrier("a2full[%d]" % b, 4) for b in range(2)]
-        self.a2empty = [Barrier("a2empty[%d]" % b) for b in range(2)]
-        self.d2full = [[Barrier("d2full[%d][%d]" % (w, b)) for b in range(2)] for w in range(2)]
-        self.d2empty = [[Barrier("d2empty[%d][%d]" % (w, b), 4) for b in range(2)] for w in range(2)]
-        self.drain1 = Barrier("drain1")
+        self.a2full = [Barrier("a2full[%d]" % b, 4) for b in range(nwg)]
+        self.a2empty = [Barrier("a2empty[%d]" % b) for b in range(nwg)]
+        self.d2full = [[Barrier("d2full[%d][%d]" % (w, b)) for b in range(nb2)] for w in range(2)]
+        self.d2empty = [[Barrier("d2empty[%d][%d]" % (w, b), 4) for b in range(nb2)] for w in range(2)]
+        self.drain = [Barrier("drain[%d]" % u) for u in range(3)]
         self.drain2 = [Barrier("drain2[%d]" % w) for w in range(2)]
         # data
         self.stage = [None] * ns  # (tile, landed)
         self.dirs = [None] * 2  # (item, landed)
         self.d1 = [None] * nd  # tile whose projections the buffer holds
         self.d1_read = {}  # tile -> set of warps that loaded it
-        self.a2 = [[None] * 4 for _ in range(2)]  # per buffer, per lane quarter: tile
-        self.d2 = [[None] * 2 for _ in range(2)]  # per warpgroup, buffer: (period, set of tiles)
-        self.folded = {}  # (warpgroup, period) -> set of fold warps
+        self.a2 = [[None] * 4 for _ in range(nwg)]  # per buffer, per lane quarter: tile
+        self.d2 = [[None] * nb2 for _ in range(2)]  # per stream, buffer: (period, set of tiles)
+        self.mag_read = {}  # tile -> set of warps that read its magnitudes (from the stage)
+        self.stage_seen = set()  # tiles whose landed stage a GEMM1 warp has seen
+        self.folded = {}  # (stream, period) -> set of fold warps
         self.g1_done = set()
         self.g2_done = set()
         self.g1_of_item_done = {}
@@ -188,7 +199,7 @@ class Cta:
         self.tma = []  # pending copies
         self.progs = {"tma": self._tma_warp(), "g1": self._gemm1_warp(),
                       "g2_0": self._gemm2_warp(0), "g2_1": self._gemm2_warp(1)}
-        for wg in range(2):
+        for wg in range(nwg):
             for q in range(4):
                 self.progs[("r", wg, q)] = self._rounding_warp(wg, q)
         for q in range(4):
@@ -231,6 +242,9 @@ class Cta:
                         if not ok:
                             break
                     old = g - ns
+                    if len(self.mag_read.get(old, ())) != 4:
+                        raise ProtocolError("stage %d refilled with tile %d before tile %d's magnitudes were read"
+                                            % (s, g, old))
                     if not (old in self.g1_done and old in self.g2_done):
                         raise ProtocolError("stage %d refilled with tile %d before both GEMMs of tile %d executed"
                                             % (s, g, old))
@@ -249,77 +263,90 @@ class Cta:
             yield self._wait("tma", self.dfull[t % 2], t // 2, may_fail=False)
 
     def _gemm1_warp(self):
+        who = "g1"
+        q = self.mma_q[who]
         ns, nd = self.ns, self.nd
         g = 0
         ok = True
         for k in range(self.n_items):
-            ok = yield self._wait("g1", self.dfull[k % 2], k // 2)
+            ok = yield self._wait(who, self.dfull[k % 2], k // 2)
             if not ok:
                 break
             for j in range(self.items[k]):
-                ok = yield self._wait("g1", self.sfull[g % ns], g // ns)
+                ok = yield self._wait(who, self.sfull[g % ns], g // ns)
                 if ok and g >= nd and self.mut != "no_d1_wait":
-                    ok = yield self._wait("g1", self.d1empty[g % nd], g // nd - 1)
+                    ok = yield self._wait(who, self.d1empty[g % nd], g // nd - 1)
                 if not ok:
                     break
-                self.mma_q["g1"].append(("gemm1", g))
-                self.mma_q["g1"].append(("commit", self.d1full[g % nd]))
+                if self.stage[g % ns] != (g, True):
+                    raise ProtocolError("%s saw stage %d holding %r for tile %d" % (who, g % ns, self.stage[g % ns], g))
+                self.stage_seen.add(g)
+                self.d1full[g % nd].arrive()
+                q.append(("gemm1", g))
+                q.append(("commit", self.d1full[g % nd]))
                 g += 1
             if not ok:
                 break
-            self.mma_q["g1"].append(("commit", self.dempty[k % 2]))
+            q.append(("commit", self.dempty[k % 2]))
         if not ok:
             self.abort = True
         if self.mut != "no_drain":
-            self.mma_q["g1"].append(("commit", self.drain1))
-            yield self._wait("g1", self.drain1, 0, may_fail=False)
+            q.append(("commit", self.drain[2]))
+            yield self._wait(who, self.drain[2], 0, may_fail=False)
 
-    def _gemm2_warp(self, w):
-        who = "g2_%d" % w
+    def _gemm2_warp(self, v):
+        who = "g2_%d" % v
         q = self.mma_q[who]
+        nb2 = self.nb2
         ok = True
-        for g in range(w, self.T, 2):
-            pw, p = self.period_of[g]
-            if self.first[g] and p >= 2 and self.mut != "no_d2_wait":
-                ok = yield self._wait(who, self.d2empty[w][p % 2], p // 2 - 1)
+        for g in range(v, self.T, 2):
+            sv, p = self.period_of[g]
+            if self.first[g] and p >= nb2 and self.mut != "no_d2_wait":
+                ok = yield self._wait(who, self.d2empty[v][p % nb2], p // nb2 - 1)
                 if not ok:
                     break
-            ok = yield self._wait(who, self.a2full[w], g // 2)
+            w = g % self.nwg
+            ok = yield self._wait(who, self.a2full[w], g // self.nwg)
             if not ok:
                 break
             q.append(("gemm2", g))
             q.append(("commit", self.a2empty[w]))
             q.append(("commit", self.sempty[g % self.ns]))
             if self.last[g]:
-                q.append(("commit", self.d2full[w][p % 2]))
+                q.append(("commit", self.d2full[v][p % nb2]))
         if not ok:
             self.abort = True
-        q.append(("commit", self.drain2[w]))
-        yield self._wait(who, self.drain2[w], 0, may_fail=False)
+        q.append(("commit", self.drain[v]))
+        yield self._wait(who, self.drain[v], 0, may_fail=False)
 
     def _rounding_warp(self, wg, q):
         who = ("r", wg, q)
         nd = self.nd
         ok = True
-        for g in range(wg, self.T, 2):
+        for g in range(wg, self.T, self.nwg):
             d = g % nd
             if self.mut == "release_early":
                 self.d1empty[d].arrive()
             ok = yield self._wait(who, self.d1full[d], g // nd)
             if not ok:
                 break
+            st = self.stage[g % self.ns]
+            if g not in self.stage_seen or st != (g, True):
+                raise ProtocolError("%r reads magnitudes of tile %d from stage holding %r" % (who, g, st))
+            self.mag_read.setdefault(g, set()).add(who)
             if self.d1[d] != g:
                 raise ProtocolError("%r reads D1[%d] holding tile %r, wants %d" % (who, d, self.d1[d], g))
             self.d1_read.setdefault(g, set()).add(who)
             if self.mut != "release_early":
                 self.d1empty[d].arrive()
             yield ("step",)  # the rounding itself
-            if g >= 2 and self.mut != "no_a2_wait":
-                ok = yield self._wait(who, self.a2empty[wg], g // 2 - 1)
+            prev = g - self.nwg
+            if prev >= 0 and self.mut != "no_a2_wait":
+                ok = yield self._wait(who, self.a2empty[wg], g // self.nwg - 1)
                 if not ok:
                     break
-            if g >= 2 and (g - 2) not in self.g2_done:
-                raise ProtocolError("%r overwrites A2[%d] before GEMM2(%d) read it" % (who, wg, g - 2))
+            if prev >= 0 and prev not in self.g2_done:
+                raise ProtocolError("%r overwrites A2[%d] before GEMM2(%d) read it" % (who, wg, prev))
             self.a2[wg][q] = g
             self.a2full[wg].arrive()
         if not ok:
@@ -334,14 +361,15 @@ class Cta:
                     if i >= len(per_item[w]):
                         continue
                     p = per_item[w][i]
-                    ok = yield self._wait(who, self.d2full[w][p % 2], p // 2)
+                    nb2 = self.nb2
+                    ok = yield self._wait(who, self.d2full[w][p % nb2], p // nb2)
                     if not ok:
                         break
-                    cur = self.d2[w][p % 2]
+                    cur = self.d2[w][p % nb2]
                     if cur is None or cur[0] != p or cur[1] != self.period_tiles[(w, p)]:
-                        raise ProtocolError("%r folds period %d of warpgroup %d from D2 holding %r" % (who, p, w, cur))
+                        raise ProtocolError("%r folds period %d of stream %d from D2 holding %r" % (who, p, w, cur))
                     self.folded.setdefault((w, p), set()).add(who)
-                    self.d2empty[w][p % 2].arrive()
+                    self.d2empty[w][p % nb2].arrive()
                 if not ok:
                     break
             if not ok:
@@ -367,19 +395,20 @@ class Cta:
 
     def _exec_gemm2(self, t):
         s = t % self.ns
-        b = t % 2
+        b = t % self.nwg
         if self.stage[s] != (t, True):
             raise ProtocolError("GEMM2(%d) reads stage %d holding %r" % (t, s, self.stage[s]))
         if self.a2[b] != [t] * 4:
             raise ProtocolError("GEMM2(%d) reads A2[%d] holding tiles %r" % (t, b, self.a2[b]))
         w, p = self.period_of[t]
+        nb2 = self.nb2
         if self.first[t]:
-            if p >= 2 and len(self.folded.get((w, p - 2), ())) != 4:
-                raise ProtocolError("GEMM2(%d) starts period %d of warpgroup %d before period %d was folded"
-                                    % (t, p, w, p - 2))
-            self.d2[w][p % 2] = (p, {t})
+            if p >= nb2 and len(self.folded.get((w, p - nb2), ())) != 4:
+                raise ProtocolError("GEMM2(%d) starts period %d of stream %d before period %d was folded"
+                                    % (t, p, w, p - nb2))
+            self.d2[w][p % nb2] = (p, {t})
         else:
-            cur = self.d2[w][p % 2]
+            cur = self.d2[w][p % nb2]
             if cur is None or cur[0] != p:
                 raise ProtocolError("GEMM2(%d) accumulates into D2 of period %r" % (t, cur))
             cur[1].add(t)
@@ -468,9 +497,10 @@ class Cta:
         raise ProtocolError("no progress within %d steps" % max_steps)
 
 
-def check(items, ns, nd, flush, seed, mutation=None, fail_prob=0.0, async_weight=1.0, slow_mma=False):
+def check(items, ns, nd, flush, seed, mutation=None, fail_prob=0.0, async_weight=1.0, slow_mma=False, nwg=3,
+          nb2=1):
     """Run one random schedule of a CTA over `items`; raises ProtocolError.
     Returns the CTA (its `abort` flag says whether a wait gave up)."""
-    cta = Cta(items, ns, nd, flush, seed, mutation, fail_prob, async_weight, slow_mma)
+    cta = Cta(items, ns, nd, flush, seed, mutation, fail_prob, async_weight, slow_mma, nwg, nb2)
     cta.run()
     return cta

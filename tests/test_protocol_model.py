@@ -31,6 +31,17 @@ def test_protocol_holds_on_random_schedules(n_items, max_tiles, ns, nd, flush):
         check(items, ns, nd, flush, seed=rng.randrange(1 << 30))
 
 
+@pytest.mark.parametrize("nwg,nb2", [(3, 1), (3, 2), (2, 2), (2, 1), (4, 1)])
+def test_protocol_holds_for_each_pipeline_shape(nwg, nb2):
+    # rounding warpgroups x accumulator buffers per GEMM2 stream, as the tile
+    # shapes of the different alphabets and ranks choose them
+    rng = random.Random(100 * nwg + nb2)
+    for trial in range(100):
+        items = make_items(rng, 4, 9)
+        check(items, 5, 3, rng.choice([1, 2, 4]), seed=rng.randrange(1 << 30), nwg=nwg, nb2=nb2)
+        check(items, 6, 2, 3, seed=rng.randrange(1 << 30), nwg=nwg, nb2=nb2, fail_prob=0.01)
+
+
 @pytest.mark.parametrize("async_weight", [1.0, 0.05])
 def test_protocol_holds_with_lagging_copies_and_mmas(async_weight):
     rng = random.Random(int(async_weight * 100) + 5)
