@@ -53,11 +53,17 @@
 //                 polls its two barriers together (every mbarrier wait costs
 //                 ~100 cycles even when its phase has completed);
 //   GEMM2 warps   two streams (one thread issues a small FP8 MMA only every
-//                 ~32 cycles): stream g % 2 issues tile g from A2[g % 3]
-//                 into its accumulator D2[v][p % NB2], p the stream's
-//                 accumulation period (at most 2048 coordinates of one item);
-//   rounding      three warpgroups, one thread per candidate row; warpgroup
-//                 g % 3 takes tile g: one wait, reads the indicator
+//                 ~32 cycles): stream v = g % 2 issues tile g from
+//                 A2[g % NWG] into its accumulator D2[v][p % NB2], p the
+//                 stream's accumulation period (at most 2048 coordinates of
+//                 one item); warpgroup w signals stream v's tiles on its own
+//                 barrier [w][v], so that every barrier of the pipeline is
+//                 waited for by one party, phase after phase (a parity wait
+//                 that runs a phase ahead of its barrier passes on the wrong
+//                 phase);
+//   rounding      NWG = ND warpgroups, one thread per candidate row;
+//                 warpgroup w = g % NWG takes tile g and owns D1 buffer w
+//                 and A2 buffer w: one wait, reads the indicator
 //                 magnitudes from the tile's stage, loads D1, releases the
 //                 buffer at once, turns the projections into indicator words
 //                 and stores them into its own A2 buffer (three warpgroups
@@ -94,15 +100,13 @@ constexpr int kTcM = 128;
 constexpr int kTcMaxStages = 24;
 constexpr int kTcPeriodCoords = 2048;  // coordinates per FP32 accumulation period
 constexpr long long kWaitLimit = 2000000000LL;
-constexpr int kTcNwg = 3;         // rounding warpgroups
-constexpr int kTcThreads = 640;  // 20 warps: 3 rounding warpgroups, fold warpgroup, TMA, GEMM1, 2 x GEMM2
-constexpr int kWarpFold0 = 12, kWarpTma = 16, kWarpG1 = 17, kWarpG2 = 18;  // GEMM2 streams: warps 18 and 19
+constexpr int kTcMaxNwg = 3;  // rounding warpgroups at most (one per D1 buffer)
 
 // Tile shape per alphabet and rank class (KCH = 1 for r <= 4, 2 above).  R is
 // the number of coordinates per tile.  Tensor memory (512 columns of 128
 // lanes) holds
 //   D1 : ND buffers of N1 = BKG * R columns     GEMM1 projections (F16, one per column)
-//   A2 : 3 buffers of KD2 / 4 columns           GEMM2 indicator operand (4 FP8 per column), one per warpgroup
+//   A2 : ND buffers of KD2 / 4 columns          GEMM2 indicator operand (4 FP8 per column), one per warpgroup
 //   D2 : 2 x NB2 buffers of N2 = 2 * NOUT cols  GEMM2 accumulators, hi | lo, NB2 per stream
 template <int K, int KCH>
 struct TcShape {
@@ -119,13 +123,19 @@ struct TcShape {
   static constexpr int A2COLS = KD2 / 4;
   static constexpr int NOUT = KCH == 1 ? 8 : 16;  // real outputs per candidate (>= 2r)
   static constexpr int N2 = 2 * NOUT;             // GEMM2 N: hi and lo halves
-  // D1 buffers and accumulators per stream: the deepest that fit, D1 first
-  static constexpr int cols(int nd, int nb2) { return nd * N1 + kTcNwg * A2COLS + 2 * nb2 * N2; }
+  // D1 and A2 buffers (one each per rounding warpgroup) and accumulators
+  // per stream: the deepest that fit, D1 first
+  static constexpr int cols(int nd, int nb2) { return nd * (N1 + A2COLS) + 2 * nb2 * N2; }
   static constexpr int ND = cols(3, 1) <= 512 ? 3 : 2;
+  // rounding warpgroups: warpgroup w owns D1 buffer w, so that every
+  // barrier of the pipeline is waited for by one party, phase after phase
+  // (a parity wait that runs a phase ahead of its barrier passes on the
+  // wrong phase)
+  static constexpr int NWG = ND;
   static constexpr int NB2 = cols(ND, 2) <= 512 ? 2 : 1;
   static constexpr int D1_OFF = 0;
   static constexpr int A2_OFF = ND * N1;
-  static constexpr int D2_OFF = A2_OFF + kTcNwg * A2COLS;
+  static constexpr int D2_OFF = A2_OFF + NWG * A2COLS;
   static constexpr int TMEM_COLS = D2_OFF + 2 * NB2 * N2;
   static_assert(TMEM_COLS <= 512, "TMEM budget");
   static_assert(N1 % 16 == 0 && N1 <= 256, "GEMM1 N");
@@ -137,6 +147,10 @@ struct TcShape {
   static constexpr int RC = (R >= 32 && BKG * 16 <= 64) ? 32 : 16;
   // a warpgroup's tiles per accumulation period
   static constexpr int FLUSH = kTcPeriodCoords / R;
+  // warps: NWG rounding warpgroups, the fold warpgroup, TMA, GEMM1, two GEMM2
+  static constexpr int WARP_FOLD0 = 4 * NWG, WARP_TMA = WARP_FOLD0 + 4, WARP_G1 = WARP_TMA + 1,
+                       WARP_G2 = WARP_G1 + 1;
+  static constexpr int THREADS = 32 * (WARP_G2 + 2);
   // boundary line whose projections fill GEMM1 row block b
   static constexpr __host__ __device__ int line(int b) { return (K == 3 && b == 1) ? 2 : b; }
 };
@@ -160,7 +174,7 @@ struct TcLayout {
   static constexpr uint32_t STAGE_TX = TILE_BYTES;
   static constexpr int A1_BYTES = kTcM * 16 * KCH;
   static constexpr int ZERO_BYTES = 4096;
-  static constexpr int NBARS = 2 * kTcMaxStages + 2 + 2 + 2 * 3 + 2 * kTcNwg + 4 + 4 + 3;
+  static constexpr int NBARS = 2 * kTcMaxStages + 2 + 2 + 2 * 3 + 3 * kTcMaxNwg + 4 + 4 + 3;
   static constexpr int FIXED = 2 * A1_BYTES + ZERO_BYTES + NBARS * 8 + 64;
   // at least 120 KB of shared memory, so that two CTAs never share an SM
   // (each holds all 512 TMEM columns); the stage ring takes what is left
@@ -288,6 +302,7 @@ __global__ void __maxnreg__(96)
   constexpr int F = Sh::FLUSH;
   constexpr int CW = R / 4;  // indicator words per class per tile
   constexpr int RC = Sh::RC;
+  constexpr int NWG = Sh::NWG;
 
   extern __shared__ __align__(1024) uint8_t smem[];
   const int warp = threadIdx.x >> 5;
@@ -299,9 +314,11 @@ __global__ void __maxnreg__(96)
   uint64_t* dempty = dfull + 2;               // [2]   every GEMM1 of the buffer's item done
   uint64_t* d1full = dempty + 2;              // [3]   D1 buffer holds its tile, stage landed (MMA + arrival)
   uint64_t* d1empty = d1full + 3;             // [3]   every rounding warp has loaded it (4 arrivals)
-  uint64_t* a2full = d1empty + 3;             // [3]   A2 buffer written (4 arrivals)
-  uint64_t* a2empty = a2full + kTcNwg;        // [3]   GEMM2 that read it done
-  uint64_t* d2full = a2empty + kTcNwg;        // [2][2] accumulation period of stream v complete
+  // A2 buffer written (4 arrivals), one barrier per (warpgroup, GEMM2
+  // stream): each is waited for by one stream, phase after phase
+  uint64_t* a2full = d1empty + 3;             // [NWG][2]
+  uint64_t* a2empty = a2full + 2 * kTcMaxNwg; // [NWG] GEMM2 that read it done
+  uint64_t* d2full = a2empty + kTcMaxNwg;     // [2][2] accumulation period of stream v complete
   uint64_t* d2empty = d2full + 4;             // [2][2] folded (4 arrivals)
   uint64_t* drain = d2empty + 4;              // [3]   teardown of the GEMM2 / GEMM1 warps
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(smem + L::BAR_OFF + L::NBARS * 8);
@@ -316,8 +333,9 @@ __global__ void __maxnreg__(96)
       ptx::mbar_init(&dfull[i], 1);
       ptx::mbar_init(&dempty[i], 1);
     }
-    for (int i = 0; i < kTcNwg; ++i) {
-      ptx::mbar_init(&a2full[i], 4);
+    for (int i = 0; i < NWG; ++i) {
+      ptx::mbar_init(&a2full[2 * i], 4);
+      ptx::mbar_init(&a2full[2 * i + 1], 4);
       ptx::mbar_init(&a2empty[i], 1);
     }
     for (int i = 0; i < 4; ++i) {
@@ -337,7 +355,7 @@ __global__ void __maxnreg__(96)
     for (int i = threadIdx.x; i < L::ZERO_BYTES / 16; i += blockDim.x) z[i] = make_uint4(0u, 0u, 0u, 0u);
   }
   ptx::fence_proxy_async_smem();
-  if (warp == kWarpTma && lane == 0) {
+  if (warp == Sh::WARP_TMA && lane == 0) {
     ptx::tma_prefetch_desc(&tm_vt);
     ptx::tma_prefetch_desc(&tm_ct);
   }
@@ -353,7 +371,7 @@ __global__ void __maxnreg__(96)
   const int64_t grid = gridDim.x;
   const int64_t first_item = blockIdx.x;
 
-  if (warp == kWarpTma) {
+  if (warp == Sh::WARP_TMA) {
     // ------------------------------------------------------------ TMA warp
     Ring<NS> st;
     int64_t loads = 0, dloads = 0;
@@ -388,7 +406,7 @@ __global__ void __maxnreg__(96)
       ptx::mbar_wait_sleep(&sfull[t % NS], static_cast<uint32_t>((t / NS) & 1), &never, kWaitLimit);
     for (int64_t t = dloads > 2 ? dloads - 2 : 0; t < dloads; ++t)
       ptx::mbar_wait_sleep(&dfull[t & 1], static_cast<uint32_t>((t >> 1) & 1), &never, kWaitLimit);
-  } else if (warp == kWarpG1) {
+  } else if (warp == Sh::WARP_G1) {
     // ---------------------------------------------------------- GEMM1 warp
     constexpr uint32_t idesc1 = ptx::idesc_f16_f16(kTcM, Sh::N1);
     Ring<NS> st;
@@ -427,15 +445,18 @@ __global__ void __maxnreg__(96)
     volatile int never = 0;
     ptx::mma_commit_elect(&drain[2]);
     warp_wait(&drain[2], 0u, &never);
-  } else if (warp == kWarpG2 || warp == kWarpG2 + 1) {
+  } else if (warp == Sh::WARP_G2 || warp == Sh::WARP_G2 + 1) {
     // ---------------------------------------------------------- GEMM2 warps
-    const int v = warp - kWarpG2;  // stream: the tiles g with g % 2 == v
+    const int v = warp - Sh::WARP_G2;  // stream: the tiles g with g % 2 == v
     constexpr int NB2 = Sh::NB2;
     constexpr uint32_t idesc2 = ptx::idesc_e4m3_f32(kTcM, Sh::N2);
     constexpr uint32_t lbo_b2 = L::N2R * 16;
     const uint32_t d2 = tmem + Sh::D2_OFF + v * NB2 * Sh::N2;
     Ring<NS> st;
-    Ring<kTcNwg> a2;            // the A2 buffer (warpgroup) of the tile and the parity of its use
+    // tile g's warpgroup is g % NWG and its A2-full barrier [g % NWG][v]
+    // completes once per lcm(NWG, 2) tiles: a ring of that length gives both
+    constexpr int LCM = NWG % 2 == 0 ? NWG : 2 * NWG;
+    Ring<LCM> a2;
     int64_t g_base = 0, p = 0;  // the CTA's first tile of the item; this stream's periods
     bool ok = true;
     for (int64_t it = first_item; it < prm.num_items && ok; it += grid) {
@@ -450,16 +471,17 @@ __global__ void __maxnreg__(96)
         const uint32_t pb = static_cast<uint32_t>(p % NB2);
         if (first && p >= NB2)
           ok = warp_wait(&d2empty[v * 2 + pb], static_cast<uint32_t>(((p / NB2) - 1) & 1), abort_flag);
-        if (ok) ok = warp_wait(&a2full[a2.idx], a2.ph, abort_flag);
+        const uint32_t w = a2.idx % NWG;
+        if (ok) ok = warp_wait(&a2full[2 * w + v], a2.ph, abort_flag);
         if (!ok) break;
         ptx::tc_fence_after();
         const uint32_t b2 = smem_base + st.idx * L::STAGE_BYTES + L::B2_OFF_IN_STAGE;
-        const uint32_t a2t = tmem + Sh::A2_OFF + a2.idx * Sh::A2COLS;
+        const uint32_t a2t = tmem + Sh::A2_OFF + w * Sh::A2COLS;
 #pragma unroll
         for (int q = 0; q < Sh::KD2 / 32; ++q)
           ptx::mma_e4m3_ts_elect(d2 + pb * Sh::N2, a2t + q * 8, ptx::smem_desc(b2 + q * 2 * lbo_b2, lbo_b2, 128),
                                  idesc2, (q > 0 || !first) ? 1u : 0u);
-        ptx::mma_commit_elect(&a2empty[a2.idx]);
+        ptx::mma_commit_elect(&a2empty[w]);
         ptx::mma_commit_elect(&sempty[st.idx]);
         if (last) {
           ptx::mma_commit_elect(&d2full[v * 2 + pb]);
@@ -475,7 +497,7 @@ __global__ void __maxnreg__(96)
     volatile int never = 0;
     ptx::mma_commit_elect(&drain[v]);
     warp_wait(&drain[v], 0u, &never);
-  } else if (warp >= kWarpFold0) {
+  } else if (warp >= Sh::WARP_FOLD0) {
     // --------------------------------------------------------- fold warpgroup
     const int q = warp & 3;
     const int row = q * 32 + lane;
@@ -550,7 +572,7 @@ __global__ void __maxnreg__(96)
       g_base += c.ntile;
     }
     if (!ok) *abort_flag = 1;
-  } else if (warp < 4 * kTcNwg) {
+  } else if (warp < 4 * NWG) {
     // ----------------------------------------------------- rounding warpgroups
     const int wg = warp >> 2;
     const int q = warp & 3;
@@ -564,10 +586,10 @@ __global__ void __maxnreg__(96)
     bool ok = true;
     for (int64_t it = first_item; it < prm.num_items && ok; it += grid) {
       const TcItem c = tc_item(prm, it);
-      int j = own_first<kTcNwg>(g_base, wg);
+      int j = own_first<NWG>(g_base, wg);
       d1.set(g_base + j);
       st.set(g_base + j);
-      for (; j < c.ntile; j += kTcNwg, d1.template step<kTcNwg>(), st.template step<kTcNwg>()) {
+      for (; j < c.ntile; j += NWG, d1.template step<NWG>(), st.template step<NWG>()) {
         const int64_t g = g_base + j;
         // D1 of tile g; its completion also says that the tile's stage has
         // landed (the GEMM1 warp saw the stage's barrier before arriving)
@@ -635,7 +657,7 @@ __global__ void __maxnreg__(96)
           }
         }
         // the GEMM2 that read this warpgroup's A2 buffer last (its previous tile) is done
-        if (g >= kTcNwg) ok = warp_wait(&a2empty[wg], a2ph ^ 1u, abort_flag);
+        if (g >= NWG) ok = warp_wait(&a2empty[wg], a2ph ^ 1u, abort_flag);
         if (!ok) break;
         ptx::tc_fence_after();
 #pragma unroll
@@ -644,7 +666,7 @@ __global__ void __maxnreg__(96)
         ptx::tmem_wait_st();
         ptx::tc_fence_before();
         __syncwarp();
-        if (lane == 0) ptx::mbar_arrive(&a2full[wg]);
+        if (lane == 0) ptx::mbar_arrive(&a2full[2 * wg + (g & 1)]);
         a2ph ^= 1u;
       }
       g_base += c.ntile;
@@ -982,7 +1004,7 @@ static int score_impl(const ScorePlan& p, const void* tiles, const void* ct, con
   prm.S_pad = p.c_tiles * kTcM;
   prm.r = p.r;
   int grid = static_cast<int>(std::min<int64_t>(prm.num_items, num_sms_current()));
-  score_tc_kernel<K, KCH><<<grid, kTcThreads, L::TOTAL, st>>>(m_vt, m_ct, prm, scale, partial, status);
+  score_tc_kernel<K, KCH><<<grid, TcShape<K, KCH>::THREADS, L::TOTAL, st>>>(m_vt, m_ct, prm, scale, partial, status);
   count_launch();
   return cuda_check(cudaGetLastError(), "score_tc_kernel");
 }

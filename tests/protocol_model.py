@@ -12,11 +12,12 @@ the programs the warps of one CTA of the tensor-core scoring kernel run:
   completes on that arrival plus the MMA's commit); it waits for each item's
   directions and commits their release after the item's last GEMM1;
 * two GEMM2 warps (streams): GEMM2 warp v takes the tiles g with
-  g % 2 == v;
-* NWG rounding warpgroups (four warps each): warpgroup g % NWG waits for D1
-  of tile g, reads the indicator magnitudes from the tile's stage, loads D1,
-  releases the buffer, rounds, and stores the indicator operand into its own
-  A2 buffer;
+  g % 2 == v and waits for A2-full barrier [g % NWG][v] (one per warpgroup
+  and stream, so that each is waited for by one stream, phase after phase);
+* NWG = ND rounding warpgroups (four warps each): warpgroup w = g % NWG owns
+  D1 buffer w; it waits for D1 of tile g, reads the indicator magnitudes
+  from the tile's stage, loads D1, releases the buffer, rounds, and stores
+  the indicator operand into its own A2 buffer;
 * GEMM2 of tile g (MMA warp g % 2) reads A2[g % NWG] and accumulates into
   the stream's accumulator D2[v][p % NB2], p the index of the tile's
   accumulation period among stream v's periods (a period is at most F of the
@@ -37,9 +38,9 @@ of an MMA queue, a pending copy).  The checker raises ProtocolError on
 
 * a deadlock: nothing can run and some warp has not finished;
 * a parity wait that could alias: a warp waits for phase k of a barrier that
-  has already completed phase k + 1 (mbarrier.try_wait.parity cannot tell
-  phase k from phase k + 2, so such a wait would block or pass on the wrong
-  phase);
+  has already completed phase k + 1, or that has not yet completed phase
+  k - 1 (mbarrier.try_wait.parity cannot tell phase k from phase k + 2, so
+  such a wait would block, or pass, on the wrong phase);
 * an arrival that would count towards the wrong phase (more arrivals than
   the barrier's count while a phase is open is caught as a phase completing
   early, which the data checks then see);
@@ -109,6 +110,11 @@ class Barrier:
         if self.done >= k + 2:
             raise ProtocolError("%s: %s starts waiting for phase %d after phase %d completed"
                                 % (self.name, who, k, k + 1))
+        if self.done < k:
+            # the barrier is still in phase k - 1 (or earlier), whose parity is
+            # not k's: a parity wait for phase k would pass at once
+            raise ProtocolError("%s: %s waits for phase %d while phase %d has not completed"
+                                % (self.name, who, k, k - 1))
         self.waiters[who] = k
 
     def ready(self, k):
@@ -135,7 +141,10 @@ class Cta:
         self.ns = ns
         self.nd = nd
         self.F = flush
-        self.nwg = nwg
+        # each rounding warpgroup owns one D1 buffer (so that its barrier is
+        # waited for by one warpgroup, phase after phase): as many
+        # warpgroups as buffers
+        self.nwg = nwg = nd
         self.nb2 = nb2
         self.mut = mutation
         self.items = list(items)
@@ -175,7 +184,10 @@ class Cta:
         self.dempty = [Barrier("dempty[%d]" % b) for b in range(2)]
         self.d1full = [Barrier("d1full[%d]" % d, 2) for d in range(nd)]
         self.d1empty = [Barrier("d1empty[%d]" % d, 4) for d in range(nd)]
-        self.a2full = [Barrier("a2full[%d]" % b, 4) for b in range(nwg)]
+        # one A2-full barrier per (warpgroup, GEMM2 stream): each is waited for
+        # by one stream, phase after phase
+        self.a2full = [[Barrier("a2full[%d][%d]" % (b, v), 4) for v in range(2)] for b in range(nwg)]
+        self.lcm = nwg if nwg % 2 == 0 else 2 * nwg
         self.a2empty = [Barrier("a2empty[%d]" % b) for b in range(nwg)]
         self.d2full = [[Barrier("d2full[%d][%d]" % (w, b)) for b in range(nb2)] for w in range(2)]
         self.d2empty = [[Barrier("d2empty[%d][%d]" % (w, b), 4) for b in range(nb2)] for w in range(2)]
@@ -306,7 +318,7 @@ class Cta:
                 if not ok:
                     break
             w = g % self.nwg
-            ok = yield self._wait(who, self.a2full[w], g // self.nwg)
+            ok = yield self._wait(who, self.a2full[w][v], g // self.lcm)
             if not ok:
                 break
             q.append(("gemm2", g))
@@ -348,7 +360,7 @@ class Cta:
             if prev >= 0 and prev not in self.g2_done:
                 raise ProtocolError("%r overwrites A2[%d] before GEMM2(%d) read it" % (who, wg, prev))
             self.a2[wg][q] = g
-            self.a2full[wg].arrive()
+            self.a2full[wg][g % 2].arrive()
         if not ok:
             self.abort = True
 
@@ -497,10 +509,10 @@ class Cta:
         raise ProtocolError("no progress within %d steps" % max_steps)
 
 
-def check(items, ns, nd, flush, seed, mutation=None, fail_prob=0.0, async_weight=1.0, slow_mma=False, nwg=3,
+def check(items, ns, nd, flush, seed, mutation=None, fail_prob=0.0, async_weight=1.0, slow_mma=False, nwg=None,
           nb2=1):
     """Run one random schedule of a CTA over `items`; raises ProtocolError.
     Returns the CTA (its `abort` flag says whether a wait gave up)."""
-    cta = Cta(items, ns, nd, flush, seed, mutation, fail_prob, async_weight, slow_mma, nwg, nb2)
+    cta = Cta(items, ns, nwg or nd, flush, seed, mutation, fail_prob, async_weight, slow_mma, nwg or nd, nb2)
     cta.run()
     return cta

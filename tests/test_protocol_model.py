@@ -12,7 +12,7 @@ from protocol_model import Barrier, ProtocolError, check, make_items
 
 
 CONFIGS = [
-    # (n_items, max tiles per item, stages, D1 buffers, accumulation period)
+    # (n_items, max tiles per item, stages, D1 buffers = rounding warpgroups, accumulation period)
     (1, 1, 3, 3, 32),   # a single tile
     (3, 1, 3, 3, 32),   # one tile per item: every tile ends an item and a period
     (2, 9, 3, 3, 2),    # short ring, short periods
@@ -31,15 +31,16 @@ def test_protocol_holds_on_random_schedules(n_items, max_tiles, ns, nd, flush):
         check(items, ns, nd, flush, seed=rng.randrange(1 << 30))
 
 
-@pytest.mark.parametrize("nwg,nb2", [(3, 1), (3, 2), (2, 2), (2, 1), (4, 1)])
+@pytest.mark.parametrize("nwg,nb2", [(3, 1), (3, 2), (2, 2), (2, 1), (4, 1), (1, 2)])
 def test_protocol_holds_for_each_pipeline_shape(nwg, nb2):
-    # rounding warpgroups x accumulator buffers per GEMM2 stream, as the tile
-    # shapes of the different alphabets and ranks choose them
+    # rounding warpgroups (= D1 buffers) x accumulator buffers per GEMM2
+    # stream, as the tile shapes of the different alphabets and ranks choose
+    # them
     rng = random.Random(100 * nwg + nb2)
     for trial in range(100):
         items = make_items(rng, 4, 9)
-        check(items, 5, 3, rng.choice([1, 2, 4]), seed=rng.randrange(1 << 30), nwg=nwg, nb2=nb2)
-        check(items, 6, 2, 3, seed=rng.randrange(1 << 30), nwg=nwg, nb2=nb2, fail_prob=0.01)
+        check(items, 5, nwg, rng.choice([1, 2, 4]), seed=rng.randrange(1 << 30), nb2=nb2)
+        check(items, 6, nwg, 3, seed=rng.randrange(1 << 30), nb2=nb2, fail_prob=0.01)
 
 
 @pytest.mark.parametrize("async_weight", [1.0, 0.05])
