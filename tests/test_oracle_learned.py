@@ -140,3 +140,58 @@ def test_adam_first_step_closed_form():
     gr = g.standard_normal(50)
     out, m, v = L.adam_step(p, gr, np.zeros(50), np.zeros(50), 1, lr=0.01, eps=0.0)
     assert np.allclose(out, p - 0.01 * np.sign(gr), atol=1e-15)
+
+
+def test_features_moments_of_complex_gaussian_factor():
+    # For i.i.d. CN(0, 1) entries, |V_ij|^2 ~ Exp(1): with lambda_j the column
+    # sums of |V_ij|^2, b_ij = n |V_ij|^2 / lambda_j has mean exactly 1 and,
+    # as n grows, the Exp(1) variance, skewness and excess kurtosis 1, 2, 6;
+    # a_i = n ||V_i||^2 / sum(lambda) is Gamma(r, 1) / r: 1, 1/r, 2/sqrt(r),
+    # 6/r.  A dropped "- 3", a wrong power or a missing normalisation moves a
+    # value far outside the sampling tolerance (5 standard errors of the
+    # estimators at n = 2^20: about 0.014, 0.08 and 0.6 for Exp(1)).
+    n, r = 1 << 20, 4
+    g = I.rng(31)
+    V = (g.standard_normal((n, r)) + 1j * g.standard_normal((n, r))) / math.sqrt(2.0)
+    lam = (np.abs(V) ** 2).sum(axis=0)
+    f = L.features(V, lam)
+    assert np.allclose(f[:r], lam / lam.sum(), atol=1e-15)
+    assert np.allclose(f[:r], 1.0 / r, atol=5e-3)
+    row = f[r:r + 4]
+    assert abs(row[0] - 1.0) < 1e-12
+    assert abs(row[1] - 1.0 / r) < 0.01
+    assert abs(row[2] - 2.0 / math.sqrt(r)) < 0.04
+    assert abs(row[3] - 6.0 / r) < 0.3
+    for j in range(r):
+        col = f[r + 4 + 4 * j:r + 8 + 4 * j]
+        assert abs(col[0] - 1.0) < 1e-12
+        assert abs(col[1] - 1.0) < 0.014
+        assert abs(col[2] - 2.0) < 0.08
+        assert abs(col[3] - 6.0) < 0.6
+
+
+def test_features_population_moments_by_hand():
+    # one column with |V_i1|^2 = (0, 0, 0, 4) and lambda = 1: b = (0, 0, 0, 16)
+    # has mean 4, population variance 48, third central moment 384 (skewness
+    # 384 / 48^1.5 = 2 / sqrt(3)), fourth (3 * 256 + 20736) / 4 = 5376 (excess
+    # kurtosis 5376 / 48^2 - 3 = -2/3); the row quantity is the same vector
+    V = np.array([[0.0], [0.0], [0.0], [2.0]], dtype=np.complex128)
+    f = L.features(V, np.array([1.0]))
+    k = 5376.0 / 48.0 ** 2 - 3.0
+    assert np.allclose(f, [1.0, 4.0, 48.0, 2.0 / math.sqrt(3.0), k, 4.0, 48.0, 2.0 / math.sqrt(3.0), k], atol=1e-12)
+
+
+def test_adam_constant_gradient_closed_form():
+    # with a constant gradient g, m_t = (1 - b1^t) g and v_t = (1 - b2^t) g^2,
+    # so the bias-corrected step is lr g / (|g| + eps) at every t: after t
+    # steps the parameters have moved by t lr g / (|g| + eps)
+    g = I.rng(11)
+    p0 = g.standard_normal(40)
+    gr = g.standard_normal(40)
+    lr, b1, b2, eps = 0.003, 0.9, 0.999, 1e-3
+    p, m, v = p0.copy(), np.zeros(40), np.zeros(40)
+    for t in range(1, 26):
+        p, m, v = L.adam_step(p, gr, m, v, t, lr=lr, b1=b1, b2=b2, eps=eps)
+        assert np.allclose(m, (1 - b1 ** t) * gr, rtol=1e-12, atol=1e-15)
+        assert np.allclose(v, (1 - b2 ** t) * gr * gr, rtol=1e-12, atol=1e-15)
+        assert np.allclose(p, p0 - t * lr * gr / (np.abs(gr) + eps), rtol=1e-12, atol=1e-14)

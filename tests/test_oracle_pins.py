@@ -646,3 +646,42 @@ def test_full_rank_by_elimination_matches_singular_values():
             dep = False
         sv = np.linalg.svd(H, compute_uv=False)
         assert O.full_rank_by_elimination(H) == (not dep) == (sv[-1] > 1e-8 * sv[0])
+
+
+@pytest.mark.parametrize("K,n,seed", [(2, 9, 40), (3, 10, 41), (5, 8, 42)])
+def test_rank1_sampling_probability_at_least_margin(K, n, seed):
+    # Theorem "tail rank-1" (Sec. 4): for Q = q q^H and c = e^{i phi}, phi
+    # uniform, Pr[f(phi) = OPT_1] >= eta, the rounding margin (K / pi) times the
+    # distance of the closest theta_i + phi* to a decision boundary.  f is
+    # constant between the breakpoints phi = theta_m - arg q_i; the optimal
+    # cells (f = OPT_1, brute force) and their measure come from the oracle's
+    # scoring at the cell midpoints; eta is taken at the midpoint of the
+    # widest optimal cell; a uniform sample of phi must hit OPT_1 at the cells'
+    # measure, which must be at least eta.
+    g = I.rng(seed)
+    q = g.standard_normal(n) + 1j * g.standard_normal(n)
+    V = q[:, None]
+    opt, _ = O.bruteforce(V, K)
+    th = np.angle(q)
+    bounds = np.pi * (2 * np.arange(K) + 1) / K
+    bp = np.sort(np.mod(bounds[None, :] - th[:, None], 2 * np.pi).ravel())
+    cells = np.concatenate([bp, [bp[0] + 2 * np.pi]])
+    mids = 0.5 * (cells[:-1] + cells[1:])
+    widths = np.diff(cells)
+    fm = O.score(V, K, np.exp(1j * mids)[:, None])
+    best = fm >= opt * (1 - 1e-12)
+    assert best.any() and fm.max() <= opt * (1 + 1e-12)
+    measure = widths[best].sum() / (2 * np.pi)
+    # the K rotated copies of an optimal cell are optimal too
+    assert best.sum() % K == 0
+    phi_star = mids[best][np.argmax(widths[best])]
+    d = np.abs(np.angle(np.exp(1j * (th[:, None] + phi_star - bounds[None, :]))))
+    eta = K / np.pi * d.min()
+    assert 0 < eta <= 1
+    assert measure >= eta - 1e-12
+    S = 40000
+    phis = g.uniform(0, 2 * np.pi, S)
+    hit = (O.score(V, K, np.exp(1j * phis)[:, None]) >= opt * (1 - 1e-12)).mean()
+    se = math.sqrt(measure * (1 - measure) / S)
+    assert abs(hit - measure) < 5 * se + 1e-12
+    assert hit >= eta - 5 * se
