@@ -67,14 +67,14 @@ def _config(mode: str, world: int):
 
 # DRAM bytes (read + write) of one score_tc_kernel launch of the default scale
 # workload (n = 2^20, r = 4, K = 3, S = 2^16, tensor-core mode), from a one-pass
-# ncu capture of the launch after the L2 flush: 72.44 MB read + 137.84 MB
-# written (the FP64 partials, S x 2r doubles per coordinate chunk, dominate
-# the writes; part of them is still in L2 when the kernel ends).
-# Measured with
+# ncu capture of the launch after the L2 flush: 73.10 MB read (one pass over
+# the packed coordinate tiles and the directions; candidate tiles that reuse
+# a coordinate tile find it in L2) + 10.76 MB written (the FP64 partial sums,
+# S x 2r doubles per coordinate chunk).  Measured with
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
 #       -k regex:score_tc -s 1 -c 1 python bench.py --steps 1 --warmup 1 --no-cpu-baseline --no-learned
 # (one pass); it must be taken again whenever the kernel changes.
-SCALE_TRAFFIC_BYTES = 72.44e6 + 137.84e6
+SCALE_TRAFFIC_BYTES = 73.10e6 + 10.76e6
 
 
 def _traffic(args):
@@ -92,6 +92,42 @@ def _peaks():
             p = json.load(fh)
         return float(p.get("bf16_tflops", 1900.0)), float(p.get("hbm_gbs", 6800.0)), "measured"
     return 1900.0, 6800.0, "fallback"
+
+
+def _sm_max_mhz():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return float(json.load(fh).get("sm_max_mhz", 2070.0))
+    return 2070.0
+
+
+N_SM = 152
+FP8_OVER_BF16 = 2.0  # nominal dense fp8 / bf16 tensor rate (4.5 / 2.25 PFLOP/s)
+
+
+def tc_roofline(flops, kern_s, bf16_peak, kind):
+    """Roofline of the tensor-core kernel against the dtype-weighted peak: of
+    the 16 r flops of an evaluation, GEMM1's 8 r run in F16 (the measured
+    dense BF16 rate, which F16 shares) and GEMM2's 8 r in FP8 E4M3 (nominally
+    twice that rate), so the pair's peak is 1 / (0.5 / P + 0.5 / (2 P)) =
+    4/3 P.  The fraction on the plain BF16 basis is kept beside it."""
+    achieved = flops / kern_s / 1e12
+    peak = bf16_peak / (0.5 + 0.5 / FP8_OVER_BF16)
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_kind": "%s dense bf16 burst %.1f TFLOP/s for GEMM1's F16 half, x%.0f (nominal fp8/bf16) for "
+                         "GEMM2's FP8 half: dtype-weighted" % (kind, bf16_peak, FP8_OVER_BF16),
+            "frac_bf16_basis": achieved / bf16_peak}
+
+
+def fp32_roofline(flops, kern_s):
+    """Roofline of the FP32 CUDA-core arm: bound by FP32 issue, peak derived
+    from the unit counts and the clock (152 SMs x 128 FP32 lanes x 2 flops x
+    the maximum SM clock), against the algorithmic 16 r flops per evaluation."""
+    achieved = flops / kern_s / 1e12
+    peak = N_SM * 128 * 2 * _sm_max_mhz() * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "peak_kind": "derived: %d SMs x 128 FP32 lanes x 2 flops x %.0f MHz" % (N_SM, _sm_max_mhz())}
 
 
 class ClockSampler:
@@ -149,12 +185,12 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def cpu_baseline(seed: int, sample_S: int):
-    """The FP64 oracle, as it stands, on the host cores: sample_S directions of
-    the same workload over the full n."""
+def cpu_baseline(seed: int, sample_S: int, threads: int = 0):
+    """The FP64 oracle, as it stands, on the host cores (all of them, or
+    `threads`): sample_S directions of the same workload over the full n."""
     import oracle
     from paper_2602_20376_gb300 import inputs
-    cores = len(os.sched_getaffinity(0))
+    cores = threads or len(os.sched_getaffinity(0))
     V = inputs.factor(N, R, seed=0, scales=SCALES, dtype=np.complex64)
     C = oracle.sphere_sample(seed, sample_S, R).astype(np.complex64)
     oracle.score(V, K, C[:2], nthreads=cores)  # load + warm
@@ -188,6 +224,35 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def score_error(V, C, ws, ws_r, mode, stream, sample=1024, seed=7):
+    """The tensor-core mode's per-candidate error on the scale workload: one
+    more (untimed) scoring of S directions, then FP64 re-scoring of a fixed
+    random sample of them (lrq_rescore, equal to the FP64 oracle to 1e-9):
+    max and median of |f_tc - f_64| / f_64."""
+    import torch
+    from paper_2602_20376_gb300 import lrq
+    dev = V.device
+    Sn = C.shape[0]
+    scores = torch.empty(Sn, dtype=torch.float32, device=dev)
+    top_idx = torch.empty(TOP_M, dtype=torch.int64, device=dev)
+    top_f = torch.empty(TOP_M, dtype=torch.float32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
+    lrq.lrq_sample_score(V, K, C, True, 987654321, mode, TOP_M, scores, top_idx, top_f, ws, status, stream)
+    m = min(sample, Sn)
+    idx = torch.from_numpy(np.random.default_rng(seed).choice(Sn, m, replace=False).astype(np.int64)).to(dev)
+    f64 = torch.empty(m, dtype=torch.float64, device=dev)
+    best = torch.empty(1, dtype=torch.int64, device=dev)
+    best_f = torch.empty(1, dtype=torch.float64, device=dev)
+    wsr = lrq.workspace(lrq.lrq_rescore_workspace_size(V.shape[0], V.shape[1], m), dev)
+    lrq.lrq_rescore(V, K, C, idx, f64, None, best, best_f, wsr, status, stream)
+    torch.cuda.synchronize()
+    lrq.check_status(status, "score error sample")
+    ref = f64.cpu().numpy()
+    rel = np.abs(scores[idx].double().cpu().numpy() - ref) / ref
+    return {"max_rel": float(rel.max()), "median_rel": float(np.median(rel)), "sample": int(m),
+            "reference": "FP64 re-scoring (lrq_rescore) of a fixed random sample of the S directions"}
+
+
 def run_ours(args):
     global S
     S = args.candidates
@@ -204,7 +269,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lrq.load()
-    mode = lrq.LRQ_MODE_BF16_TC if args.mode == "bf16" else lrq.LRQ_MODE_FP32
+    mode = lrq.LRQ_MODE_TC if args.mode == "bf16" else lrq.LRQ_MODE_FP32
 
     V_host = torch.from_numpy(inputs.factor(N, R, seed=0, scales=SCALES, dtype=np.complex64)).pin_memory()
     V = V_host.to(dev)
@@ -294,17 +359,20 @@ def run_ours(args):
     peak_tf, _, peak_kind = _peaks()
     flops = 16.0 * R * N * S  # two complex r-contractions per evaluation (algorithmic)
     kern_avg_s = kern_ms * 1e-3 / args.steps
-    achieved = flops / kern_avg_s / 1e12
+    if args.mode == "bf16":
+        roof = tc_roofline(flops, kern_avg_s, peak_tf, peak_kind)
+    else:
+        roof = fp32_roofline(flops, kern_avg_s)
+    roof.update({"traffic": _traffic(args), "kernel": "score_tc_kernel" if args.mode == "bf16" else "score_fp32_kernel",
+                 "kernel_ms": kern_avg_s * 1e3, "flops_per_launch": flops})
+    tc_err = score_error(V, C, ws, ws_r, mode, stream) if args.mode == "bf16" else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f16+e4m3" if args.mode == "bf16" else "f32",
         "data": "synthetic", "config": _config(args.mode, world),
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak_tf, "unit": "TFLOP/s",
-                     "frac": achieved / peak_tf, "traffic": _traffic(args),
-                     "kernel": "score_tc_kernel" if args.mode == "bf16" else "score_fp32_kernel",
-                     "kernel_ms": kern_avg_s * 1e3, "peak_kind": peak_kind + " bf16 dense (burst)",
-                     "flops_per_launch": flops},
+        "roofline": roof,
+        "tc_error": tc_err,
         "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": N * R * 8,
                 "d2h_bytes_per_step": (TOP_M + 2) * 8},
         "gpu_launches": int(launches),
@@ -318,6 +386,9 @@ def run_ours(args):
     if world == 1 and not args.no_cpu_baseline:
         cb = cpu_baseline(1, args.cpu_sample)
         cb.pop("seconds")
+        one = cpu_baseline(2, max(4, args.cpu_sample // 16), threads=1)
+        one.pop("seconds")
+        cb["single_thread"] = one
         line["cpu_baseline"] = cb
     print(json.dumps(line), flush=True)
     if world > 1:
@@ -458,7 +529,7 @@ def run_maxcut(args):
     lrq.lrq_cut_count(rp, ci, planted, cut)
     torch.cuda.synchronize()
     planted_cut = int(cut.item())
-    ws = lrq.workspace(lrq.lrq_sample_score_workspace_size(n, 3, 3, SS, lrq.LRQ_MODE_BF16_TC, m), dev)
+    ws = lrq.workspace(lrq.lrq_sample_score_workspace_size(n, 3, 3, SS, lrq.LRQ_MODE_TC, m), dev)
     wsr = lrq.workspace(lrq.lrq_rescore_workspace_size(n, 3, m), dev)
 
     null = args.sampler == "null"
@@ -469,9 +540,9 @@ def run_maxcut(args):
     def step(i):
         if null:  # the null-vector sampler (randomised Algorithm 2) in place of the uniform sphere
             lrq.lrq_sample_null_directions(V, 3, 1 + i, SS, Cn, draws, nst)
-            out = lrq.sample_score(V, 3, C=Cn, mode=lrq.LRQ_MODE_BF16_TC, top_m=m, ws=ws)
+            out = lrq.sample_score(V, 3, C=Cn, mode=lrq.LRQ_MODE_TC, top_m=m, ws=ws)
         else:
-            out = lrq.sample_score(V, 3, C=None, S=SS, seed=1 + i, mode=lrq.LRQ_MODE_BF16_TC, top_m=m, ws=ws)
+            out = lrq.sample_score(V, 3, C=None, S=SS, seed=1 + i, mode=lrq.LRQ_MODE_TC, top_m=m, ws=ws)
         rs = lrq.rescore(V, 3, out["C"], out["top_idx"], want_z=True, ws=wsr)
         row = torch.nonzero(out["top_idx"] == rs["best"]).flatten()[0]  # z rows follow top_idx
         lrq.lrq_cut_count(rp, ci, rs["z"][row], cut)

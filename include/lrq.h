@@ -56,10 +56,29 @@ typedef enum {
   LRQ_EWORKSPACE = 6     /* ws is NULL, misaligned or smaller than required            */
 } lrq_status;
 
+/* Scoring modes of lrq_sample_score.
+ *
+ * LRQ_MODE_FP32: CUDA-core FP32 scoring; f within 1e-5 relative of the FP64
+ *   value of the same candidate (blocked FP32 sums added in FP64).
+ * LRQ_MODE_TC: tcgen05 tensor-core scoring.  Operand and accumulator types:
+ *   GEMM1 (boundary projections, whose signs give the rounding): F16 x F16
+ *   with an F16 accumulator, every coordinate row and every direction scaled
+ *   by a power of two (signs unchanged); GEMM2 (per-class sums): FP8 E4M3 x
+ *   E4M3 with FP32 accumulation, the class operand split as hi + lo E4M3 and
+ *   scaled per coordinate by a power of two; FP32 accumulation periods of at
+ *   most 2048 coordinates added error-free (two-sum) and written in FP64.
+ *   Error bound: a projection is off by at most 2^-6.8 sum_j |V_ij|_1 |c_j|_1,
+ *   so a code can differ from the FP64 decision only where |w_i| sin(margin)
+ *   is below that; each such coordinate moves ||V^H z|| by at most
+ *   2 sin(pi/K) |V_i|, and the E4M3 class operand adds at most
+ *   2^-8 sqrt(2) max|beta| |V_i| + sqrt(2) 2^-15 max|V component| per
+ *   coordinate.  The winners are re-scored in FP64 (lrq_rescore).
+ * LRQ_MODE_BF16_TC: deprecated alias of LRQ_MODE_TC (its first version used
+ *   BF16 operands for both contractions); kept so that old callers compile. */
 typedef enum {
-  LRQ_MODE_FP32 = 0,     /* CUDA-core FP32 scoring                                      */
-  LRQ_MODE_TC = 1,       /* tcgen05 tensor-core scoring: F16 signs, FP8 x2 class sums, FP32 accumulate */
-  LRQ_MODE_BF16_TC = 1   /* the same mode under its first name (its operands were BF16 then) */
+  LRQ_MODE_FP32 = 0,
+  LRQ_MODE_TC = 1,
+  LRQ_MODE_BF16_TC = 1
 } lrq_mode;
 
 /* Human-readable name of a status code (static string, never NULL). */
@@ -200,11 +219,13 @@ int lrq_rescore(const void* V, int64_t n, int r, int K, const void* C, int64_t S
  * Scratch: a fixed 4 MiB array inside the library (each GPU that loads the
  * library holds it until the process exits).  Sizes whose scratch need,
  * lrq_rescore_workspace_size(n, r, m), exceeds 4194304 bytes are rejected
- * with LRQ_EUNSUPPORTED (e.g. m = 64 works up to n = 2^25).  The first call
- * on each device looks up the array's device address; make that first call
- * before any stream capture.  All calls on a device share the array: calls
- * that overlap on the GPU (e.g. on two streams) race and must be serialised
- * by the caller.
+ * with LRQ_EUNSUPPORTED (e.g. m = 64 works up to n = 2^25).  The array's
+ * device address belongs to a CUDA context: the first call in each context
+ * (the device's primary context, a caller's own driver-API context, a new
+ * primary context after a device reset) looks it up and caches it for that
+ * context; make that first call before any stream capture.  All calls in a
+ * context share the array: calls that overlap on the GPU (e.g. on two
+ * streams) race and must be serialised by the caller.
  * ------------------------------------------------------------------------ */
 int lrq_rescore_no_alloc(const void* V, int64_t n, int r, int K, const void* C, int64_t S,
                          const int64_t* idx, int m, double* f_out, uint8_t* z_out, int64_t* best_out,

@@ -12,17 +12,24 @@
 // The scratch is the file-scope array below (kNoAllocScratchBytes = 4 MiB).
 // Every GPU that loads the library holds one copy of it until the process
 // exits.  Host code cannot use the array's name as a device address, so the
-// first call on each device looks the address up with cudaGetSymbolAddress
-// (with that device current) and caches it; make that first call before any
-// stream capture.  All calls on a device share the one array and it keeps
-// the last call's contents: calls whose kernels overlap on the GPU (for
-// instance on two streams) race on it and must be serialised by the caller.
-// Nothing in the array has to start at zero: every entry the kernels read is
-// written earlier in the same call.
+// address is looked up with cudaGetSymbolAddress in the calling thread's
+// current CUDA context the first time a call runs in that context, and
+// cached per context: the address belongs to a context (a caller running in
+// its own driver-API context, or one that reset the device and so got a new
+// primary context, gets that context's address, never a stale one).  The
+// first call in each context does this set-up; make it before any stream
+// capture.  All calls in a context share the one array and it keeps the last
+// call's contents: calls whose kernels overlap on the GPU (for instance on
+// two streams) race on it and must be serialised by the caller.  Nothing in
+// the array has to start at zero: every entry the kernels read is written
+// earlier in the same call.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
 #include <mutex>
+#include <utility>
+#include <vector>
 
 #include "lrq_internal.h"
 
@@ -32,22 +39,61 @@ constexpr size_t kNoAllocScratchBytes = size_t(4) << 20;
 
 static __device__ __align__(256) unsigned char g_rescore_scratch[kNoAllocScratchBytes];
 
+// The calling thread's current context and its process-unique id (driver
+// entry points reached through the runtime, so the library links no
+// libcuda).  False when no context is current.
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+static bool current_context_id(unsigned long long* id) {
+  static std::once_flag once;
+  static CtxGetCurrentFn get_current = nullptr;
+  static CtxGetIdFn get_id = nullptr;
+  std::call_once(once, []() {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_current = reinterpret_cast<CtxGetCurrentFn>(p);
+    p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuCtxGetId", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      get_id = reinterpret_cast<CtxGetIdFn>(p);
+  });
+  if (!get_current || !get_id) return false;
+  CUcontext ctx = nullptr;
+  if (get_current(&ctx) != CUDA_SUCCESS || ctx == nullptr) return false;
+  return get_id(ctx, id) == CUDA_SUCCESS;
+}
+
 static int scratch_address(void** out) {
   static std::mutex mu;
-  static void* cache[64] = {nullptr};
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64)
-    return fail(LRQ_ECUDA, "lrq_rescore_no_alloc: no current CUDA device");
-  std::lock_guard<std::mutex> lock(mu);
-  if (cache[dev] == nullptr) {
-    void* p = nullptr;
+  static std::vector<std::pair<unsigned long long, void*>> cache;  // context id -> address
+  unsigned long long id = 0;
+  void* p = nullptr;
+  if (!current_context_id(&id)) {
+    // no context current yet: the runtime's lookup makes the device's
+    // primary context current; then it has an id
     cudaError_t e = cudaGetSymbolAddress(&p, g_rescore_scratch);
     if (e != cudaSuccess || p == nullptr)
       return fail(LRQ_ECUDA, std::string("lrq_rescore_no_alloc: cudaGetSymbolAddress failed: ") +
                                  cudaGetErrorString(e));
-    cache[dev] = p;
+    if (!current_context_id(&id)) return fail(LRQ_ECUDA, "lrq_rescore_no_alloc: no current CUDA context");
   }
-  *out = cache[dev];
+  std::lock_guard<std::mutex> lock(mu);
+  for (const auto& kv : cache)
+    if (kv.first == id) {
+      *out = kv.second;
+      return LRQ_OK;
+    }
+  if (p == nullptr) {
+    cudaError_t e = cudaGetSymbolAddress(&p, g_rescore_scratch);
+    if (e != cudaSuccess || p == nullptr)
+      return fail(LRQ_ECUDA, std::string("lrq_rescore_no_alloc: cudaGetSymbolAddress failed: ") +
+                                 cudaGetErrorString(e));
+  }
+  cache.emplace_back(id, p);
+  *out = p;
   return LRQ_OK;
 }
 

@@ -26,8 +26,8 @@ LRQ_ENOCONV = 5
 LRQ_EWORKSPACE = 6
 
 LRQ_MODE_FP32 = 0
-LRQ_MODE_TC = 1  # tensor-core mode: F16 signs, FP8 class sums
-LRQ_MODE_BF16_TC = LRQ_MODE_TC  # its first name
+LRQ_MODE_TC = 1  # tensor-core mode: F16 x F16 (F16 accumulate) signs, FP8 E4M3 hi + lo class sums (FP32 accumulate)
+LRQ_MODE_BF16_TC = LRQ_MODE_TC  # deprecated alias (the mode's first version used BF16 operands)
 
 _lock = threading.Lock()
 _lib = None

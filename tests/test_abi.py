@@ -87,12 +87,12 @@ def test_rescore_and_cut_reject_bad_arguments(lib):
 
 def test_workspace_queries(lib):
     from paper_2602_20376_gb300 import lrq
-    a = lrq.lrq_sample_score_workspace_size(1 << 20, 4, 3, 1 << 16, lrq.LRQ_MODE_BF16_TC, 64)
+    a = lrq.lrq_sample_score_workspace_size(1 << 20, 4, 3, 1 << 16, lrq.LRQ_MODE_TC, 64)
     b = lrq.lrq_sample_score_workspace_size(1 << 20, 4, 3, 1 << 16, lrq.LRQ_MODE_FP32, 64)
     assert a > b > 0
     assert lrq.lrq_rescore_workspace_size(1 << 20, 4, 64) > 0
     with pytest.raises(lrq.LrqError):
-        lrq.lrq_sample_score_workspace_size(1 << 20, 4, 9, 1 << 16, lrq.LRQ_MODE_BF16_TC, 64)
+        lrq.lrq_sample_score_workspace_size(1 << 20, 4, 9, 1 << 16, lrq.LRQ_MODE_TC, 64)
 
 
 def test_mlp_batch_limit(lib):
