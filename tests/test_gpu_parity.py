@@ -151,6 +151,25 @@ def _tc_bound(V, K, C):
     return flip + rnd
 
 
+def _tc_bound_chunked(V, K, C, chunk=8):
+    """_tc_bound over the rows of C a few at a time (its S x n intermediates
+    would not fit in memory at n = 2^20)."""
+    return np.concatenate([_tc_bound(V, K, C[i:i + chunk]) for i in range(0, C.shape[0], chunk)])
+
+
+def _tc_rounding_floor(V, K):
+    """The bound's part that does not depend on the direction (the hi + lo
+    E4M3 rounding of the class operand): a sufficient test for candidates
+    whose deviation is below it, so that the direction-dependent part need
+    only be computed for the others."""
+    V = V.astype(np.complex128)
+    w = np.exp(2j * np.pi * np.arange(K) / K)
+    beta = np.abs(w - 1).max() if K % 2 else np.abs(np.diff(np.append(w, w[0]))).max() / 2
+    amax = max(np.abs(V.real).max(), np.abs(V.imag).max())
+    return 2.0 ** -8 * np.sqrt(2) * beta * np.linalg.norm(V, axis=1).sum() + \
+        np.sqrt(2) * 2.0 ** -15 * amax * V.shape[0]
+
+
 def _check_bf16(lrq, n, r, K, S, top_m, seed=0):
     V = I.factor(n, r, seed=seed + 11 * n + K, scales=np.linspace(2.0, 0.5, r), dtype=np.complex64)
     C = I.directions(S, r, seed=seed + S + r)
@@ -184,12 +203,19 @@ def test_score_bf16_matches_oracle(lrq, n, r, K, S):
     _check_bf16(lrq, n, r, K, S, min(8, S))
 
 
+def _best_of_s_gap(ref, idx):
+    """Relative gap between the oracle's best of all S candidates (Sec. 4.2,
+    Eq. 10) and the best of the tensor-core top m (after FP64 re-scoring,
+    whose values equal the oracle's): 0 when the best is among the top m."""
+    return (ref.max() - ref[idx].max()) / ref.max()
+
+
 def test_score_bf16_best_of_s_in_top_m(lrq):
+    # the oracle's best of S is among the tensor-core top 64, or the best of
+    # those is within 1e-4 relative of it
     rel, ref, idx = _check_bf16(lrq, 20000, 4, 3, 2048, 64, seed=5)
-    best = int(np.argmax(ref))
-    srt = np.sort(ref)[::-1]
-    if (srt[0] - srt[63]) / srt[0] > 1e-3:
-        assert best in set(idx.tolist())
+    gap = _best_of_s_gap(ref, idx)
+    assert int(np.argmax(ref)) in set(idx.tolist()) or gap <= 1e-4, gap
 
 
 @pytest.mark.parametrize("K", [3, 4])
@@ -241,12 +267,88 @@ def test_full_scale_sampled_parity(lrq):
     assert np.all(np.abs(f64 - ref) <= 1e-9 * ref)
     t = int(np.argmax(ref))
     assert int(res["best"].item()) == idx[t]
-    # sampled candidates: BF16 scores against the oracle
+    # sampled candidates: tensor-core scores against the oracle, within the
+    # derived per-candidate bound
     samp = I.rng(3).choice(S, 48, replace=False)
     f = out["scores"].cpu().numpy()[samp].astype(np.float64)
     ref_s = O.score(V, K, C[samp])
+    bound = _tc_bound_chunked(V, K, C[samp]) + 1e-5 * np.sqrt(ref_s)
+    dev = np.abs(np.sqrt(f) - np.sqrt(ref_s))
+    assert np.all(dev <= bound), (np.max(dev / bound), np.argmax(dev / bound))
     rel = np.abs(f - ref_s) / ref_s
-    assert rel.max() < 2e-2 and np.median(rel) < 3e-3, (rel.max(), np.median(rel))
+    assert np.median(rel) < 3e-3, np.median(rel)
+
+
+@pytest.mark.slow
+def test_full_scale_every_candidate(lrq):
+    # the scale workload as timed (n = 2^20, r = 4, K = 3, S = 2^16): the oracle
+    # scores all 2^16 directions on the host cores (minutes); every
+    # tensor-core score is within the derived bound (first the sufficient
+    # direction-free part, then the whole bound for the rest); the oracle's
+    # best of S is among the top 64 or within 1e-4 relative of their best; the
+    # FP64 winner is the oracle's best of the top 64
+    n, r, K, S, m = 1 << 20, 4, 3, 1 << 16, 64
+    V = I.factor(n, r, seed=0, scales=(4, 2, 1, 0.5), dtype=np.complex64)
+    Vd = _dev(V)
+    out = lrq.sample_score(Vd, K, S=S, seed=1, mode=BF16, top_m=m, want_scores=True)
+    res = lrq.rescore(Vd, K, out["C"], out["top_idx"])
+    torch.cuda.synchronize()
+    lrq.check_status(out["dev_status"])
+    lrq.check_status(res["dev_status"])
+    C = out["C"].cpu().numpy()
+    f = out["scores"].cpu().numpy().astype(np.float64)
+    ref = O.score(V, K, C)
+    dev = np.abs(np.sqrt(f) - np.sqrt(ref))
+    floor = _tc_rounding_floor(V, K) + 1e-5 * np.sqrt(ref)
+    rest = np.nonzero(dev > floor)[0]
+    if rest.size:
+        bound = _tc_bound_chunked(V, K, C[rest]) + 1e-5 * np.sqrt(ref[rest])
+        assert np.all(dev[rest] <= bound), (rest.size, np.max(dev[rest] / bound))
+    rel = np.abs(f - ref) / ref
+    idx = out["top_idx"].cpu().numpy()
+    gap = _best_of_s_gap(ref, idx)
+    print("full scale: max rel %.3e, median rel %.3e, candidates checked against the full bound %d, "
+          "best of S in top %d: %s, gap %.3e" % (rel.max(), np.median(rel), rest.size, m,
+                                                 int(np.argmax(ref)) in set(idx.tolist()), gap))
+    assert int(np.argmax(ref)) in set(idx.tolist()) or gap <= 1e-4, gap
+    f64 = res["f"].cpu().numpy()
+    assert np.all(np.abs(f64 - ref[idx]) <= 1e-9 * ref[idx])
+    assert int(res["best"].item()) == idx[int(np.argmax(ref[idx]))]
+
+
+@pytest.mark.slow
+def test_torus_pipeline_cuts_every_edge(lrq):
+    # P9 (App. G.2 torus rows; "rank 2 is exact"): the 1000 x 1000 torus is
+    # bipartite, its top Laplacian eigenvector the checkerboard, so its
+    # Max-3-Cut is |E| = 2 n.  The path -- rank-2 FP64 truncation of the CSR
+    # Laplacian, sampled directions, tensor-core scoring, FP64 re-scoring of
+    # the top 64, exact cut of the winner's codes -- must find it.
+    k1 = k2 = 1000
+    n = k1 * k2
+    rowptr, colidx = I.torus_graph(k1, k2)
+    rp, ci = _dev(rowptr), _dev(colidx)
+    Q = lrq.laplacian_matrix(rp, ci)
+    # the top eigenvalue 8 is 2 - 2 cos(2 pi / 1000) ~ 4e-5 above the next
+    # (fourfold) one, so Lanczos needs thousands of steps
+    import time
+    t0 = time.perf_counter()
+    tr = lrq.truncate(Q, 2, tol=1e-6, max_iter=4096, want_c128=False, device=DEV)
+    torch.cuda.synchronize()
+    print("torus truncation: %d Lanczos steps, %.1f s" % (tr["iters"], time.perf_counter() - t0))
+    assert abs(float(tr["lam"][0].item()) - 8.0) <= 1e-6 * 8
+    V = tr["V32"]
+    out = lrq.sample_score(V, 3, S=1 << 14, seed=5, mode=BF16, top_m=64)
+    res = lrq.rescore(V, 3, out["C"], out["top_idx"], want_z=True)
+    torch.cuda.synchronize()
+    lrq.check_status(out["dev_status"])
+    lrq.check_status(res["dev_status"])
+    best = int(torch.argmax(res["f"]).item())
+    z = res["z"][best].contiguous()
+    cut = torch.zeros(1, dtype=torch.int64, device=DEV)
+    lrq.lrq_cut_count(rp, ci, z, cut)
+    torch.cuda.synchronize()
+    assert int(cut.item()) == 2 * n
+    assert int(cut.item()) == O.cut_count(rowptr, colidx, z.cpu().numpy())
 
 
 @pytest.mark.slow
