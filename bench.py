@@ -411,13 +411,17 @@ def _line(metric, value, unit, args, ms, config, **extra):
     print(json.dumps(out), flush=True)
 
 
-def learned_gain(dev, n, ntrain, neval, steps):
-    """Median S_u / S_l of the learned proposal (trained here on the GPU)."""
+def learned_gain(dev, n, ntrain, neval, steps, hard=False):
+    """Median S_u / S_l and S_e1 / S_l of the learned proposal (trained here on
+    the GPU); hard=True draws sigma from the regime where the noise is
+    comparable to the planted signal."""
     import torch
 
     from paper_2602_20376_gb300 import proposal as P
+    sig = P.SIGMA_HARD if hard else P.SIGMA_EASY
+    base = 2 * 10 ** 6 if hard else 10 ** 6
     t0 = time.perf_counter()
-    V, lam = P.truncate_instances(n, range(10 ** 6, 10 ** 6 + ntrain + neval), device=dev)
+    V, lam = P.truncate_instances(n, range(base, base + ntrain + neval), device=dev, sigma_range=sig)
     Vg, feat = P.features(V, lam)
     targets = P.training_targets(Vg[:ntrain], P.K_ANGSYNC, 1 << 14, 555)
     model = P.Proposal(feat.shape[1], seed=0, device=dev)
@@ -428,15 +432,16 @@ def learned_gain(dev, n, ntrain, neval, steps):
     torch.cuda.synchronize()
     t2 = time.perf_counter()
     rows = P.evaluate(model, Vg[ntrain:], feat[ntrain:], P.K_ANGSYNC, 1 << 16, 777)
-    su = sorted(r[1] for r in rows)
-    sl = sorted(r[2] for r in rows)
+    med = lambda xs: sorted(xs)[len(xs) // 2]  # noqa: E731
     fin = lambda x: x if x != float("inf") else None  # noqa: E731
-    return {"median_ratio": P.median_gain(rows), "median_S_uniform": fin(su[len(su) // 2]),
-            "median_S_learned": fin(sl[len(sl) // 2]), "level": 0.999, "S_max": 1 << 16,
+    return {"median_ratio": P.median_gain(rows), "median_ratio_vs_e1": P.median_gain(rows, baseline=3),
+            "median_S_uniform": fin(med([r[1] for r in rows])), "median_S_learned": fin(med([r[2] for r in rows])),
+            "e1_reached": sum(1 for r in rows if r[3] != float("inf")),
+            "level": 0.999, "S_max": 1 << 16,
             "reached": sum(1 for r in rows if r[2] != float("inf")), "instances": len(rows),
-            "workload": "angular synchronisation Q = x x^H + sigma W, x on A_8^n, sigma ~ U[0.5, 2], n=%d, "
+            "workload": "angular synchronisation Q = x x^H + sigma W, x on A_8^n, sigma ~ U[%g, %g], n=%d, "
                         "rank-4 truncation, K=8; %d training instances (top 1%% of 2^14 uniform directions "
-                        "each), %d held-out" % (n, ntrain, neval),
+                        "each), %d held-out" % (sig[0], sig[1], n, ntrain, neval),
             "train_steps": steps, "loss_first10": float(losses[:10].mean()), "loss_last10": float(losses[-10:].mean()),
             "data_s": t1 - t0, "train_s": t2 - t1, "kernels": "BF16 MLP fwd/bwd, vMF NLL, Adam, vMF sampler"}
 
@@ -446,8 +451,10 @@ def run_learned(args):
     torch.cuda.set_device(0)
     from paper_2602_20376_gb300 import lrq
     lrq.load()
-    res = learned_gain(torch.device("cuda", 0), args.learned_n, max(args.learned_train, 512), args.learned_eval * 2,
-                       max(args.learned_steps, 800))
+    dev = torch.device("cuda", 0)
+    ntrain, neval, steps = max(args.learned_train, 512), max(args.learned_eval, 256), max(args.learned_steps, 800)
+    res = learned_gain(dev, args.learned_n, ntrain, neval, steps)
+    res["hard"] = learned_gain(dev, args.learned_n, ntrain, neval, steps, hard=True)
     _line("median S_u/S_l to 0.999*best (learned vs uniform proposals)", res["median_ratio"], "x", args, None,
           {"workload": res["workload"]}, dtype="bf16", samples_to_best=res)
 

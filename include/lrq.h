@@ -506,6 +506,20 @@ int lrq_enumerate(const void* V, int64_t n, int r, int K, double budget, uint8_t
  *   counter (s, b, draw, 0x564D46).  A rejection loop that failed 1000 times
  *   (never observed) reports LRQ_ETIMEOUT.
  * lrq_adam_step: Adam with bias correction for step t >= 1 on count floats.
+ * lrq_proposal_targets: training targets.  For each of the m indices idx[t]
+ *   (device int64, in [0, S); the scoring's top-m selection, e.g. the top 1%
+ *   of S uniform directions) the direction c = C[idx[t]] (C: S x r
+ *   complex64, device) is moved to the canonical window -- c omega^-k with
+ *   k = ceil(K arg(c_1) / (2 pi) - 1/2), so that arg c_1 lies in
+ *   (-pi/K, pi/K] (Sec. 2.3: c and omega^k c score the same) -- and written
+ *   as 2r floats (Re c_1, Im c_1, Re c_2, ...) to targets_out (m x 2r,
+ *   device).  FP64 inside.  An index outside [0, S) reports LRQ_EINVAL in
+ *   dev_status and writes zeros.
+ * lrq_standardize_fit: per feature f of feat (B x F floats, device) the mean
+ *   over the B rows and the sample standard deviation (ddof 1, at least
+ *   1e-6; 1 when B = 1), FP64 sums, to mean_out and std_out (F floats each).
+ * lrq_standardize: X_out[b][f] = (feat[b][f] - mean[f]) / std_dev[f] (B x F
+ *   floats, device): the network's input.
  * ------------------------------------------------------------------------ */
 int lrq_proposal_num_features(int r);
 int64_t lrq_proposal_num_params(int F);
@@ -520,6 +534,11 @@ int lrq_vmf_sample(const float* O, int B, int S, int K, uint64_t seed, void* C_o
                    void* stream);
 int lrq_adam_step(float* params, const float* grads, float* m, float* v, int64_t count, int t, float lr,
                   float beta1, float beta2, float eps, void* stream);
+int lrq_proposal_targets(const void* C, int64_t S, int r, int K, const int64_t* idx, int64_t m, float* targets_out,
+                         int32_t* dev_status, void* stream);
+int lrq_standardize_fit(const float* feat, int B, int F, float* mean_out, float* std_out, void* stream);
+int lrq_standardize(const float* feat, int B, int F, const float* mean, const float* std_dev, float* X_out,
+                    void* stream);
 
 /* --------------------------------------------------------------------------
  * lrq_cut_count -- exact Max-K-Cut value of an assignment on a graph.

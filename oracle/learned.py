@@ -37,6 +37,9 @@ Definitions implemented here, in plain FP64 numpy:
   law statistically.
 * canonical window: multiply c by omega^{-k} so that arg c_1 lies in
   (-pi/K, pi/K].
+* feature standardisation: centre each feature on its mean over the
+  training rows, divide by the sample standard deviation (ddof 1, at least
+  1e-6; 1 for a single row).
 * Adam (Kingma and Ba, 2015) with bias correction.
 
 Parity pins live in tests/test_oracle_learned.py.  Parity unpinned: the
@@ -267,6 +270,23 @@ def to_real8(C):
     out[:, 0::2] = C.real
     out[:, 1::2] = C.imag
     return out
+
+
+# --------------------------------------------------------------------------
+# feature standardisation
+# --------------------------------------------------------------------------
+def standardize_fit(feat):
+    """Per feature: mean over the rows and sample standard deviation (ddof 1,
+    at least 1e-6; 1 for a single row)."""
+    feat = np.asarray(feat, dtype=np.float64)
+    mean = feat.mean(axis=0)
+    if feat.shape[0] < 2:
+        return mean, np.ones(feat.shape[1])
+    return mean, np.maximum(feat.std(axis=0, ddof=1), 1e-6)
+
+
+def standardize(feat, mean, std):
+    return (np.asarray(feat, dtype=np.float64) - mean) / std
 
 
 # --------------------------------------------------------------------------

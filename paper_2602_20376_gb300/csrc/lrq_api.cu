@@ -416,6 +416,29 @@ int lrq_adam_step(float* params, const float* grads, float* m, float* v, int64_t
   return launch_adam(params, grads, m, v, count, t, lr, beta1, beta2, eps, static_cast<cudaStream_t>(stream));
 }
 
+int lrq_proposal_targets(const void* C, int64_t S, int r, int K, const int64_t* idx, int64_t m, float* targets_out,
+                         int32_t* dev_status, void* stream) {
+  if (S < 1 || m < 0 || r < 1 || r > kMaxRank) return fail(LRQ_EINVAL, "bad sizes");
+  if (K < 2 || K > kMaxK) return fail(LRQ_EINVAL, "K must be in [2, 64]");
+  if (m == 0) return LRQ_OK;
+  if (!C || !idx || !targets_out || !dev_status) return fail(LRQ_EINVAL, "NULL pointer argument");
+  return launch_proposal_targets(static_cast<const float2*>(C), S, idx, m, r, K, targets_out, dev_status,
+                                 static_cast<cudaStream_t>(stream));
+}
+
+int lrq_standardize_fit(const float* feat, int B, int F, float* mean_out, float* std_out, void* stream) {
+  if (B < 1 || F < 1) return fail(LRQ_EINVAL, "bad sizes");
+  if (!feat || !mean_out || !std_out) return fail(LRQ_EINVAL, "NULL pointer argument");
+  return launch_standardize_fit(feat, B, F, mean_out, std_out, static_cast<cudaStream_t>(stream));
+}
+
+int lrq_standardize(const float* feat, int B, int F, const float* mean, const float* std_dev, float* X_out,
+                    void* stream) {
+  if (B < 1 || F < 1) return fail(LRQ_EINVAL, "bad sizes");
+  if (!feat || !mean || !std_dev || !X_out) return fail(LRQ_EINVAL, "NULL pointer argument");
+  return launch_standardize(feat, B, F, mean, std_dev, X_out, static_cast<cudaStream_t>(stream));
+}
+
 int lrq_rank1_workspace_size(int64_t n, size_t* bytes) {
   if (!bytes) return fail(LRQ_EINVAL, "bytes is NULL");
   if (n < 1 || n >= (int64_t(1) << 31)) return fail(LRQ_EINVAL, "n must be in [1, 2^31)");

@@ -125,6 +125,11 @@ int launch_vmf_sample(const float* O, int B, int S, int K, uint64_t seed, float2
                       cudaStream_t st);
 int launch_adam(float* p, const float* g, float* m, float* v, int64_t count, int t, float lr, float b1, float b2,
                 float eps, cudaStream_t st);
+int launch_proposal_targets(const float2* C, int64_t S, const int64_t* idx, int64_t m, int r, int K, float* out,
+                            int32_t* status, cudaStream_t st);
+int launch_standardize_fit(const float* feat, int B, int F, float* mean, float* sd, cudaStream_t st);
+int launch_standardize(const float* feat, int B, int F, const float* mean, const float* sd, float* X,
+                       cudaStream_t st);
 // exact rank-1 sweep (FP64)
 size_t rank1_workspace_bytes(int64_t n);
 int launch_rank1(const double2* q, int64_t n, int K, uint8_t* z_out, double* f_out, const int32_t* rowptr,

@@ -139,6 +139,12 @@ def load() -> ctypes.CDLL:
         lib.lrq_vmf_sample.restype = I
         lib.lrq_adam_step.argtypes = [P, P, P, P, I64, I, F32, F32, F32, F32, P]
         lib.lrq_adam_step.restype = I
+        lib.lrq_proposal_targets.argtypes = [P, I64, I, I, P, I64, P, P, P]
+        lib.lrq_proposal_targets.restype = I
+        lib.lrq_standardize_fit.argtypes = [P, I, I, P, P, P]
+        lib.lrq_standardize_fit.restype = I
+        lib.lrq_standardize.argtypes = [P, I, I, P, P, P, P]
+        lib.lrq_standardize.restype = I
         lib.lrq_truncate_workspace_size.argtypes = [ctypes.POINTER(LrqMatrix), I, I, ctypes.POINTER(SZ)]
         lib.lrq_truncate_workspace_size.restype = I
         lib.lrq_truncate.argtypes = [ctypes.POINTER(LrqMatrix), I, ctypes.c_double, I, U64, P, P, P,
@@ -183,6 +189,7 @@ def exported_symbols():
             "lrq_sample_score_batched", "lrq_batched_graph_create", "lrq_graph_launch", "lrq_graph_destroy",
             "lrq_proposal_num_features", "lrq_proposal_num_params", "lrq_proposal_features", "lrq_mlp_forward",
             "lrq_mlp_backward", "lrq_vmf_nll", "lrq_vmf_sample", "lrq_adam_step",
+            "lrq_proposal_targets", "lrq_standardize_fit", "lrq_standardize",
             "lrq_cut_count", "lrq_set_timing_events", "lrq_kernel_launches"]
 
 
@@ -322,6 +329,27 @@ def lrq_vmf_sample(O, S, K, seed, C_out, dev_status, stream=None):
 def lrq_adam_step(params, grads, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
     _check(load().lrq_adam_step(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), params.numel(), int(t), float(lr),
                                 float(beta1), float(beta2), float(eps), _stream(stream)), "lrq_adam_step")
+
+
+def lrq_proposal_targets(C, K, idx, targets_out, dev_status, stream=None):
+    """C: S x r complex64; idx: m int64; targets_out: m x 2r float32 (device)."""
+    S, r = C.shape
+    m = idx.numel()
+    assert idx.dtype == torch.int64 and targets_out.dtype == torch.float32 and targets_out.numel() == m * 2 * r
+    _check(load().lrq_proposal_targets(_ptr(C), S, r, int(K), _ptr(idx), m, _ptr(targets_out), _ptr(dev_status),
+                                       _stream(stream)), "lrq_proposal_targets")
+
+
+def lrq_standardize_fit(feat, mean_out, std_out, stream=None):
+    B, F = feat.shape
+    _check(load().lrq_standardize_fit(_ptr(feat), B, F, _ptr(mean_out), _ptr(std_out), _stream(stream)),
+           "lrq_standardize_fit")
+
+
+def lrq_standardize(feat, mean, std, X_out, stream=None):
+    B, F = feat.shape
+    _check(load().lrq_standardize(_ptr(feat), B, F, _ptr(mean), _ptr(std), _ptr(X_out), _stream(stream)),
+           "lrq_standardize")
 
 
 def lrq_truncate_workspace_size(Q: LrqMatrix, r: int, max_iter: int = 0) -> int:

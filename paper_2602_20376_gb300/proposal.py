@@ -1,11 +1,12 @@
 """Learned proposal: training and evaluation driver over the C ABI.
 
-Every numerical step runs in liblrq's kernels (truncation, features, MLP
-forward/backward, vMF loss, vMF sampling, Adam, scoring); this module only
-orders the calls and keeps tensors.  PyTorch provides device memory, the
-synthetic instance generator (seeded torch generators on the device) and
-small glue (feature standardisation, top-1% selection, the canonical window,
-prefix maxima).
+Every numerical step of the method runs in liblrq's kernels (truncation,
+features, feature standardisation, MLP forward/backward, vMF loss, vMF
+sampling, Adam, scoring with its top-m selection, the canonical window of
+the targets); this module only orders the calls and keeps tensors.  PyTorch
+provides device memory, the synthetic instance generator (seeded torch
+generators on the device) and the evaluation's bookkeeping (prefix maxima of
+the score streams).
 
 Instances (angular synchronisation): Q = x x^H + sigma W with x_i uniform on
 A_8, sigma ~ U[0.5, 2], W Hermitian with CN(0, 1) entries above the diagonal
@@ -31,13 +32,18 @@ WIDTH = 256
 N_OUT = 160
 
 
-def make_instance(n: int, seed: int, device="cuda"):
+SIGMA_EASY = (0.5, 2.0)     # the angular-synchronisation workload: ||sigma W|| ~ 2 sigma sqrt(n) << n
+SIGMA_HARD = (12.0, 20.0)   # at n = 4096: ||sigma W|| ~ 2 sigma sqrt(n) ~ n / 2, comparable to lambda_1 = n
+
+
+def make_instance(n: int, seed: int, device="cuda", sigma_range=SIGMA_EASY):
     """Q (n x n complex128 on the device), the planted x and sigma."""
     g = torch.Generator(device=device)
     g.manual_seed(int(seed))
     k = torch.randint(0, K_ANGSYNC, (n,), generator=g, device=device)
     x = torch.polar(torch.ones(n, dtype=torch.float64, device=device), 2 * math.pi * k.double() / K_ANGSYNC)
-    sigma = 0.5 + 1.5 * torch.rand((), generator=g, device=device, dtype=torch.float64).item()
+    lo, hi = sigma_range
+    sigma = lo + (hi - lo) * torch.rand((), generator=g, device=device, dtype=torch.float64).item()
     G = torch.randn((n, n), generator=g, device=device, dtype=torch.complex128)  # CN(0, 1)
     W = torch.triu(G, 1)
     W = W + W.conj().T
@@ -46,11 +52,11 @@ def make_instance(n: int, seed: int, device="cuda"):
     return Q, k, sigma
 
 
-def truncate_instances(n: int, seeds, device="cuda"):
+def truncate_instances(n: int, seeds, device="cuda", sigma_range=SIGMA_EASY):
     """V (B x n x 4 complex64) and lambda (B x 4 float64) for each seed."""
     Vs, lams = [], []
     for s in seeds:
-        Q, _, _ = make_instance(n, s, device)
+        Q, _, _ = make_instance(n, s, device, sigma_range)
         out = lrq.truncate(lrq.dense_matrix(Q), R, tol=1e-8, seed=int(s), want_c128=False, want_c64=True,
                            device=device)
         Vs.append(out["V32"])
@@ -70,15 +76,6 @@ def features(V, lam):
     return Vg, feat
 
 
-def canonical(C, K: int):
-    """Rows c times omega^{-k} with arg c_1 in (-pi/K, pi/K]; returns B x 8 reals."""
-    ang = torch.angle(C[:, 0].to(torch.complex128))
-    k = torch.ceil(ang * K / (2 * math.pi) - 0.5)
-    rot = torch.polar(torch.ones_like(k), -2 * math.pi * k / K)
-    Cc = C.to(torch.complex128) * rot[:, None]
-    return torch.view_as_real(Cc).reshape(C.shape[0], -1).float()
-
-
 def uniform_scores(Vg, K: int, S: int, seed: int, want_C=False):
     """FP32 scores of S uniform directions (drawn on the device from seed)."""
     out = lrq.sample_score(Vg, K, C=None, S=S, seed=seed, mode=lrq.LRQ_MODE_FP32, top_m=1, want_scores=True)
@@ -93,13 +90,18 @@ def scores_of(Vg, K: int, C):
 
 
 def training_targets(Vg, K: int, S_train: int, seed: int, frac=0.01):
+    """Per instance the top frac of S_train uniform directions (the scoring's
+    top-m selection), in the canonical window (lrq_proposal_targets)."""
     T = max(1, int(round(frac * S_train)))
-    out = []
+    dev = Vg.device
+    out = torch.empty((Vg.shape[0], T, 2 * R), dtype=torch.float32, device=dev)
+    status = torch.zeros(1, dtype=torch.int32, device=dev)
     for b in range(Vg.shape[0]):
-        f, C = uniform_scores(Vg[b], K, S_train, seed + b, want_C=True)
-        top = torch.topk(f, T).indices
-        out.append(canonical(C[top], K))
-    return torch.stack(out)  # B x T x 8
+        sc = lrq.sample_score(Vg[b], K, C=None, S=S_train, seed=seed + b, mode=lrq.LRQ_MODE_FP32, top_m=T)
+        lrq.check_status(sc["dev_status"], "target scoring")
+        lrq.lrq_proposal_targets(sc["C"], K, sc["top_idx"], out[b], status)
+    lrq.check_status(status, "lrq_proposal_targets")
+    return out  # B x T x 8
 
 
 class Proposal:
@@ -127,11 +129,12 @@ class Proposal:
         self.std = torch.ones(F, device=device)
 
     def standardize(self, feat):
-        return ((feat - self.mean) / self.std).contiguous()
+        X = torch.empty_like(feat)
+        lrq.lrq_standardize(feat.contiguous(), self.mean, self.std, X)
+        return X
 
     def fit_standardizer(self, feat):
-        self.mean = feat.mean(dim=0)
-        self.std = feat.std(dim=0).clamp_min(1e-6)
+        lrq.lrq_standardize_fit(feat.contiguous(), self.mean, self.std)
 
     def forward(self, X):
         B = X.shape[0]
@@ -182,18 +185,26 @@ def prefix_to_reach(scores, target):
 
 
 def evaluate(model: Proposal, Vg, feat, K: int, S_max: int, seed: int, level=0.999):
-    """Per instance (U*, S_u, S_l); the learned stream has the same length S_max."""
+    """Per instance (U*, S_u, S_l, S_e1); the learned stream has the same
+    length S_max.  S_e1 is the fixed-direction baseline: the single direction
+    e_1 in the gauge of lrq_proposal_features (1 if it reaches level U*, else
+    inf), which shows what the network adds over a constant guess."""
     X = model.standardize(feat)
     C = model.sample(X, S_max, K, seed)
+    e1 = torch.zeros((1, R), dtype=torch.complex64, device=Vg.device)
+    e1[0, 0] = 1.0
     rows = []
     for b in range(Vg.shape[0]):
         fu = uniform_scores(Vg[b], K, S_max, seed + 7919 * (b + 1))
         ustar = float(fu.max().item())
         fl = scores_of(Vg[b], K, C[b].contiguous())
-        rows.append((ustar, prefix_to_reach(fu, level * ustar), prefix_to_reach(fl, level * ustar)))
+        fe = float(scores_of(Vg[b], K, e1).max().item())
+        rows.append((ustar, prefix_to_reach(fu, level * ustar), prefix_to_reach(fl, level * ustar),
+                     1.0 if fe >= level * ustar else math.inf))
     return rows
 
 
-def median_gain(rows):
-    ratios = sorted(su / sl for _, su, sl in rows)
+def median_gain(rows, baseline=1):
+    """Median of S_baseline / S_l (baseline 1: uniform sampling; 3: e_1)."""
+    ratios = sorted(r[baseline] / r[2] for r in rows)
     return ratios[len(ratios) // 2]

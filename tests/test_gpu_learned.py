@@ -220,6 +220,49 @@ def test_adam_step_matches_oracle(lrq):
     assert np.abs(Vv.cpu().numpy() - v_ref).max() <= 1e-6
 
 
+@pytest.mark.parametrize("K,r", [(8, 4), (3, 2), (5, 7)])
+def test_proposal_targets_match_oracle(lrq, K, r):
+    # gathered directions in the canonical window (Sec. 2.3), against the
+    # oracle's canonicalize of the same rows; an index outside [0, S) is
+    # reported and yields zeros
+    S, m = 3000, 257
+    C = I.directions(S, r, seed=70 + K)
+    idx = I.rng(71).choice(S, m, replace=False).astype(np.int64)
+    out = torch.empty((m, 2 * r), dtype=torch.float32, device=DEV)
+    status = torch.zeros(1, dtype=torch.int32, device=DEV)
+    lrq.lrq_proposal_targets(_t(C), K, _t(idx), out, status)
+    torch.cuda.synchronize()
+    lrq.check_status(status, "lrq_proposal_targets")
+    ref = OL.to_real8(OL.canonicalize(C[idx].astype(np.complex128), K))
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-6
+    bad = idx.copy()
+    bad[5] = S
+    lrq.lrq_proposal_targets(_t(C), K, _t(bad), out, status)
+    torch.cuda.synchronize()
+    assert int(status.item()) == lrq.LRQ_EINVAL
+    assert np.all(out.cpu().numpy()[5] == 0)
+
+
+@pytest.mark.parametrize("B", [1, 2, 97])
+def test_standardize_matches_oracle(lrq, B):
+    g = I.rng(72 + B)
+    feat = (g.standard_normal((B, 24)) * np.linspace(0.1, 30.0, 24) + 7.0).astype(np.float32)
+    feat[:, 3] = 1.5  # constant feature: its standard deviation is clamped
+    F = _t(feat)
+    mean = torch.empty(24, device=DEV)
+    std = torch.empty(24, device=DEV)
+    X = torch.empty_like(F)
+    lrq.lrq_standardize_fit(F, mean, std)
+    lrq.lrq_standardize(F, mean, std, X)
+    torch.cuda.synchronize()
+    m_ref, s_ref = OL.standardize_fit(feat.astype(np.float64))
+    assert np.allclose(mean.cpu().numpy(), m_ref, rtol=1e-6, atol=1e-6)
+    assert np.allclose(std.cpu().numpy(), s_ref, rtol=1e-6, atol=1e-9)
+    ref = OL.standardize(feat.astype(np.float64), mean.cpu().numpy().astype(np.float64),
+                         std.cpu().numpy().astype(np.float64))
+    assert np.abs(X.cpu().numpy() - ref).max() <= 1e-4 * max(1.0, np.abs(ref).max())
+
+
 @pytest.mark.slow
 def test_trained_proposal_beats_uniform_sampling(lrq):
     # angular synchronisation at n = 1024 (K = 8, rank-4 truncation): train on

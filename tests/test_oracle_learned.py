@@ -195,3 +195,18 @@ def test_adam_constant_gradient_closed_form():
         assert np.allclose(m, (1 - b1 ** t) * gr, rtol=1e-12, atol=1e-15)
         assert np.allclose(v, (1 - b2 ** t) * gr * gr, rtol=1e-12, atol=1e-15)
         assert np.allclose(p, p0 - t * lr * gr / (np.abs(gr) + eps), rtol=1e-12, atol=1e-14)
+
+
+def test_standardize_invariants():
+    g = I.rng(12)
+    feat = g.standard_normal((50, 6)) * np.array([1.0, 10.0, 0.1, 3.0, 1.0, 1.0]) + 5.0
+    feat[:, 4] = 2.5  # a constant feature
+    mean, std = L.standardize_fit(feat)
+    X = L.standardize(feat, mean, std)
+    keep = [0, 1, 2, 3, 5]
+    assert np.allclose(X[:, keep].mean(axis=0), 0.0, atol=1e-12)
+    assert np.allclose(X[:, keep].std(axis=0, ddof=1), 1.0, atol=1e-12)
+    assert std[4] == 1e-6 and np.all(X[:, 4] == 0.0)
+    # a single row: centred to zero, unscaled
+    m1, s1 = L.standardize_fit(feat[:1])
+    assert np.all(s1 == 1.0) and np.all(L.standardize(feat[:1], m1, s1) == 0.0)
