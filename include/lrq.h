@@ -181,6 +181,44 @@ int lrq_sample_score(const void* V, int64_t n, int r, int K, void* C, int genera
                      float* top_f_out, void* ws, size_t ws_bytes, int32_t* dev_status, void* stream);
 
 /* --------------------------------------------------------------------------
+ * Prepared instance -- lrq_sample_score split in two, for many calls on one V.
+ *
+ * Of the work in lrq_sample_score, the finiteness check of V and (tensor-core
+ * mode) the column sums of conj(V) and the packed coordinate operands depend
+ * on V only.  lrq_prepare does that part once into a caller-owned device
+ * buffer; every lrq_sample_score_prepared call then draws or reads its
+ * directions, packs them, scores and selects exactly as lrq_sample_score
+ * does (same top_idx_out, top_f_out and scores_out for the same V, C, K,
+ * mode, top_m).
+ *
+ *   lrq_prepared_create(n, r, K, mode, &h)  validates as lrq_sample_score
+ *       does (n, r, K, mode); host only, allocates the host object *h.
+ *   lrq_prepared_size(h, &bytes)  device bytes of the prepared buffer (0 in
+ *       FP32 mode, which reads V itself).
+ *   lrq_prepare(h, V, buf, buf_bytes, dev_status, stream)  asynchronous;
+ *       buf: at least that many bytes, 256-byte aligned (or NULL when 0);
+ *       a non-finite V sets *dev_status = LRQ_EINVAL.  h remembers V and buf:
+ *       both must stay allocated and unchanged while h is used (a changed V
+ *       needs a new lrq_prepare).  Calls on other streams must be ordered
+ *       after this one by the caller.
+ *   lrq_sample_score_prepared_workspace_size(h, S, top_m, &bytes)
+ *   lrq_sample_score_prepared(h, C, generate_C, seed, S, top_m, scores_out,
+ *       top_idx_out, top_f_out, ws, ws_bytes, dev_status, stream)
+ *       arguments as in lrq_sample_score; LRQ_EINVAL before lrq_prepare.
+ *       Calls on one h may run concurrently with separate workspaces.
+ *   lrq_prepared_destroy(h)  frees the host object (not buf, not V).
+ * ------------------------------------------------------------------------ */
+typedef struct lrq_prepared_v lrq_prepared_v;
+int lrq_prepared_create(int64_t n, int r, int K, int mode, lrq_prepared_v** out);
+void lrq_prepared_destroy(lrq_prepared_v* h);
+int lrq_prepared_size(const lrq_prepared_v* h, size_t* bytes /* host */);
+int lrq_prepare(lrq_prepared_v* h, const void* V, void* buf, size_t buf_bytes, int32_t* dev_status, void* stream);
+int lrq_sample_score_prepared_workspace_size(const lrq_prepared_v* h, int64_t S, int top_m, size_t* bytes /* host */);
+int lrq_sample_score_prepared(const lrq_prepared_v* h, void* C, int generate_C, uint64_t seed, int64_t S, int top_m,
+                              float* scores_out, int64_t* top_idx_out, float* top_f_out, void* ws, size_t ws_bytes,
+                              int32_t* dev_status, void* stream);
+
+/* --------------------------------------------------------------------------
  * lrq_rescore -- FP64 re-scoring of selected candidates.
  *
  * For each of the m candidates idx[t] (rows of C), recompute w = V c, the
@@ -505,6 +543,12 @@ int lrq_enumerate(const void* V, int64_t n, int r, int K, double budget, uint8_t
  *   in [0, K); C_out: B x S x 4 complex64.  Philox4x32-10 keyed by seed with
  *   counter (s, b, draw, 0x564D46).  A rejection loop that failed 1000 times
  *   (never observed) reports LRQ_ETIMEOUT.
+ * lrq_vmf_modes: the 16 component means mu_m of the mixture of O (u / ||u||;
+ *   e_1 when u = 0) as directions of C^4, ordered by mixture weight (largest
+ *   logit first, lower component index on ties): C_out B x 16 x 4 complex64
+ *   (device).  These are the proposal's most probable directions; a stream
+ *   that starts with them and continues with lrq_vmf_sample draws is the
+ *   learned stream of the evaluation.  B in [1, 65535].
  * lrq_adam_step: Adam with bias correction for step t >= 1 on count floats.
  * lrq_proposal_targets: training targets.  For each of the m indices idx[t]
  *   (device int64, in [0, S); the scoring's top-m selection, e.g. the top 1%
@@ -532,6 +576,7 @@ int lrq_mlp_backward(const float* params, int F, int B, const float* X, const fl
 int lrq_vmf_nll(const float* O, int B, const float* targets, int T, double* loss_out, float* dO, void* stream);
 int lrq_vmf_sample(const float* O, int B, int S, int K, uint64_t seed, void* C_out, int32_t* dev_status,
                    void* stream);
+int lrq_vmf_modes(const float* O, int B, void* C_out, void* stream);
 int lrq_adam_step(float* params, const float* grads, float* m, float* v, int64_t count, int t, float lr,
                   float beta1, float beta2, float eps, void* stream);
 int lrq_proposal_targets(const void* C, int64_t S, int r, int K, const int64_t* idx, int64_t m, float* targets_out,

@@ -32,6 +32,8 @@ Definitions implemented here, in plain FP64 numpy:
   prod_{i<=j} (4 nu^2 - (2i-1)^2) / (j! (8 kappa)^j) above.
 * loss: mean over targets x of -log sum_m pi_m C_8(kappa_m) exp(kappa_m
   mu_m . x), and its gradient with respect to the network outputs.
+* modes: the component means ordered by mixture weight (largest logit
+  first, lower index on ties), the proposal's most probable directions.
 * Wood's rejection sampler for vMF (A. T. A. Wood, Simulation of the von
   Mises Fisher distribution, 1994), used here only to check the sampler's
   law statistically.
@@ -253,6 +255,23 @@ def wood_sample(mu, kappa, N, rng):
         v -= (v @ mu) * mu
         v /= np.linalg.norm(v)
         out[s] = w * mu + math.sqrt(max(0.0, 1.0 - w * w)) * v
+    return out
+
+
+def vmf_modes(O):
+    """Per instance the component means mu_m = u_m / ||u_m|| (e_1 when u_m = 0)
+    as complex 4-vectors (c_j = mu[2j] + i mu[2j+1]), ordered by mixture
+    weight: largest logit first, lower component index on ties.  B x 16 x 4."""
+    O = np.asarray(O, dtype=np.float64).reshape(-1, N_COMP, HEAD)
+    B = O.shape[0]
+    out = np.empty((B, N_COMP, P_DIM // 2), dtype=np.complex128)
+    for b in range(B):
+        order = sorted(range(N_COMP), key=lambda m: (-O[b, m, P_DIM + 1], m))
+        for rank, m in enumerate(order):
+            u = O[b, m, :P_DIM]
+            nrm = math.sqrt(float(np.dot(u, u)))
+            mu = u / nrm if nrm > 0 else np.eye(P_DIM)[0]
+            out[b, rank] = mu[0::2] + 1j * mu[1::2]
     return out
 
 

@@ -427,6 +427,32 @@ __global__ void __launch_bounds__(128) vmf_sample_kernel(const float* __restrict
   }
 }
 
+// The mixture's component means, ordered by weight (largest logit first,
+// lower component index on ties): the most probable directions of the
+// proposal, as directions of C^4.  A component with u = 0 gives e_1, the
+// same convention as the sampler.  One warp per instance.
+__global__ void vmf_modes_kernel(const float* __restrict__ O, int B, float2* __restrict__ C) {
+  const int b = blockIdx.x;
+  const int m = threadIdx.x;
+  if (b >= B || m >= kComp) return;
+  const float* Ob = O + static_cast<int64_t>(b) * kOut;
+  const float lm = Ob[m * kHead + kDim + 1];
+  int rank = 0;
+  for (int k = 0; k < kComp; ++k) {
+    const float lk = Ob[k * kHead + kDim + 1];
+    rank += (lk > lm || (lk == lm && k < m)) ? 1 : 0;
+  }
+  double nrm = 0.0;
+  for (int d = 0; d < kDim; ++d) nrm += static_cast<double>(Ob[m * kHead + d]) * Ob[m * kHead + d];
+  nrm = sqrt(nrm);
+  float2* out = C + (static_cast<int64_t>(b) * kComp + rank) * (kDim / 2);
+  for (int j = 0; j < kDim / 2; ++j) {
+    const double re = nrm > 0.0 ? Ob[m * kHead + 2 * j] / nrm : (j == 0 ? 1.0 : 0.0);
+    const double im = nrm > 0.0 ? Ob[m * kHead + 2 * j + 1] / nrm : 0.0;
+    out[j] = make_float2(static_cast<float>(re), static_cast<float>(im));
+  }
+}
+
 // ---------------------------------------------------------------------------
 // Adam (Kingma and Ba) with bias correction
 // ---------------------------------------------------------------------------
@@ -520,6 +546,12 @@ int launch_vmf_sample(const float* O, int B, int S, int K, uint64_t seed, float2
   vmf_sample_kernel<<<grid, 128, 0, st>>>(O, B, S, K, seed, C, status);
   count_launch();
   return cuda_check(cudaGetLastError(), "vmf_sample_kernel");
+}
+
+int launch_vmf_modes(const float* O, int B, float2* C, cudaStream_t st) {
+  vmf_modes_kernel<<<B, 32, 0, st>>>(O, B, C);
+  count_launch();
+  return cuda_check(cudaGetLastError(), "vmf_modes_kernel");
 }
 
 int launch_adam(float* p, const float* g, float* m, float* v, int64_t count, int t, float lr, float b1, float b2,

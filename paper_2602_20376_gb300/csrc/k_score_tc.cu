@@ -907,9 +907,11 @@ static PackTables make_pack_tables(const Alphabet& a) {
   return tb;
 }
 
+// The instance's operands (depend on V only): augmented rows, the GEMM2
+// scale, the per-coordinate indicator magnitudes and the class rows.
 template <int K, int KCH>
-static int pack_impl(const ScorePlan& p, const Alphabet& a, const float2* V, const float2* C, void* tiles,
-                     void* ct, float* scale, uint32_t* iw, cudaStream_t st) {
+static int pack_v_impl(const ScorePlan& p, const Alphabet& a, const float2* V, void* tiles, float* scale,
+                       uint32_t* iw, cudaStream_t st) {
   using Sh = TcShape<K, KCH>;
   using L = TcLayout<K, KCH>;
   PackTables tb = make_pack_tables(a);
@@ -932,11 +934,17 @@ static int pack_impl(const ScorePlan& p, const Alphabet& a, const float2* V, con
   pack_b2_kernel<K, KCH><<<static_cast<unsigned>(ceil_div(nb, 256)), 256, 0, st>>>(
       V, p.n, p.r, p.n_tiles, tb, scale, reinterpret_cast<const uint8_t*>(iw), static_cast<uint8_t*>(tiles));
   count_launch(2);
+  return cuda_check(cudaGetLastError(), "tc operand packing");
+}
+
+// The directions (depend on C only).
+template <int KCH>
+static int pack_dirs_impl(const ScorePlan& p, const float2* C, void* ct, cudaStream_t st) {
   int64_t nc = p.c_tiles * kTcM;
   pack_dirs_kernel<KCH><<<static_cast<unsigned>(ceil_div(nc, 256)), 256, 0, st>>>(C, p.S, p.r, p.c_tiles,
                                                                                   static_cast<__half*>(ct));
   count_launch();
-  return cuda_check(cudaGetLastError(), "tc pack kernels");
+  return cuda_check(cudaGetLastError(), "pack_dirs_kernel");
 }
 
 // ---------------------------------------------------------------------------
@@ -1067,9 +1075,13 @@ size_t tc_bytes_dirs(int r, int64_t c_tiles) {
     }                                                                   \
   } while (0)
 
-int launch_tc_pack(const ScorePlan& p, const Alphabet& a, const float2* V, const float2* C, void* tiles, void* ct,
-                   void* scale, void* iw, cudaStream_t st) {
-  LRQ_TC_DISPATCH(pack_impl, p, a, V, C, tiles, ct, static_cast<float*>(scale), static_cast<uint32_t*>(iw), st);
+int launch_tc_pack_v(const ScorePlan& p, const Alphabet& a, const float2* V, void* tiles, void* scale, void* iw,
+                     cudaStream_t st) {
+  LRQ_TC_DISPATCH(pack_v_impl, p, a, V, tiles, static_cast<float*>(scale), static_cast<uint32_t*>(iw), st);
+}
+
+int launch_tc_pack_dirs(const ScorePlan& p, const float2* C, void* ct, cudaStream_t st) {
+  return p.r > 4 ? pack_dirs_impl<2>(p, C, ct, st) : pack_dirs_impl<1>(p, C, ct, st);
 }
 
 int launch_score_tc(const ScorePlan& p, const Alphabet& a, const void* tiles, const void* ct, const void* scale,

@@ -11,6 +11,7 @@
 #include <cstdio>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <string>
 
 #include "lrq_internal.h"
@@ -109,7 +110,7 @@ static size_t take(size_t& cursor, size_t bytes) {
   return off;
 }
 
-int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_sms, ScorePlan* p) {
+int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_sms, ScorePlan* p, bool with_prep) {
   std::memset(p, 0, sizeof(*p));
   p->n = n;
   p->S = S;
@@ -159,25 +160,45 @@ int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_
   size_t cur = 0;
   p->sz_partial = static_cast<size_t>(p->npart) * S_pad * 2 * r * sizeof(double);
   p->off_partial = take(cur, p->sz_partial);
-  p->sz_T = 2 * kMaxRank * sizeof(double);
-  p->off_T = take(cur, p->sz_T);
-  p->sz_Tpart = 256 * 2 * kMaxRank * sizeof(double);
-  p->off_Tpart = take(cur, p->sz_Tpart);
+  if (with_prep) {
+    p->sz_T = 2 * kMaxRank * sizeof(double);
+    p->off_T = take(cur, p->sz_T);
+    p->sz_Tpart = 256 * 2 * kMaxRank * sizeof(double);
+    p->off_Tpart = take(cur, p->sz_Tpart);
+  }
   if (mode == LRQ_MODE_BF16_TC) {
-    p->sz_tiles = tc_bytes_tiles(K, r, p->n_tiles);
-    p->off_tiles = take(cur, p->sz_tiles);
+    if (with_prep) {
+      p->sz_tiles = tc_bytes_tiles(K, r, p->n_tiles);
+      p->off_tiles = take(cur, p->sz_tiles);
+    }
     p->sz_ct = tc_bytes_dirs(r, p->c_tiles);
     p->off_ct = take(cur, p->sz_ct);
-    p->sz_scale = 4 * sizeof(float);
-    p->off_scale = take(cur, p->sz_scale);
-    p->sz_iw = tc_bytes_indicator_scale(K, p->n_tiles);
-    p->off_iw = take(cur, p->sz_iw);
+    if (with_prep) {
+      p->sz_scale = 4 * sizeof(float);
+      p->off_scale = take(cur, p->sz_scale);
+      p->sz_iw = tc_bytes_indicator_scale(K, p->n_tiles);
+      p->off_iw = take(cur, p->sz_iw);
+    }
   }
   p->sz_scores = static_cast<size_t>(S) * sizeof(float);
   p->off_scores = take(cur, p->sz_scores);
   p->sz_keys = (static_cast<size_t>(S) + topm_scratch_keys(S, top_m)) * sizeof(uint64_t);
   p->off_keys = take(cur, p->sz_keys);
   p->total = cur;
+  return LRQ_OK;
+}
+
+int plan_prepare(int64_t n, int r, int K, int mode, PrepLayout* L) {
+  std::memset(L, 0, sizeof(*L));
+  if (mode != LRQ_MODE_BF16_TC) return LRQ_OK;  // the FP32 path reads V itself
+  L->n_tiles = ceil_div(n, tc_rows_per_tile(K));
+  size_t cur = 0;
+  L->off_T = take(cur, 2 * kMaxRank * sizeof(double));
+  L->off_Tpart = take(cur, 256 * 2 * kMaxRank * sizeof(double));
+  L->off_tiles = take(cur, tc_bytes_tiles(K, r, L->n_tiles));
+  L->off_scale = take(cur, 4 * sizeof(float));
+  L->off_iw = take(cur, tc_bytes_indicator_scale(K, L->n_tiles));
+  L->total = cur;
   return LRQ_OK;
 }
 
@@ -226,7 +247,67 @@ static int check_score_args(int64_t n, int r, int K, int64_t S, int mode, int to
   return LRQ_OK;
 }
 
+// What scoring needs of one instance V, independent of the directions.
+struct InstanceOperands {
+  const float2* V;
+  uint8_t* tiles;   // packed coordinate tiles (tensor-core mode)
+  float* scale;     // GEMM2 operand scale
+  uint8_t* iw;      // indicator magnitudes
+  double* T;        // column sums of conj(V) (odd K, tensor-core mode)
+  double* Tpart;    // their per-block partials
+};
+
+static int prepare_operands(const ScorePlan& p, const Alphabet& a, const InstanceOperands& io, int32_t* dev_status,
+                            cudaStream_t st) {
+  int e;
+  if ((e = launch_check_finite(reinterpret_cast<const float*>(io.V), 2 * p.n * p.r, dev_status, st))) return e;
+  if (p.mode != LRQ_MODE_BF16_TC) return LRQ_OK;
+  if (p.K % 2 == 1) {
+    int nb = static_cast<int>(std::min<int64_t>(256, std::max<int64_t>(1, ceil_div(p.n, 4096))));
+    if ((e = launch_colsum(io.V, p.n, p.r, io.Tpart, io.T, nb, st))) return e;
+  }
+  return launch_tc_pack_v(p, a, io.V, io.tiles, io.scale, io.iw, st);
+}
+
+// Directions -> scores -> top-m, on prepared operands; w is the per-call
+// workspace laid out by p.
+static int score_directions(const ScorePlan& p, const Alphabet& a, const InstanceOperands& io, float2* Cf,
+                            bool generate, uint64_t seed, uint8_t* w, float* scores_out, int64_t* top_idx_out,
+                            float* top_f_out, int32_t* dev_status, cudaStream_t st) {
+  int e;
+  double* partial = reinterpret_cast<double*>(w + p.off_partial);
+  float* scores = scores_out ? scores_out : reinterpret_cast<float*>(w + p.off_scores);
+  uint64_t* keys = reinterpret_cast<uint64_t*>(w + p.off_keys);
+  uint64_t* keys_scratch = keys + p.S;
+  if (generate && (e = launch_sample_directions(seed, p.S, p.r, Cf, st))) return e;
+  if ((e = launch_check_finite(reinterpret_cast<const float*>(Cf), 2 * p.S * p.r, dev_status, st))) return e;
+  const double* Tuse = nullptr;
+  if (p.mode == LRQ_MODE_BF16_TC) {
+    if (p.K % 2 == 1) Tuse = io.T;
+    if ((e = launch_tc_pack_dirs(p, Cf, w + p.off_ct, st))) return e;
+    timing_start(st);
+    if ((e = launch_score_tc(p, a, io.tiles, w + p.off_ct, io.scale, io.iw, partial, dev_status, st))) return e;
+    timing_stop(st);
+  } else {
+    timing_start(st);
+    if ((e = launch_score_fp32(p, a, io.V, Cf, partial, st))) return e;
+    timing_stop(st);
+  }
+  if ((e = launch_finalize(p, a, partial, Tuse, scores, keys, st))) return e;
+  return launch_topm(keys, p.S, p.top_m, keys_scratch, top_idx_out, top_f_out, st);
+}
+
 }  // namespace lrq
+
+// A prepared instance (host object; its device buffer is the caller's).
+struct lrq_prepared_v {
+  int64_t n;
+  int r, K, mode;
+  lrq::PrepLayout L;
+  const float2* V;
+  uint8_t* buf;
+  bool ready;
+};
 
 using namespace lrq;
 
@@ -277,39 +358,86 @@ int lrq_sample_score(const void* V, int64_t n, int r, int K, void* C, int genera
   if ((e = check_ws(ws, ws_bytes, p.total))) return e;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   uint8_t* w = static_cast<uint8_t*>(ws);
-  const float2* Vf = static_cast<const float2*>(V);
-  float2* Cf = static_cast<float2*>(C);
-  double* partial = reinterpret_cast<double*>(w + p.off_partial);
-  double* T = reinterpret_cast<double*>(w + p.off_T);
-  float* scores = scores_out ? scores_out : reinterpret_cast<float*>(w + p.off_scores);
-  uint64_t* keys = reinterpret_cast<uint64_t*>(w + p.off_keys);
-  uint64_t* keys_scratch = keys + S;
-  Alphabet a = make_alphabet(K);
+  InstanceOperands io{static_cast<const float2*>(V), w + p.off_tiles, reinterpret_cast<float*>(w + p.off_scale),
+                      w + p.off_iw, reinterpret_cast<double*>(w + p.off_T), reinterpret_cast<double*>(w + p.off_Tpart)};
+  const Alphabet a = make_alphabet(K);
+  if ((e = prepare_operands(p, a, io, dev_status, st))) return e;
+  return score_directions(p, a, io, static_cast<float2*>(C), generate_C != 0, seed, w, scores_out, top_idx_out,
+                          top_f_out, dev_status, st);
+}
 
-  if (generate_C && (e = launch_sample_directions(seed, S, r, Cf, st))) return e;
-  if ((e = launch_check_finite(reinterpret_cast<const float*>(V), 2 * n * r, dev_status, st))) return e;
-  if ((e = launch_check_finite(reinterpret_cast<const float*>(C), 2 * S * r, dev_status, st))) return e;
-  const double* Tuse = nullptr;
-  if (mode == LRQ_MODE_BF16_TC) {
-    if (K % 2 == 1) {
-      int nb = static_cast<int>(std::min<int64_t>(256, std::max<int64_t>(1, ceil_div(n, 4096))));
-      if ((e = launch_colsum(Vf, n, r, reinterpret_cast<double*>(w + p.off_Tpart), T, nb, st))) return e;
-      Tuse = T;
-    }
-    if ((e = launch_tc_pack(p, a, Vf, Cf, w + p.off_tiles, w + p.off_ct, w + p.off_scale, w + p.off_iw, st)))
-      return e;
-    timing_start(st);
-    if ((e = launch_score_tc(p, a, w + p.off_tiles, w + p.off_ct, w + p.off_scale, w + p.off_iw, partial, dev_status,
-                             st)))
-      return e;
-    timing_stop(st);
-  } else {
-    timing_start(st);
-    if ((e = launch_score_fp32(p, a, Vf, Cf, partial, st))) return e;
-    timing_stop(st);
-  }
-  if ((e = launch_finalize(p, a, partial, Tuse, scores, keys, st))) return e;
-  return launch_topm(keys, S, top_m, keys_scratch, top_idx_out, top_f_out, st);
+int lrq_prepared_create(int64_t n, int r, int K, int mode, lrq_prepared_v** out) {
+  if (!out) return fail(LRQ_EINVAL, "out is NULL");
+  *out = nullptr;
+  int e = check_score_args(n, r, K, 1, mode, 1);
+  if (e) return e;
+  lrq_prepared_v* h = new (std::nothrow) lrq_prepared_v();
+  if (!h) return fail(LRQ_EINVAL, "host allocation failed");
+  h->n = n;
+  h->r = r;
+  h->K = K;
+  h->mode = mode;
+  plan_prepare(n, r, K, mode, &h->L);
+  h->V = nullptr;
+  h->buf = nullptr;
+  h->ready = false;
+  *out = h;
+  return LRQ_OK;
+}
+
+void lrq_prepared_destroy(lrq_prepared_v* h) { delete h; }
+
+int lrq_prepared_size(const lrq_prepared_v* h, size_t* bytes) {
+  if (!h || !bytes) return fail(LRQ_EINVAL, "NULL argument");
+  *bytes = h->L.total;
+  return LRQ_OK;
+}
+
+int lrq_prepare(lrq_prepared_v* h, const void* V, void* buf, size_t buf_bytes, int32_t* dev_status, void* stream) {
+  if (!h || !V || !dev_status) return fail(LRQ_EINVAL, "NULL pointer argument");
+  int e = check_ws(buf, buf_bytes, h->L.total);
+  if (e) return e;
+  h->ready = false;
+  ScorePlan p;
+  plan_score(h->n, h->r, h->K, 1, h->mode, 1, num_sms_current(), &p, false);
+  uint8_t* b = static_cast<uint8_t*>(buf);
+  InstanceOperands io{static_cast<const float2*>(V), b + h->L.off_tiles, reinterpret_cast<float*>(b + h->L.off_scale),
+                      b + h->L.off_iw, reinterpret_cast<double*>(b + h->L.off_T),
+                      reinterpret_cast<double*>(b + h->L.off_Tpart)};
+  if ((e = prepare_operands(p, make_alphabet(h->K), io, dev_status, static_cast<cudaStream_t>(stream)))) return e;
+  h->V = static_cast<const float2*>(V);
+  h->buf = b;
+  h->ready = true;
+  return LRQ_OK;
+}
+
+int lrq_sample_score_prepared_workspace_size(const lrq_prepared_v* h, int64_t S, int top_m, size_t* bytes) {
+  if (!h || !bytes) return fail(LRQ_EINVAL, "NULL argument");
+  int e = check_score_args(h->n, h->r, h->K, S, h->mode, top_m);
+  if (e) return e;
+  ScorePlan p;
+  plan_score(h->n, h->r, h->K, S, h->mode, top_m, num_sms_current(), &p, false);
+  *bytes = p.total;
+  return LRQ_OK;
+}
+
+int lrq_sample_score_prepared(const lrq_prepared_v* h, void* C, int generate_C, uint64_t seed, int64_t S, int top_m,
+                              float* scores_out, int64_t* top_idx_out, float* top_f_out, void* ws, size_t ws_bytes,
+                              int32_t* dev_status, void* stream) {
+  if (!h) return fail(LRQ_EINVAL, "handle is NULL");
+  if (!h->ready) return fail(LRQ_EINVAL, "instance not prepared (call lrq_prepare first)");
+  int e = check_score_args(h->n, h->r, h->K, S, h->mode, top_m);
+  if (e) return e;
+  if (!C || !top_idx_out || !top_f_out || !dev_status) return fail(LRQ_EINVAL, "NULL pointer argument");
+  ScorePlan p;
+  plan_score(h->n, h->r, h->K, S, h->mode, top_m, num_sms_current(), &p, false);
+  if ((e = check_ws(ws, ws_bytes, p.total))) return e;
+  uint8_t* b = h->buf;
+  InstanceOperands io{h->V, b + h->L.off_tiles, reinterpret_cast<float*>(b + h->L.off_scale), b + h->L.off_iw,
+                      reinterpret_cast<double*>(b + h->L.off_T), reinterpret_cast<double*>(b + h->L.off_Tpart)};
+  return score_directions(p, make_alphabet(h->K), io, static_cast<float2*>(C), generate_C != 0, seed,
+                          static_cast<uint8_t*>(ws), scores_out, top_idx_out, top_f_out, dev_status,
+                          static_cast<cudaStream_t>(stream));
 }
 
 int lrq_rescore_workspace_size(int64_t n, int r, int m, size_t* bytes) {
@@ -406,6 +534,13 @@ int lrq_vmf_sample(const float* O, int B, int S, int K, uint64_t seed, void* C_o
   if (!O || !C_out || !dev_status) return fail(LRQ_EINVAL, "NULL pointer argument");
   return launch_vmf_sample(O, B, S, K, seed, static_cast<float2*>(C_out), dev_status,
                            static_cast<cudaStream_t>(stream));
+}
+
+int lrq_vmf_modes(const float* O, int B, void* C_out, void* stream) {
+  if (B < 1) return fail(LRQ_EINVAL, "B must be >= 1");
+  if (B > 65535) return fail(LRQ_EUNSUPPORTED, "B above 65535");
+  if (!O || !C_out) return fail(LRQ_EINVAL, "NULL pointer argument");
+  return launch_vmf_modes(O, B, static_cast<float2*>(C_out), static_cast<cudaStream_t>(stream));
 }
 
 int lrq_adam_step(float* params, const float* grads, float* m, float* v, int64_t count, int t, float lr,

@@ -71,7 +71,19 @@ struct ScorePlan {
   size_t off_keys, sz_keys;         // selection keys
   size_t total;
 };
-int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_sms, ScorePlan* p);
+// with_prep = false leaves out the instance's operands (T, tiles, scale,
+// indicator magnitudes): a prepared instance holds them (PrepLayout).
+int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_sms, ScorePlan* p,
+               bool with_prep = true);
+
+// Byte offsets into a prepared instance's buffer: what scoring needs of V
+// that does not depend on the directions.
+struct PrepLayout {
+  int64_t n_tiles;
+  size_t off_T, off_Tpart, off_tiles, off_scale, off_iw;
+  size_t total;
+};
+int plan_prepare(int64_t n, int r, int K, int mode, PrepLayout* L);
 
 struct RescorePlan {
   int64_t n;
@@ -123,6 +135,7 @@ int launch_mlp_backward(const float* params, int F, int B, const float* X, const
 int launch_vmf_nll(const float* O, int B, const float* X, int T, double* loss, float* dO, cudaStream_t st);
 int launch_vmf_sample(const float* O, int B, int S, int K, uint64_t seed, float2* C, int32_t* status,
                       cudaStream_t st);
+int launch_vmf_modes(const float* O, int B, float2* C, cudaStream_t st);
 int launch_adam(float* p, const float* g, float* m, float* v, int64_t count, int t, float lr, float b1, float b2,
                 float eps, cudaStream_t st);
 int launch_proposal_targets(const float2* C, int64_t S, const int64_t* idx, int64_t m, int r, int K, float* out,
@@ -153,8 +166,9 @@ size_t enum_workspace_bytes(int64_t n, int r);
 int launch_enumerate(const double2* V, int64_t n, int r, int K, uint8_t* z_out, double* f_out, int64_t* n_sets_out,
                      void* ws, int32_t* status, cudaStream_t st);
 // tensor-core path
-int launch_tc_pack(const ScorePlan& p, const Alphabet& a, const float2* V, const float2* C, void* tiles, void* ct,
-                   void* scale, void* iw, cudaStream_t st);
+int launch_tc_pack_v(const ScorePlan& p, const Alphabet& a, const float2* V, void* tiles, void* scale, void* iw,
+                     cudaStream_t st);
+int launch_tc_pack_dirs(const ScorePlan& p, const float2* C, void* ct, cudaStream_t st);
 int launch_score_tc(const ScorePlan& p, const Alphabet& a, const void* tiles, const void* ct, const void* scale,
                     const void* iw, double* partial, int32_t* status, cudaStream_t st);
 

@@ -95,6 +95,18 @@ def load() -> ctypes.CDLL:
         lib.lrq_sample_score_workspace_size.restype = I
         lib.lrq_sample_score.argtypes = [P, I64, I, I, P, I, U64, I64, I, I, P, P, P, P, SZ, P, P]
         lib.lrq_sample_score.restype = I
+        lib.lrq_prepared_create.argtypes = [I64, I, I, I, ctypes.POINTER(P)]
+        lib.lrq_prepared_create.restype = I
+        lib.lrq_prepared_destroy.argtypes = [P]
+        lib.lrq_prepared_destroy.restype = None
+        lib.lrq_prepared_size.argtypes = [P, ctypes.POINTER(SZ)]
+        lib.lrq_prepared_size.restype = I
+        lib.lrq_prepare.argtypes = [P, P, P, SZ, P, P]
+        lib.lrq_prepare.restype = I
+        lib.lrq_sample_score_prepared_workspace_size.argtypes = [P, I64, I, ctypes.POINTER(SZ)]
+        lib.lrq_sample_score_prepared_workspace_size.restype = I
+        lib.lrq_sample_score_prepared.argtypes = [P, P, I, U64, I64, I, P, P, P, P, SZ, P, P]
+        lib.lrq_sample_score_prepared.restype = I
         lib.lrq_rescore_workspace_size.argtypes = [I64, I, I, ctypes.POINTER(SZ)]
         lib.lrq_rescore_workspace_size.restype = I
         lib.lrq_rescore.argtypes = [P, I64, I, I, P, I64, P, I, P, P, P, P, P, SZ, P, P]
@@ -137,6 +149,8 @@ def load() -> ctypes.CDLL:
         lib.lrq_vmf_nll.restype = I
         lib.lrq_vmf_sample.argtypes = [P, I, I, I, U64, P, P, P]
         lib.lrq_vmf_sample.restype = I
+        lib.lrq_vmf_modes.argtypes = [P, I, P, P]
+        lib.lrq_vmf_modes.restype = I
         lib.lrq_adam_step.argtypes = [P, P, P, P, I64, I, F32, F32, F32, F32, P]
         lib.lrq_adam_step.restype = I
         lib.lrq_proposal_targets.argtypes = [P, I64, I, I, P, I64, P, P, P]
@@ -181,14 +195,16 @@ def load() -> ctypes.CDLL:
 def exported_symbols():
     """Names of the entry points include/lrq.h declares."""
     return ["lrq_status_string", "lrq_last_error", "lrq_abi_version", "lrq_sample_directions",
-            "lrq_sample_score_workspace_size", "lrq_sample_score", "lrq_rescore_workspace_size",
+            "lrq_sample_score_workspace_size", "lrq_sample_score", "lrq_prepared_create", "lrq_prepared_destroy",
+            "lrq_prepared_size", "lrq_prepare", "lrq_sample_score_prepared_workspace_size",
+            "lrq_sample_score_prepared", "lrq_rescore_workspace_size",
             "lrq_rescore", "lrq_rescore_no_alloc", "lrq_truncate_workspace_size", "lrq_truncate",
             "lrq_sample_null_directions", "lrq_spectral_energy", "lrq_rank1_workspace_size", "lrq_rank1_sweep", "lrq_two_eigvec_q", "lrq_greedy_workspace_size", "lrq_greedy_cut",
             "lrq_enumerate_workspace_size", "lrq_enumerate", "lrq_batched_plan_create", "lrq_batched_plan_destroy",
             "lrq_batched_workspace_size", "lrq_batched_prepare", "lrq_batched_autotune", "lrq_batched_tile",
             "lrq_sample_score_batched", "lrq_batched_graph_create", "lrq_graph_launch", "lrq_graph_destroy",
             "lrq_proposal_num_features", "lrq_proposal_num_params", "lrq_proposal_features", "lrq_mlp_forward",
-            "lrq_mlp_backward", "lrq_vmf_nll", "lrq_vmf_sample", "lrq_adam_step",
+            "lrq_mlp_backward", "lrq_vmf_nll", "lrq_vmf_sample", "lrq_vmf_modes", "lrq_adam_step",
             "lrq_proposal_targets", "lrq_standardize_fit", "lrq_standardize",
             "lrq_cut_count", "lrq_set_timing_events", "lrq_kernel_launches"]
 
@@ -324,6 +340,12 @@ def lrq_vmf_sample(O, S, K, seed, C_out, dev_status, stream=None):
     B = O.shape[0]
     _check(load().lrq_vmf_sample(_ptr(O), B, int(S), int(K), int(seed), _ptr(C_out), _ptr(dev_status),
                                  _stream(stream)), "lrq_vmf_sample")
+
+
+def lrq_vmf_modes(O, C_out, stream=None):
+    B = O.shape[0]
+    assert O.dtype == torch.float32 and C_out.dtype == torch.complex64 and C_out.numel() == B * 16 * 4
+    _check(load().lrq_vmf_modes(_ptr(O), B, _ptr(C_out), _stream(stream)), "lrq_vmf_modes")
 
 
 def lrq_adam_step(params, grads, m, v, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, stream=None):
@@ -623,6 +645,75 @@ class BatchedPlan:
             self.graph = None
         if self.h:
             load().lrq_batched_plan_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class PreparedInstance:
+    """Owns an lrq_prepared_v handle and its device buffer; keeps V alive.
+    prepare(V) packs V's operands once; sample_score(...) then scores
+    directions against them (same results as the module-level sample_score)."""
+
+    def __init__(self, n, r, K, mode=LRQ_MODE_TC, device="cuda"):
+        h = ctypes.c_void_p()
+        _check(load().lrq_prepared_create(int(n), int(r), int(K), int(mode), ctypes.byref(h)), "lrq_prepared_create")
+        self.h = h
+        self.n, self.r, self.K, self.mode, self.device = int(n), int(r), int(K), int(mode), device
+        nb = ctypes.c_size_t(0)
+        _check(load().lrq_prepared_size(self.h, ctypes.byref(nb)), "lrq_prepared_size")
+        self.nbytes = int(nb.value)
+        self.buf = workspace(self.nbytes, device) if self.nbytes else None
+        self.V = None
+        self.dev_status = torch.zeros(1, dtype=torch.int32, device=device)
+
+    def prepare(self, V, stream=None):
+        assert V.dtype == torch.complex64 and tuple(V.shape) == (self.n, self.r)
+        bb = self.buf.numel() if self.buf is not None else 0
+        _check(load().lrq_prepare(self.h, _ptr(V), _ptr(self.buf), bb, _ptr(self.dev_status), _stream(stream)),
+               "lrq_prepare")
+        self.V = V
+        return self
+
+    def workspace_size(self, S, top_m):
+        out = ctypes.c_size_t(0)
+        _check(load().lrq_sample_score_prepared_workspace_size(self.h, int(S), int(top_m), ctypes.byref(out)),
+               "lrq_sample_score_prepared_workspace_size")
+        return int(out.value)
+
+    def score_into(self, C, generate_C, seed, top_m, scores_out, top_idx_out, top_f_out, ws, dev_status,
+                   stream=None):
+        assert C.dtype == torch.complex64 and C.shape[1] == self.r
+        _check(load().lrq_sample_score_prepared(self.h, _ptr(C), int(bool(generate_C)), int(seed), C.shape[0],
+                                                int(top_m), _ptr(scores_out), _ptr(top_idx_out), _ptr(top_f_out),
+                                                _ptr(ws), ws.numel() * ws.element_size(), _ptr(dev_status),
+                                                _stream(stream)), "lrq_sample_score_prepared")
+
+    def sample_score(self, C=None, S=None, seed=0, top_m=64, want_scores=False, ws=None, dev_status=None,
+                     stream=None):
+        dev = self.device
+        generate = C is None
+        if generate:
+            C = torch.empty((int(S), self.r), dtype=torch.complex64, device=dev)
+        S = C.shape[0]
+        need = self.workspace_size(S, top_m)
+        if ws is None or ws.numel() < need:
+            ws = workspace(need, dev)
+        if dev_status is None:
+            dev_status = torch.zeros(1, dtype=torch.int32, device=dev)
+        top_idx = torch.empty(top_m, dtype=torch.int64, device=dev)
+        top_f = torch.empty(top_m, dtype=torch.float32, device=dev)
+        scores = torch.empty(S, dtype=torch.float32, device=dev) if want_scores else None
+        self.score_into(C, generate, seed, top_m, scores, top_idx, top_f, ws, dev_status, stream)
+        return dict(C=C, top_idx=top_idx, top_f=top_f, scores=scores, dev_status=dev_status, ws=ws)
+
+    def close(self):
+        if self.h:
+            load().lrq_prepared_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -16,7 +16,10 @@ gauge of lrq_proposal_features and moved to the canonical window
 arg c_1 in (-pi/K, pi/K] (Sec. 2.3: c and omega^k c score the same).
 Metric: for a held-out instance, U* = the best score of S_max uniform
 directions; S_u (S_l) = the shortest prefix of the uniform (learned) stream
-whose best reaches 0.999 U*; reported as the median of S_u / S_l.
+whose best reaches 0.999 U*; reported as the median of S_u / S_l.  The
+learned stream is the mixture's 16 component means by weight
+(lrq_vmf_modes), then vMF draws.  The fixed-direction baseline stream is e_1
+(the leading eigenvector's direction in the gauge), then the uniform stream.
 """
 from __future__ import annotations
 
@@ -33,7 +36,13 @@ N_OUT = 160
 
 
 SIGMA_EASY = (0.5, 2.0)     # the angular-synchronisation workload: ||sigma W|| ~ 2 sigma sqrt(n) << n
-SIGMA_HARD = (12.0, 20.0)   # at n = 4096: ||sigma W|| ~ 2 sigma sqrt(n) ~ n / 2, comparable to lambda_1 = n
+
+
+def sigma_hard(n: int):
+    """The high-noise regime: sigma sqrt(n) in [3n/16, 5n/16], so that
+    ||sigma W|| ~ 2 sigma sqrt(n) ~ n / 2 is comparable to lambda_1 = n
+    (sigma in [12, 20] at n = 4096)."""
+    return (0.1875 * math.sqrt(n), 0.3125 * math.sqrt(n))
 
 
 def make_instance(n: int, seed: int, device="cuda", sigma_range=SIGMA_EASY):
@@ -157,6 +166,12 @@ class Proposal:
         lrq.lrq_adam_step(self.params, grads, self.m, self.v, self.t, lr=lr)
         return loss
 
+    def modes(self, X):
+        O, _ = self.forward(X)
+        C = torch.empty((X.shape[0], 16, R), dtype=torch.complex64, device=X.device)
+        lrq.lrq_vmf_modes(O, C)
+        return C
+
     def sample(self, X, S: int, K: int, seed: int):
         O, _ = self.forward(X)
         C = torch.empty((X.shape[0], S, R), dtype=torch.complex64, device=X.device)
@@ -185,26 +200,37 @@ def prefix_to_reach(scores, target):
 
 
 def evaluate(model: Proposal, Vg, feat, K: int, S_max: int, seed: int, level=0.999):
-    """Per instance (U*, S_u, S_l, S_e1); the learned stream has the same
-    length S_max.  S_e1 is the fixed-direction baseline: the single direction
-    e_1 in the gauge of lrq_proposal_features (1 if it reaches level U*, else
-    inf), which shows what the network adds over a constant guess."""
+    """Per instance (U*, S_u, S_l, S_e1u, S_draws), each S the 1-based length of
+    the shortest prefix of its stream reaching level U* (inf if none):
+    S_u uniform directions; S_l the learned stream (16 modes, then
+    S_max - 16 vMF draws); S_e1u the fixed direction e_1 followed by the
+    uniform stream; S_draws the vMF draws alone."""
     X = model.standardize(feat)
-    C = model.sample(X, S_max, K, seed)
+    M = model.modes(X)
+    C = model.sample(X, S_max - M.shape[1], K, seed)
     e1 = torch.zeros((1, R), dtype=torch.complex64, device=Vg.device)
     e1[0, 0] = 1.0
     rows = []
     for b in range(Vg.shape[0]):
         fu = uniform_scores(Vg[b], K, S_max, seed + 7919 * (b + 1))
         ustar = float(fu.max().item())
-        fl = scores_of(Vg[b], K, C[b].contiguous())
+        lev = level * ustar
+        fm = scores_of(Vg[b], K, M[b].contiguous())
+        fd = scores_of(Vg[b], K, C[b].contiguous())
         fe = float(scores_of(Vg[b], K, e1).max().item())
-        rows.append((ustar, prefix_to_reach(fu, level * ustar), prefix_to_reach(fl, level * ustar),
-                     1.0 if fe >= level * ustar else math.inf))
+        su = prefix_to_reach(fu, lev)
+        rows.append((ustar, su, prefix_to_reach(torch.cat([fm, fd]), lev), 1.0 if fe >= lev else 1.0 + su,
+                     prefix_to_reach(fd, lev)))
     return rows
 
 
 def median_gain(rows, baseline=1):
-    """Median of S_baseline / S_l (baseline 1: uniform sampling; 3: e_1)."""
+    """Median of S_baseline / S_l (baseline 1: uniform sampling; 3: e_1, then
+    uniform)."""
     ratios = sorted(r[baseline] / r[2] for r in rows)
     return ratios[len(ratios) // 2]
+
+
+def reached_within(rows, col: int, budget: int) -> int:
+    """Instances whose stream in column col reaches the level within budget draws."""
+    return sum(1 for r in rows if r[col] <= budget)

@@ -237,3 +237,36 @@ def test_spectral_energy_rejects_bad_arguments_on_host(lib):
     assert lib.lrq_spectral_energy(ctypes.byref(bad), P(256), 2, P(512), P(1024), P(2048), None) == 1
     dense = L.LrqMatrix(L.LRQ_MATRIX_DENSE_C128, 100, 4096, 50, None, None, None, 0)
     assert lib.lrq_spectral_energy(ctypes.byref(dense), P(256), 2, P(512), P(1024), P(2048), None) == 1
+
+
+@pytest.mark.parametrize("n,r,K,mode,code", [(0, 4, 8, 1, 1), (64, 9, 8, 1, 1), (64, 4, 1, 1, 1),
+                                             (64, 4, 8, 7, 1), (64, 4, 9, 1, 2)])
+def test_prepared_create_rejects_bad_arguments_on_host(lib, n, r, K, mode, code):
+    h = ctypes.c_void_p()
+    assert lib.lrq_prepared_create(n, r, K, mode, ctypes.byref(h)) == code
+    assert not h.value
+
+
+def test_prepared_sizes_and_unprepared_call(lib):
+    from paper_2602_20376_gb300 import lrq
+    sizes = {}
+    for mode in (lrq.LRQ_MODE_FP32, lrq.LRQ_MODE_TC):
+        h = ctypes.c_void_p()
+        assert lib.lrq_prepared_create(100000, 4, 8, mode, ctypes.byref(h)) == 0
+        nb = ctypes.c_size_t(0)
+        assert lib.lrq_prepared_size(h, ctypes.byref(nb)) == 0
+        sizes[mode] = nb.value
+        # scoring before lrq_prepare is refused on the host
+        st = lib.lrq_sample_score_prepared(h, ctypes.c_void_p(256), 1, 0, 1024, 4, None, ctypes.c_void_p(256),
+                                           ctypes.c_void_p(256), ctypes.c_void_p(256), 1 << 30,
+                                           ctypes.c_void_p(256), None)
+        assert st == lrq.LRQ_EINVAL and "prepare" in lrq.lrq_last_error()
+        # a buffer below the size is refused before any launch
+        if nb.value:
+            st = lib.lrq_prepare(h, ctypes.c_void_p(256), ctypes.c_void_p(256), nb.value - 1, ctypes.c_void_p(256),
+                                 None)
+            assert st == lrq.LRQ_EWORKSPACE
+        lib.lrq_prepared_destroy(h)
+    assert sizes[lrq.LRQ_MODE_FP32] == 0
+    # the packed coordinate tiles dominate: at least 8 bytes per coordinate
+    assert sizes[lrq.LRQ_MODE_TC] >= 8 * 100000

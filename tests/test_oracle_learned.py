@@ -210,3 +210,39 @@ def test_standardize_invariants():
     # a single row: centred to zero, unscaled
     m1, s1 = L.standardize_fit(feat[:1])
     assert np.all(s1 == 1.0) and np.all(L.standardize(feat[:1], m1, s1) == 0.0)
+
+
+def test_vmf_modes_by_hand():
+    # component m: u = (m + 1) e_(m mod 8), so mu_m = e_(m mod 8); logits
+    # -(m mod 5): ranks go 0, 5, 10, 15 (logit 0), then 1, 6, 11, ...
+    O = np.zeros((1, L.N_COMP, L.HEAD))
+    for m in range(L.N_COMP):
+        O[0, m, m % 8] = m + 1.0
+        O[0, m, 8] = 0.3
+        O[0, m, 9] = -(m % 5)
+    O[0, 7, :8] = 0.0  # a zero u: the mode is e_1 by convention
+    got = L.vmf_modes(O.reshape(1, -1))[0]
+    order = [0, 5, 10, 15, 1, 6, 11, 2, 7, 12, 3, 8, 13, 4, 9, 14]
+    for rank, m in enumerate(order):
+        want = np.zeros(8)
+        want[0 if m == 7 else m % 8] = 1.0
+        assert np.array_equal(got[rank], want[0::2] + 1j * want[1::2]), (rank, m)
+    # the order is the mixture weights' order (softmax is monotone)
+    _, _, logpi = L.head(O.reshape(1, -1))
+    assert np.all(np.diff(logpi[0][order]) <= 0)
+
+
+def test_vmf_modes_unit_norm_and_direction():
+    rng = np.random.default_rng(5)
+    O = rng.standard_normal((3, L.N_OUT))
+    modes = L.vmf_modes(O)
+    Oh = O.reshape(3, L.N_COMP, L.HEAD)
+    for b in range(3):
+        ranks = np.argsort(-Oh[b, :, 9], kind="stable")
+        for rank, m in enumerate(ranks):
+            c = modes[b, rank]
+            assert abs(np.linalg.norm(c) - 1.0) < 1e-12
+            u = Oh[b, m, :8]
+            # mu is the positive multiple of u
+            x = L.to_real8(c[None])[0]
+            assert np.dot(x, u) > 0 and np.allclose(x * np.linalg.norm(u), u, atol=1e-12)
