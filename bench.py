@@ -661,6 +661,7 @@ def run_batched(args):
         lrq.check_status(plan.status, "batched")
     ms = sum(x.elapsed_time(y) for x, y in zip(a, b)) / args.steps
     kms = sum(x.elapsed_time(y) for x, y in zip(ka, kb)) / args.steps
+    mixed = _mixed_subbatch(torch, lrq, probs, g, tg, dev, args) if args.exact_subbatch > 0 else None
     tiles = {}
     for p in range(P):
         tiles[plan.tile(p)] = tiles.get(plan.tile(p), 0) + 1
@@ -677,8 +678,51 @@ def run_batched(args):
                     "frac": flops / (kms * 1e-3) / 1e12 / peak_alu, "traffic": None,
                     "kernel": "batched_score_kernel", "kernel_ms": kms,
                     "peak_kind": "derived: 152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz"},
-          batched={"prep_s": t_prep, "autotune_s": t_at, "tiles": tiles})
+          batched={"prep_s": t_prep, "autotune_s": t_at, "tiles": tiles, "mixed": mixed})
     plan.close()
+
+
+def _mixed_subbatch(torch, lrq, probs, g, tg, dev, args):
+    """The labelled exact sub-batch: problems with n ~ U{8..48}, r = 2,
+    K ~ U{2,3,4,8} (same instance recipe, truncated to r = 2) added to the 512
+    sampled ones and solved by vertex enumeration in the same graph-captured
+    persistent launch; returns the mixed launch's time and its size."""
+    from paper_2602_20376_gb300 import lrq as L
+    ex, sets = [], 0
+    for p in range(args.exact_subbatch):
+        n = int(g.integers(8, 49))
+        Kp = int(g.choice([2, 3, 4, 8]))
+        tg.manual_seed(5000 + p)
+        V0 = torch.randn((n, 2), generator=tg, device=dev, dtype=torch.complex128)
+        Q = V0 @ V0.conj().T
+        nrm = torch.linalg.eigvalsh(V0.conj().T @ V0)[-1].item()
+        G = torch.randn((n, n), generator=tg, device=dev, dtype=torch.complex128)
+        Q += (0.05 * nrm / (2.0 * np.sqrt(n) * np.sqrt(0.5))) * 0.5 * (G + G.conj().T)
+        tr = L.truncate(L.dense_matrix(Q), 2, tol=1e-10, seed=p, want_c128=False)
+        ex.append(dict(V=tr["V32"], K=Kp, exact=True))
+        BK = Kp // 2 if Kp % 2 == 0 else Kp
+        N = n * BK
+        sets += N * (N - 1) * (N - 2) // 6 + N
+    torch.cuda.synchronize()
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plan = lrq.BatchedPlan(probs + ex, top_m=4, stream=stream)
+        plan.capture()
+        for _ in range(args.warmup):
+            plan.replay()
+        stream.synchronize()
+        a, b = _events(torch, args.steps), _events(torch, args.steps)
+        for i in range(args.steps):
+            a[i].record(stream)
+            plan.replay()
+            b[i].record(stream)
+        stream.synchronize()
+        lrq.check_status(plan.status, "mixed batched")
+    ms = sum(x.elapsed_time(y) for x, y in zip(a, b)) / args.steps
+    plan.close()
+    return {"ms_per_step": ms, "exact_problems": len(ex), "index_sets": sets,
+            "workload": "exact sub-batch: n ~ U{8..48}, r = 2, K ~ U{2,3,4,8}, solved by vertex enumeration "
+                        "(Algorithm 2) in the same launch as the 512 sampled instances"}
 
 
 def run_rank1(args, hybrid=False):
@@ -765,6 +809,8 @@ def main():
     ap.add_argument("--sampler", choices=["uniform", "null"], default="uniform",
                     help="direction sampler of the maxcut workload")
     ap.add_argument("--no-learned", action="store_true", help="leave samples_to_best out of the default line")
+    ap.add_argument("--exact-subbatch", type=int, default=32,
+                    help="exact problems (S = 0) added to the batched workload's mixed launch")
     ap.add_argument("--learned-n", type=int, default=4096)
     ap.add_argument("--learned-train", type=int, default=256)
     ap.add_argument("--learned-eval", type=int, default=256)

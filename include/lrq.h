@@ -300,10 +300,20 @@ int lrq_rescore_no_alloc(const void* V, int64_t n, int r, int K, const void* C, 
  *   problems : P problem descriptors (HOST array; V and C device pointers,
  *              which must stay valid while the plan is used).
  *   best_f_out : P doubles (device), FP64 objective of each problem's winner.
- *   best_idx_out : P int64 (device), the winner's candidate index.
- * Limits: 1 <= r_p <= 8, 2 <= K_p <= 64, 1 <= S_p <= 8192, 1 <= n_p < 2^31,
- * 1 <= top_m <= min(16, S_p), P <= 65535.  Non-finite V or C -> LRQ_EINVAL
- * in *dev_status.
+ *   best_idx_out : P int64 (device), the winner's candidate index (-1 for
+ *              an exact problem).
+ * Exact sub-batch: a problem with S = 0 (and C = NULL) is solved exactly in
+ * the same persistent launch by vertex enumeration (Sec. 3, Algorithm 2;
+ * the candidates and FP64 arithmetic of lrq_enumerate, on V converted to
+ * FP64): best_f_out is max over A_K^n of ||V^H z||^2 and best_idx_out is
+ * -1.  Allowed when r <= 4, K <= 8, n <= 512 and r n^(2r+1) <= 1e10 (for
+ * r = 2: n <= 87); otherwise plan creation fails with
+ * LRQ_EUNSUPPORTED.  A vertex at which too many coordinates touch a
+ * boundary to be branched exactly reports LRQ_EUNSUPPORTED in *dev_status,
+ * as does a V whose first column is zero (no index set of full rank).
+ * Limits: 1 <= r_p <= 8, 2 <= K_p <= 64, 0 <= S_p <= 8192, 1 <= n_p < 2^31,
+ * 1 <= top_m <= 16 and top_m <= S_p for every sampled problem, P <= 65535.
+ * Non-finite V or C -> LRQ_EINVAL in *dev_status.
  * ------------------------------------------------------------------------ */
 typedef struct {
   const void* V;   /* n x r complex64 (device) */

@@ -16,6 +16,14 @@
 // flushed to FP64 per stage), then one block per problem selects the top-m
 // keys and re-scores them in FP64 (decision and sums in FP64), and keeps
 // the best (ties to the smaller candidate index).
+//
+// Exact sub-batch: a problem given with S = 0 is solved exactly by vertex
+// enumeration (Sec. 3, Algorithm 2) in the same persistent launch.  Its
+// index sets, levels d = r..1 in turn, are cut into chunks of kBEnumChunk
+// consecutive ranks; a chunk is one work item (FP64 null vectors and
+// candidate scores, as in the standalone solver), whose best candidate goes
+// to the problem's slot for that chunk, and the selection step reduces the
+// chunks in the solver's deterministic order.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,6 +35,7 @@
 #include <tuple>
 #include <vector>
 
+#include "enum_device.cuh"
 #include "lrq_device.cuh"
 #include "lrq_internal.h"
 
@@ -37,6 +46,9 @@ constexpr int kBRows = 128;       // V rows per shared-memory stage
 constexpr int kBMaxS = 8192;      // candidates per problem
 constexpr int kBMaxTopM = 16;
 constexpr int kBTiles[3] = {64, 128, 256};
+constexpr int kBEnumRanksPerThread = 16;
+constexpr int kBEnumChunk = kBThreads * kBEnumRanksPerThread;  // index sets per exact work item
+constexpr double kBEnumBudget = 1e10;                            // r n^(2r+1) of one exact problem
 
 struct BProb {
   const float2* V;
@@ -44,9 +56,13 @@ struct BProb {
   int64_t n;
   int r, K, S, tile;
   int gen;          // 1: draw C from seed (+ epoch)
-  int pad;
+  int exact;        // 1: solved exactly by vertex enumeration (S = 0)
   uint64_t seed;
   int64_t key_off;  // offset of the problem's selection keys
+  int64_t eb_off;   // exact: offset of its chunk results
+  int nchunks;      // exact: work items
+  int pad;
+  unsigned long long lvl_total[kEnumMaxD];  // exact: index sets of level d at [d - 1]
 };
 
 struct BItem {
@@ -63,6 +79,8 @@ struct BTable {
 
 // decision tables for K = 0..64 (entries below 2 unused), filled once per device
 static __device__ BTable g_btab[kMaxK + 1];
+// the exact solver's tables for K = 2..8
+static __device__ EnumTables g_etab[kMaxTcK + 1];
 
 // ---------------------------------------------------------------------------
 // direction sampling and input checks
@@ -213,10 +231,71 @@ __device__ __forceinline__ void b_dispatch_k(const BProb& pb, int s0, BShared& s
   }
 }
 
+// One exact work item: index sets [chunk kBEnumChunk, (chunk + 1) kBEnumChunk)
+// of the problem's levels d = r..1 taken in turn, kBEnumRanksPerThread
+// consecutive ranks per thread; the block's best candidate (the solver's
+// order) goes to ebest[eb_off + chunk].  Kept out of line so that the
+// scoring path keeps its registers.
+__device__ __noinline__ void b_enum_item(const BProb& pb, int chunk, BShared& sh, EnumBest* __restrict__ ebest,
+                                         int32_t* status) {
+  const EnumTables& tb = g_etab[pb.K];
+  const EnumV32 va{pb.V, pb.r};
+  const int n = static_cast<int>(pb.n);
+  const int N = n * tb.BK;
+  unsigned long long total = 0;
+  for (int d = 1; d <= pb.r; ++d) total += pb.lvl_total[d - 1];
+  EnumBest best;
+  best.f = -1.0;
+  best.level = 0;
+  best.sign = 1;
+  best.rank = 0;
+  best.choice = 0;
+  unsigned long long q = static_cast<unsigned long long>(chunk) * kBEnumChunk +
+                         static_cast<unsigned long long>(threadIdx.x) * kBEnumRanksPerThread;
+  const unsigned long long qend = min(total, q + kBEnumRanksPerThread);
+  while (q < qend) {
+    int d = pb.r;
+    unsigned long long base = 0;
+    while (d >= 1 && q >= base + pb.lvl_total[d - 1]) {
+      base += pb.lvl_total[d - 1];
+      --d;
+    }
+    if (d < 1) break;
+    const int m = 2 * d - 1;
+    const unsigned long long l0 = q - base;
+    const unsigned long long l1 = min(qend - base, pb.lvl_total[d - 1]);
+    int I[kEnumMaxRows];
+    unrank(l0, N, m, I);
+    for (unsigned long long lr = l0; lr < l1; ++lr) {
+      if (lr > l0) next_comb(N, m, I);
+      if (!valid_set(I, m, tb.BK)) continue;
+      double H[kEnumMaxRows * 2 * kEnumMaxD];
+      build_rows(va, pb.r, d, I, m, tb, H);
+      double ct[2 * kEnumMaxD];
+      if (!null_vector_fp64<kEnumMaxRows>(H, m, ct)) continue;
+      eval_vertex(va, n, pb.r, d, I, m, ct, +1, tb, best, lr, -1, nullptr, nullptr, status);
+      eval_vertex(va, n, pb.r, d, I, m, ct, -1, tb, best, lr, -1, nullptr, nullptr, status);
+    }
+    q = base + l1;
+  }
+  EnumBest* sb = reinterpret_cast<EnumBest*>(sh.comb);
+  __syncthreads();
+  sb[threadIdx.x] = best;
+  __syncthreads();
+  for (int h = kBThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h && enum_better(sb[threadIdx.x + h], sb[threadIdx.x])) sb[threadIdx.x] = sb[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) ebest[pb.eb_off + chunk] = sb[0];
+  __syncthreads();
+}
+
 __global__ void __launch_bounds__(kBThreads) batched_score_kernel(const BProb* __restrict__ probs,
                                                                   const BItem* __restrict__ items, int nitems,
                                                                   int* __restrict__ counter,
-                                                                  uint64_t* __restrict__ keys) {
+                                                                  uint64_t* __restrict__ keys,
+                                                                  EnumBest* __restrict__ ebest,
+                                                                  int32_t* status) {
   __shared__ BShared sh;
   for (;;) {
     if (threadIdx.x == 0) sh.next = atomicAdd(counter, 1);
@@ -226,6 +305,10 @@ __global__ void __launch_bounds__(kBThreads) batched_score_kernel(const BProb* _
     if (it >= nitems) break;
     const BItem w = items[it];
     const BProb pb = probs[w.p];
+    if (pb.exact) {
+      b_enum_item(pb, w.s0, sh, ebest, status);
+      continue;
+    }
     switch (pb.r) {
       case 1: b_dispatch_k<1>(pb, w.s0, sh, keys); break;
       case 2: b_dispatch_k<2>(pb, w.s0, sh, keys); break;
@@ -301,8 +384,35 @@ __device__ double b_rescore(const BProb& pb, int s, double* red) {
   return f;
 }
 
+// Exact problem: the best of its chunk results, in the solver's order.
+__device__ void b_select_exact(const BProb& pb, const EnumBest* __restrict__ ebest, double* best_f, int64_t* best_idx,
+                               int32_t* status) {
+  __shared__ EnumBest sb[kBThreads];
+  EnumBest best;
+  best.f = -1.0;
+  best.level = 0;
+  best.sign = 1;
+  best.rank = 0;
+  best.choice = 0;
+  for (int c = threadIdx.x; c < pb.nchunks; c += kBThreads)
+    if (enum_better(ebest[pb.eb_off + c], best)) best = ebest[pb.eb_off + c];
+  sb[threadIdx.x] = best;
+  __syncthreads();
+  for (int h = kBThreads / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h && enum_better(sb[threadIdx.x + h], sb[threadIdx.x])) sb[threadIdx.x] = sb[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    // no index set of full rank at any level (V's first column is zero)
+    if (sb[0].f < 0.0) dev_fail(status, LRQ_EUNSUPPORTED);
+    best_f[blockIdx.x] = sb[0].f;
+    best_idx[blockIdx.x] = -1;
+  }
+}
+
 __global__ void __launch_bounds__(kBThreads) batched_select_kernel(const BProb* __restrict__ probs,
                                                                    const uint64_t* __restrict__ keys, int top_m,
+                                                                   const EnumBest* __restrict__ ebest,
                                                                    double* __restrict__ best_f,
                                                                    int64_t* __restrict__ best_idx,
                                                                    int64_t* __restrict__ epoch,
@@ -310,6 +420,11 @@ __global__ void __launch_bounds__(kBThreads) batched_select_kernel(const BProb* 
   __shared__ uint64_t redk[kBThreads / 32];
   __shared__ double redd[kBThreads / 32];
   const BProb pb = probs[blockIdx.x];
+  if (blockIdx.x == 0 && threadIdx.x == 0) *epoch += 1;  // the next call draws fresh directions
+  if (pb.exact) {
+    b_select_exact(pb, ebest, best_f, best_idx, status);
+    return;
+  }
   const uint64_t* kp = keys + pb.key_off;
   const int m = min(top_m, pb.S);
   double bf = -1.0;
@@ -346,7 +461,6 @@ __global__ void __launch_bounds__(kBThreads) batched_select_kernel(const BProb* 
     best_f[blockIdx.x] = bf;
     best_idx[blockIdx.x] = bs;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) *epoch += 1;  // the next call draws fresh directions
 }
 
 // ---------------------------------------------------------------------------
@@ -359,7 +473,9 @@ struct lrq_batched_plan_impl {
   int device = 0;
   int grid = 0;
   int64_t nkeys = 0, ncgen = 0;
-  size_t off_probs = 0, off_items = 0, off_counter = 0, off_epoch = 0, off_keys = 0, off_C = 0, total = 0;
+  size_t off_probs = 0, off_items = 0, off_counter = 0, off_epoch = 0, off_keys = 0, off_C = 0, off_ebest = 0,
+         total = 0;
+  int64_t nebest = 0;
   int nitems = 0;
   bool prepared = false;
   const void* prepared_ws = nullptr;
@@ -401,8 +517,27 @@ int ensure_tables(int dev) {
   }
   int e = cuda_check(cudaMemcpyToSymbol(g_btab, t.data(), t.size() * sizeof(BTable)), "upload decision tables");
   if (e) return e;
+  std::vector<EnumTables> et(kMaxTcK + 1);
+  std::memset(et.data(), 0, et.size() * sizeof(EnumTables));
+  for (int K = 2; K <= kMaxTcK; ++K) et[K] = make_enum_tables(K);
+  if ((e = cuda_check(cudaMemcpyToSymbol(g_etab, et.data(), et.size() * sizeof(EnumTables)),
+                      "upload enumeration tables")))
+    return e;
   g_btab_ready[dev] = true;
   return LRQ_OK;
+}
+
+// Index sets of an exact problem's levels d = 1..r, and its work items.
+void exact_levels(const lrq_problem& q, unsigned long long* lvl) {
+  const int BK = (q.K % 2 == 0) ? q.K / 2 : q.K;
+  for (int d = 1; d <= kEnumMaxD; ++d) lvl[d - 1] = d <= q.r ? binom(static_cast<int>(q.n) * BK, 2 * d - 1) : 0ull;
+}
+
+int64_t exact_chunks(const lrq_problem& q) {
+  unsigned long long lvl[kEnumMaxD], total = 0;
+  exact_levels(q, lvl);
+  for (int d = 0; d < kEnumMaxD; ++d) total += lvl[d];
+  return static_cast<int64_t>((total + kBEnumChunk - 1) / kBEnumChunk);
 }
 
 void layout(lrq_batched_plan_impl* pl) {
@@ -416,7 +551,14 @@ void layout(lrq_batched_plan_impl* pl) {
   int64_t nitems = 0;
   pl->nkeys = 0;
   pl->ncgen = 0;
+  pl->nebest = 0;
   for (const lrq_problem& q : pl->probs) {
+    if (q.S == 0) {  // exact
+      const int64_t ch = exact_chunks(q);
+      nitems += ch;
+      pl->nebest += ch;
+      continue;
+    }
     nitems += ceil_div(q.S, kBTiles[0]);  // room for the smallest tile
     pl->nkeys += q.S;
     if (!q.C) pl->ncgen += q.S * q.r;
@@ -427,6 +569,7 @@ void layout(lrq_batched_plan_impl* pl) {
   pl->off_epoch = take(sizeof(int64_t));
   pl->off_keys = take(static_cast<size_t>(pl->nkeys) * sizeof(uint64_t));
   pl->off_C = take(static_cast<size_t>(pl->ncgen) * sizeof(float2));
+  pl->off_ebest = take(static_cast<size_t>(pl->nebest) * sizeof(EnumBest));
   pl->total = cur;
 }
 
@@ -436,13 +579,25 @@ int upload(lrq_batched_plan_impl* pl, uint8_t* ws, const std::vector<int>& subse
            int* nitems_out) {
   const int P = static_cast<int>(pl->probs.size());
   std::vector<BProb> hp(P);
-  int64_t key_off = 0, c_off = 0;
+  int64_t key_off = 0, c_off = 0, eb_off = 0;
   float2* Cgen = reinterpret_cast<float2*>(ws + pl->off_C);
   for (int p = 0; p < P; ++p) {
     const lrq_problem& q = pl->probs[p];
     BProb b;
     std::memset(&b, 0, sizeof(b));
     b.V = static_cast<const float2*>(q.V);
+    if (q.S == 0) {
+      b.exact = 1;
+      b.n = q.n;
+      b.r = q.r;
+      b.K = q.K;
+      exact_levels(q, b.lvl_total);
+      b.nchunks = static_cast<int>(exact_chunks(q));
+      b.eb_off = eb_off;
+      eb_off += b.nchunks;
+      hp[p] = b;
+      continue;
+    }
     b.gen = q.C ? 0 : 1;
     b.C = q.C ? static_cast<const float2*>(q.C) : Cgen + c_off;
     if (!q.C) c_off += q.S * q.r;
@@ -460,14 +615,22 @@ int upload(lrq_batched_plan_impl* pl, uint8_t* ws, const std::vector<int>& subse
   if (which.empty())
     for (int p = 0; p < P; ++p) which.push_back(p);
   std::vector<BItem> items;
-  for (int p : which)
+  for (int p : which) {
+    if (hp[p].exact) {
+      for (int c = 0; c < hp[p].nchunks; ++c) items.push_back(BItem{p, c});
+      continue;
+    }
     for (int s0 = 0; s0 < hp[p].S; s0 += hp[p].tile) items.push_back(BItem{p, s0});
-  // longest first: cost ~ n_p * tile * (r_p + 1)
-  std::stable_sort(items.begin(), items.end(), [&](const BItem& a, const BItem& b) {
-    const double ca = static_cast<double>(hp[a.p].n) * hp[a.p].tile * (hp[a.p].r + 1);
-    const double cb = static_cast<double>(hp[b.p].n) * hp[b.p].tile * (hp[b.p].r + 1);
-    return ca > cb;
-  });
+  }
+  // longest first: cost ~ n_p * tile * (r_p + 1) FP32 lane operations for a
+  // scoring item; an exact item's kBEnumChunk index sets each cost two
+  // vertices of about n_p (4 d + 24) FP64 operations, weighted 32x
+  auto cost = [&](const BItem& it) {
+    const BProb& b = hp[it.p];
+    if (b.exact) return static_cast<double>(b.n) * kBEnumChunk * 2.0 * (4.0 * b.r + 24.0) * 32.0 / kBThreads;
+    return static_cast<double>(b.n) * b.tile * (b.r + 1);
+  };
+  std::stable_sort(items.begin(), items.end(), [&](const BItem& a, const BItem& b) { return cost(a) > cost(b); });
   int e = cuda_check(cudaMemcpyAsync(ws + pl->off_probs, hp.data(), hp.size() * sizeof(BProb),
                                      cudaMemcpyHostToDevice, st),
                      "upload problems");
@@ -497,12 +660,13 @@ int launch_sequence(const lrq_batched_plan_impl* pl, uint8_t* ws, int nitems, bo
   int e = cuda_check(cudaMemsetAsync(counter, 0, sizeof(int), st), "reset item counter");
   if (e) return e;
   timing_start(st);
+  EnumBest* ebest = reinterpret_cast<EnumBest*>(ws + pl->off_ebest);
   batched_score_kernel<<<pl->grid, kBThreads, 0, st>>>(probs, reinterpret_cast<const BItem*>(ws + pl->off_items),
-                                                       nitems, counter, keys);
+                                                       nitems, counter, keys, ebest, status);
   timing_stop(st);
   count_launch();
   if (select) {
-    batched_select_kernel<<<P, kBThreads, 0, st>>>(probs, keys, pl->top_m, best_f, best_idx, epoch, status);
+    batched_select_kernel<<<P, kBThreads, 0, st>>>(probs, keys, pl->top_m, ebest, best_f, best_idx, epoch, status);
     count_launch();
   }
   return cuda_check(cudaGetLastError(), "batched kernels");
@@ -533,7 +697,15 @@ int lrq_batched_plan_create(const lrq_problem* problems, int P, int top_m, lrq_b
     if (q.n < 1 || q.n >= (int64_t(1) << 31)) return fail(LRQ_EINVAL, "problem " + std::to_string(p) + ": bad n");
     if (q.r < 1 || q.r > kMaxRank) return fail(LRQ_EINVAL, "problem " + std::to_string(p) + ": r not in [1, 8]");
     if (q.K < 2 || q.K > kMaxK) return fail(LRQ_EINVAL, "problem " + std::to_string(p) + ": K not in [2, 64]");
-    if (q.S < 1 || q.S > kBMaxS) return fail(LRQ_EINVAL, "problem " + std::to_string(p) + ": S not in [1, 8192]");
+    if (q.S == 0) {  // exact sub-batch
+      if (q.C) return fail(LRQ_EINVAL, "problem " + std::to_string(p) + ": exact (S = 0) takes no directions");
+      int e = enumerate_check(q.n, q.r, q.K, kBEnumBudget);
+      if (e) return fail(e, "problem " + std::to_string(p) + " (exact): " + lrq_last_error());
+      if (exact_chunks(q) > (int64_t(1) << 24))
+        return fail(LRQ_EUNSUPPORTED, "problem " + std::to_string(p) + ": too many index sets");
+      continue;
+    }
+    if (q.S < 1 || q.S > kBMaxS) return fail(LRQ_EINVAL, "problem " + std::to_string(p) + ": S not in [0, 8192]");
     if (top_m > q.S) return fail(LRQ_EINVAL, "problem " + std::to_string(p) + ": top_m > S");
   }
   int dev = 0;
@@ -609,7 +781,8 @@ int lrq_batched_autotune(lrq_batched_plan* plan, void* ws, size_t ws_bytes, int3
   if ((e = cuda_check(cudaMemsetAsync(w + plan->off_epoch, 0, sizeof(int64_t), st), "reset epoch"))) return e;
   std::map<std::tuple<int, int, int>, std::vector<int>> classes;
   for (int p = 0; p < P; ++p)
-    classes[std::make_tuple(plan->probs[p].r, plan->probs[p].K, n_bucket(plan->probs[p].n))].push_back(p);
+    if (plan->probs[p].S > 0)
+      classes[std::make_tuple(plan->probs[p].r, plan->probs[p].K, n_bucket(plan->probs[p].n))].push_back(p);
   cudaEvent_t t0, t1;
   if ((e = cuda_check(cudaEventCreate(&t0), "event"))) return e;
   if ((e = cuda_check(cudaEventCreate(&t1), "event"))) {
@@ -653,6 +826,7 @@ int lrq_batched_autotune(lrq_batched_plan* plan, void* ws, size_t ws_bytes, int3
 
 int lrq_batched_tile(const lrq_batched_plan* plan, int p) {
   if (!plan || p < 0 || p >= static_cast<int>(plan->probs.size())) return -1;
+  if (plan->probs[p].S == 0) return 0;  // exact: no candidate tile
   return plan->tile[p];
 }
 

@@ -588,7 +588,8 @@ def truncate(Q: LrqMatrix, r, tol=0.0, max_iter=0, seed=0, want_c128=True, want_
 class BatchedPlan:
     """Owns an lrq_batched_plan, its workspace and outputs; keeps the problem
     tensors alive.  problems: list of dicts with V (n x r complex64, device),
-    K, and either C (S x r complex64, device) or S and seed."""
+    K, and either C (S x r complex64, device), or S and seed, or exact=True
+    (S = 0: solved exactly by vertex enumeration in the same launch)."""
 
     def __init__(self, problems, top_m=4, device="cuda", stream=None):
         self.keep = []
@@ -597,7 +598,7 @@ class BatchedPlan:
             V = q["V"]
             C = q.get("C")
             self.keep += [V, C]
-            S = C.shape[0] if C is not None else int(q["S"])
+            S = 0 if q.get("exact") else (C.shape[0] if C is not None else int(q["S"]))
             arr[i] = LrqProblem(_addr(V), V.shape[0], V.shape[1], int(q["K"]), _addr(C), S, int(q.get("seed", 0)))
         h = ctypes.c_void_p()
         _check(load().lrq_batched_plan_create(arr, len(problems), int(top_m), ctypes.byref(h)),

@@ -175,8 +175,12 @@ def test_batched_plan_rejects_bad_problems_on_host(lib):
     ok = lrq.LrqProblem(256, 100, 4, 3, None, 1000, 1)
     for bad in (lrq.LrqProblem(None, 100, 4, 3, None, 1000, 1), lrq.LrqProblem(256, 0, 4, 3, None, 1000, 1),
                 lrq.LrqProblem(256, 100, 9, 3, None, 1000, 1), lrq.LrqProblem(256, 100, 4, 1, None, 1000, 1),
-                lrq.LrqProblem(256, 100, 4, 3, None, 8193, 1), lrq.LrqProblem(256, 100, 4, 3, None, 0, 1)):
+                lrq.LrqProblem(256, 100, 4, 3, None, 8193, 1), lrq.LrqProblem(256, 40, 2, 3, 512, 0, 1)):
         assert create([ok, bad]) == 1
+    # S = 0 asks for the exact solver: outside its limits the plan is refused
+    for bad in (lrq.LrqProblem(256, 100, 4, 3, None, 0, 1), lrq.LrqProblem(256, 40, 2, 12, None, 0, 1),
+                lrq.LrqProblem(256, 600, 1, 3, None, 0, 1), lrq.LrqProblem(256, 90, 2, 3, None, 0, 1)):
+        assert create([ok, bad]) == 2
     assert create([ok], top_m=17) == 1
     assert create([ok], top_m=0) == 1
     assert lib.lrq_batched_plan_create(None, 1, 1, ctypes.byref(ctypes.c_void_p())) == 1

@@ -183,3 +183,73 @@ def test_batched_full_size_sampled(lrq):
     bi = plan.best_idx.cpu().numpy()
     _check(lrq, [probs[p] for p in pick], bf[pick], bi[pick])
     plan.close()
+
+
+def _exact_problem(n, r, K, seed):
+    V = I.factor(n, r, seed=seed, scales=np.linspace(2.0, 0.5, r), dtype=np.complex64)
+    return dict(V=torch.from_numpy(V).to(DEV), K=K, Vh=V, exact=True)
+
+
+def test_mixed_launch_exact_problems_match_bruteforce(lrq):
+    # sampled problems and exact ones (S = 0) in one persistent launch; the
+    # exact ones are small enough for the oracle's brute force over A_K^n
+    sampled = _problems(8, seed=11)
+    exact = [_exact_problem(n, r, K, 500 + i) for i, (n, r, K) in
+             enumerate([(8, 2, 3), (10, 2, 4), (12, 2, 3), (16, 2, 2), (9, 3, 2), (7, 1, 8), (7, 2, 8), (13, 2, 2)])]
+    probs = [q for pair in zip(sampled, exact) for q in pair]
+    plan = lrq.BatchedPlan(probs, top_m=4)
+    plan.run()
+    torch.cuda.synchronize()
+    lrq.check_status(plan.status, "mixed batched")
+    bf = plan.best_f.cpu().numpy()
+    bi = plan.best_idx.cpu().numpy()
+    for p, q in enumerate(probs):
+        if q.get("exact"):
+            f_bf, _ = oracle.bruteforce(q["Vh"].astype(np.complex128), q["K"])
+            assert bi[p] == -1
+            assert abs(bf[p] - f_bf) <= 1e-10 * f_bf, (p, bf[p], f_bf)
+    sp = [p for p, q in enumerate(probs) if not q.get("exact")]
+    assert plan.tile(sp[0]) in (64, 128, 256) and plan.tile(1) == 0
+    _check(lrq, [probs[p] for p in sp], bf[sp], bi[sp])
+    plan.close()
+
+
+@pytest.mark.parametrize("n,r,K", [(24, 2, 3), (33, 2, 8), (48, 2, 4), (12, 3, 3)])
+def test_exact_subbatch_equals_standalone_solver(lrq, n, r, K):
+    # the same candidates and FP64 arithmetic as lrq_enumerate (which the
+    # oracle checks), on V converted to FP64: the optimum must agree, and no
+    # sampled direction may beat it
+    q = _exact_problem(n, r, K, 900 + n)
+    other = _problems(3, seed=12, explicit_every=0)
+    plan = lrq.BatchedPlan([other[0], q, other[1], other[2]], top_m=2)
+    plan.run()
+    torch.cuda.synchronize()
+    lrq.check_status(plan.status, "mixed batched")
+    ref = lrq.enumerate_exact(q["V"].to(torch.complex128), K)
+    torch.cuda.synchronize()
+    lrq.check_status(ref["dev_status"], "lrq_enumerate")
+    f_ex = float(plan.best_f[1].item())
+    assert abs(f_ex - float(ref["f"].item())) <= 1e-12 * f_ex
+    C = I.directions(4096, r, seed=n)
+    assert oracle.score(q["Vh"], K, C).max() <= f_ex * (1 + 1e-12)
+    plan.close()
+
+
+def test_exact_subbatch_in_a_graph_replays(lrq):
+    probs = _problems(4, seed=13, explicit_every=2) + [_exact_problem(20, 2, 3, 77)]
+    stream = torch.cuda.Stream()
+    with torch.cuda.stream(stream):
+        plan = lrq.BatchedPlan(probs, top_m=2, stream=stream)
+        plan.capture()
+        plan.replay()
+        stream.synchronize()
+        f0 = float(plan.best_f[4].item())
+        plan.replay()
+        stream.synchronize()
+        f1 = float(plan.best_f[4].item())
+    lrq.check_status(plan.status, "graph")
+    assert f0 == f1  # the exact answer does not depend on the call index
+    ref = lrq.enumerate_exact(probs[4]["V"].to(torch.complex128), 3)
+    torch.cuda.synchronize()
+    assert abs(f0 - float(ref["f"].item())) <= 1e-12 * f0
+    plan.close()
