@@ -499,7 +499,7 @@ def learned_gain(dev, n, ntrain, neval, steps, hard=False):
                         "each), %d held-out" % (sig[0], sig[1], n, ntrain, neval),
             "train_steps": steps, "loss_first10": float(losses[:10].mean()), "loss_last10": float(losses[-10:].mean()),
             "data_s": t1 - t0, "train_s": t2 - t1,
-            "kernels": "BF16 MLP fwd/bwd, vMF NLL, Adam, vMF modes and sampler"}
+            "kernels": "tcgen05 BF16 MLP fwd/bwd (mlp_gemm_tc_kernel), vMF NLL, Adam, vMF modes and sampler"}
 
 
 def run_learned(args):

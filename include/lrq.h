@@ -539,8 +539,11 @@ int lrq_enumerate(const void* V, int64_t n, int r, int K, double budget, uint8_t
  *   row-major (in x out).  X: B x F; H1, H2: B x 256 (written by forward,
  *   read by backward); O: B x 160.  backward: dO (B x 160) -> grads (same
  *   layout as params), scratch: 2 B x 256 floats.  bf16 != 0 rounds every
- *   GEMM operand to bfloat16 (products accumulate in FP32).  1 <= B <=
- *   2097120 (LRQ_EUNSUPPORTED above).
+ *   GEMM operand to bfloat16 and runs the GEMMs on the tensor cores
+ *   (tcgen05, BF16 x BF16 -> FP32 in tensor memory); a bounded device wait
+ *   in that path that runs out (never observed) writes NaN into its output
+ *   tile.  bf16 == 0 computes in FP32 on the CUDA cores.  1 <= B <= 2097120
+ *   (LRQ_EUNSUPPORTED above).
  * lrq_vmf_nll: O (B x 160): per component m, outputs 10m..10m+7 give
  *   mu_m = u / ||u||, 10m+8 gives kappa_m = softplus, 10m+9 the mixture
  *   logit.  targets: B x T x 8 unit vectors.  loss_out (1 double, device):

@@ -9,7 +9,8 @@
 // flat FP32 array W1 (F x 256), b1, W2 (256 x 256), b2, W3 (256 x 160), b3,
 // each W row-major (in x out) so that a layer is y = x W + b.  In BF16 mode
 // every GEMM operand is rounded to bfloat16 (round to nearest even) as it is
-// staged in shared memory and the products accumulate in FP32.
+// staged in shared memory and the products accumulate in FP32, on the tensor
+// cores (k_mlp_tc.cu); FP32 mode runs the CUDA-core GEMM below.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -484,10 +485,15 @@ int launch_features(const float2* V, int B, int64_t n, int r, const double* lamb
   return cuda_check(cudaGetLastError(), "features_kernel");
 }
 
+// BF16 mode on the tensor cores (k_mlp_tc.cu); FP32 mode on the CUDA cores
 static void gemm(cudaStream_t st, int M, int N, int K, const float* A, int lda, int ta, const float* Bm, int ldb,
                  int tb, const float* bias, int relu, const float* mask, float* C, int ldc, int bf16) {
+  if (bf16) {
+    launch_mlp_gemm_tc(st, M, N, K, A, lda, ta, Bm, ldb, tb, bias, relu, mask, C, ldc);
+    return;
+  }
   dim3 grid(static_cast<unsigned>(ceil_div(N, 32)), static_cast<unsigned>(ceil_div(M, 32)));
-  mlp_gemm_kernel<<<grid, 256, 0, st>>>(M, N, K, A, lda, ta, Bm, ldb, tb, bias, relu, mask, C, ldc, bf16);
+  mlp_gemm_kernel<<<grid, 256, 0, st>>>(M, N, K, A, lda, ta, Bm, ldb, tb, bias, relu, mask, C, ldc, 0);
   count_launch();
 }
 

@@ -130,6 +130,9 @@ int launch_features(const float2* V, int B, int64_t n, int r, const double* lamb
                     int32_t* status, cudaStream_t st);
 int launch_mlp_forward(const float* params, int F, int B, const float* X, float* H1, float* H2, float* O, int bf16,
                        cudaStream_t st);
+// C = act(op(A) op(B) + bias) (* mask > 0), BF16 operands, FP32 accumulation, tcgen05
+void launch_mlp_gemm_tc(cudaStream_t st, int M, int N, int K, const float* A, int lda, int ta, const float* Bm,
+                        int ldb, int tb, const float* bias, int relu, const float* mask, float* C, int ldc);
 int launch_mlp_backward(const float* params, int F, int B, const float* X, const float* H1, const float* H2,
                         const float* dO, float* grads, float* scratch, int bf16, cudaStream_t st);
 int launch_vmf_nll(const float* O, int B, const float* X, int T, double* loss, float* dO, cudaStream_t st);
