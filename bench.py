@@ -3,30 +3,35 @@
 One step = one pass of the whole path over one batch of synthetic input:
 draw S uniform directions (Philox, on the GPU), score them with the
 tensor-core kernel (F16 GEMM1 projections -> sector rounding -> FP8 GEMM2
-per-class sums -> f), select the top 64, re-score those in FP64 and pick the
-winner.
+per-class sums -> f) against the instance's operands (packed once by
+lrq_prepare), select the top 64, re-score those in FP64 and pick the
+winner.  The end-to-end leg copies V in from host memory, prepares it and
+reads the winner back inside its timed region, every step.
 
 Workload: n = 2^20, r = 4, K = 3, S = 2^16 directions per step per GPU;
 V ~ CN(0,1) * diag(4, 2, 1, 0.5) in complex64 (seed 0); step s on rank g uses
 direction seed 1 + s * world + g.  Metric: candidate*n evaluations per
 second (S * n per step), whole job.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--mode bf16|fp32]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--mode tc|fp32]
                   [--workload scale|exact|maxcut|batched|learned|rank1|hybrid] [--sampler uniform|null]
 
 --impl reference times the FP64 CPU oracle on the host cores on a bounded
 sample of the same workload (same metric, unit and config).
 
 The default line (workload "scale") also carries "samples_to_best": the
-learned proposal's median S_u / S_l on held-out angular-synchronisation
-instances (n = 4096, K = 8, r = 4), trained on the GPU in the same run.
+learned proposal's median S_u / S_l on 256 held-out angular-synchronisation
+instances (n = 4096, K = 8, r = 4), trained on the GPU in the same run, with
+the fixed direction e_1 as a second baseline, at the workload's sigma and in
+a high-noise regime ("hard").
 The other workloads print one line each for the remaining paths:
   exact    n = 12, r = 2, K = 3: vertex enumeration + 4096 sampled directions
   maxcut   planted 3-partition SBM, n = 10^6: Laplacian truncation (r = 3),
-           2^17 BF16 candidates, FP64 rescore, exact cut count
-  batched  512 instances, n log-uniform in [64, 8192], r in 2..6,
-           K in {2, 3, 4, 8}: one graph-captured persistent launch
+           2^17 tensor-core-scored candidates, FP64 rescore, exact cut count
            (--sampler null: null-vector directions instead of uniform ones)
+  batched  512 instances, n log-uniform in [64, 8192], r in 2..6,
+           K in {2, 3, 4, 8}: one graph-captured persistent launch; also
+           the same launch with an exact sub-batch (--exact-subbatch)
   learned  the learned proposal at a larger training set
   rank1    SBM n = 10^6: rank-2 Laplacian truncation, the two-eigenvector
            rounding vector q = u1 + i u2, exact rank-1 sweep (Algorithm 1)
@@ -59,7 +64,7 @@ def _config(mode: str, world: int):
     return {"workload": "scale: n=2^20, r=4, K=3, S=2^16 uniform directions per GPU per step; "
                         "V ~ CN(0,1) diag(4,2,1,0.5) complex64; top-64 FP64 rescore",
             "n": N, "r": R, "K": K, "S_per_gpu": S, "top_m": TOP_M,
-            "mode": ("tensor-core (F16 signs, FP8 hi+lo class sums) + FP64 rescore" if mode == "bf16"
+            "mode": ("tensor-core (F16 signs, FP8 hi+lo class sums) + FP64 rescore" if mode == "tc"
                      else "FP32 CUDA-core + FP64 rescore"),
             "parallelism": "replicas over candidates (dp%d)" % world,
             "prepared_v": "V's operands packed once (lrq_prepare) before the device-timed steps, which score "
@@ -82,7 +87,7 @@ SCALE_TRAFFIC_BYTES = 73.10e6 + 10.76e6
 def _traffic(args):
     if args.traffic is not None:
         return args.traffic
-    if args.mode == "bf16" and args.candidates == S and args.workload == "scale":
+    if args.mode == "tc" and args.candidates == S and args.workload == "scale":
         return SCALE_TRAFFIC_BYTES
     return None
 
@@ -258,7 +263,7 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * secs / len(vals), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
-            "config": dict(_config("bf16", 1), S_per_step=sample_S),
+            "config": dict(_config("tc", 1), S_per_step=sample_S),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": vals[0]["cores"], "kind": "oracle",
                              "sample": vals[0]["sample"]},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -310,7 +315,7 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     lrq.load()
-    mode = lrq.LRQ_MODE_TC if args.mode == "bf16" else lrq.LRQ_MODE_FP32
+    mode = lrq.LRQ_MODE_TC if args.mode == "tc" else lrq.LRQ_MODE_FP32
 
     V_host = torch.from_numpy(inputs.factor(N, R, seed=0, scales=SCALES, dtype=np.complex64)).pin_memory()
     V = V_host.to(dev)
@@ -406,17 +411,17 @@ def run_ours(args):
     peak_tf, _, peak_kind = _peaks()
     flops = 16.0 * R * N * S  # two complex r-contractions per evaluation (algorithmic)
     kern_avg_s = kern_ms * 1e-3 / args.steps
-    if args.mode == "bf16":
+    if args.mode == "tc":
         roof = tc_roofline(flops, kern_avg_s, peak_tf, peak_kind)
     else:
         roof = fp32_roofline(flops, kern_avg_s)
-    roof.update({"traffic": _traffic(args), "kernel": "score_tc_kernel" if args.mode == "bf16" else "score_fp32_kernel",
+    roof.update({"traffic": _traffic(args), "kernel": "score_tc_kernel" if args.mode == "tc" else "score_fp32_kernel",
                  "kernel_ms": kern_avg_s * 1e3, "flops_per_launch": flops})
-    tc_err = score_error(V, C, ws, ws_r, mode, stream) if args.mode == "bf16" else None
+    tc_err = score_error(V, C, ws, ws_r, mode, stream) if args.mode == "tc" else None
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": step_ms / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f16+e4m3" if args.mode == "bf16" else "f32",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f16+e4m3" if args.mode == "tc" else "f32",
         "data": "synthetic", "config": _config(args.mode, world),
         "roofline": roof,
         "tc_error": tc_err,
@@ -832,7 +837,9 @@ def main():
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--mode", choices=["bf16", "fp32"], default="bf16")
+    ap.add_argument("--mode", choices=["tc", "fp32", "bf16"], default="tc",
+                    help="tc: tensor-core mode (F16 projections, FP8 hi + lo class sums); fp32: CUDA-core "
+                         "mode; bf16: deprecated alias of tc")
     ap.add_argument("--candidates", type=int, default=S,
                     help="directions per step per GPU (default 2^16; smaller only for profiling runs)")
     ap.add_argument("--cpu-sample", type=int, default=256)
@@ -852,6 +859,8 @@ def main():
     ap.add_argument("--learned-eval", type=int, default=256)
     ap.add_argument("--learned-steps", type=int, default=800)
     args = ap.parse_args()
+    if args.mode == "bf16":
+        args.mode = "tc"
     if args.impl == "reference":
         run_reference(args)
     elif args.workload == "scale":
