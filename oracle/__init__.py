@@ -110,6 +110,8 @@ def _load():
         lib.oracle_sphere_sample.restype = None
         lib.oracle_rank1_sweep.argtypes = [P, I64, I, P]
         lib.oracle_rank1_sweep.restype = D
+        lib.oracle_greedy_sequential.argtypes = [P, P, I64, I, P, I64]
+        lib.oracle_greedy_sequential.restype = I64
         _lib = lib
         return lib
 
@@ -342,6 +344,23 @@ def greedy_cut(rowptr, colidx, K: int, z, max_rounds=None):
         rounds += 1
         moves += int(mv.sum())
     return z.astype(np.uint8), rounds, moves, converged
+
+
+def greedy_sequential(rowptr, colidx, K: int, z, max_moves=None):
+    """Sequential steepest ascent from labels z: one move at a time, always the
+    vertex of largest gain (ties to the smaller index), to the smallest label
+    attaining its minimum neighbour count, until no vertex gains.  The other
+    reading of the appendix's "steepest ascent" (greedy_cut moves, per round,
+    every gaining vertex no neighbour outranks).  Returns (labels uint8,
+    moves)."""
+    rp = np.ascontiguousarray(rowptr, dtype=np.int32)
+    ci = np.ascontiguousarray(colidx, dtype=np.int32)
+    zz = np.ascontiguousarray(np.asarray(z, dtype=np.uint8).copy())
+    mv = _load().oracle_greedy_sequential(_ptr(rp), _ptr(ci), len(rp) - 1, int(K), _ptr(zz),
+                                          -1 if max_moves is None else int(max_moves))
+    if mv < 0:
+        raise ValueError("oracle_greedy_sequential rejected its arguments")
+    return zz, int(mv)
 
 
 # --------------------------------------------------------------------------

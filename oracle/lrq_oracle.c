@@ -430,3 +430,125 @@ double oracle_rank1_sweep(const double* q, int64_t n, int K, uint8_t* z_best) {
   free(k);
   return best;
 }
+
+/* --------------------------------------------------------------------------
+ * Sequential steepest ascent for Max-K-Cut (App. "Hybrid Warm-Start" names
+ * steepest ascent without fixing how moves are grouped): repeatedly take the
+ * single vertex with the largest gain g_i = n_i(z_i) - min_{c != z_i} n_i(c)
+ * (n_i(c): neighbours of i with label c over the CSR adjacency, self loops
+ * ignored, parallel edges with multiplicity; ties to the smaller index) and
+ * move it to the smallest label attaining the minimum, until no vertex gains
+ * or max_moves moves were made (max_moves < 0: no limit).  The cut rises by
+ * g_i with each move.  A binary max-heap of (gain, index) keys with lazy
+ * deletion finds the steepest vertex.  Returns the number of moves, or -1 on
+ * a label outside [0, K) or an allocation failure; z is updated in place.
+ * ------------------------------------------------------------------------ */
+static int64_t gs_key(int64_t gain, int64_t i) { return (gain << 32) | (int64_t)(0xFFFFFFFFu - (uint32_t)i); }
+
+static int gs_push(int64_t** heap, int64_t* size, int64_t* cap, int64_t key) {
+  if (*size == *cap) {
+    int64_t nc = *cap * 2 + 16;
+    int64_t* nh = (int64_t*)realloc(*heap, (size_t)nc * sizeof(int64_t));
+    if (!nh) return -1;
+    *heap = nh;
+    *cap = nc;
+  }
+  int64_t* h = *heap;
+  int64_t k = (*size)++;
+  h[k] = key;
+  while (k > 0) {
+    int64_t p = (k - 1) / 2;
+    if (h[p] >= h[k]) break;
+    int64_t t = h[p];
+    h[p] = h[k];
+    h[k] = t;
+    k = p;
+  }
+  return 0;
+}
+
+static int64_t gs_pop(int64_t* h, int64_t* size) {
+  int64_t top = h[0];
+  h[0] = h[--(*size)];
+  int64_t k = 0;
+  for (;;) {
+    int64_t l = 2 * k + 1, r = l + 1, m = k;
+    if (l < *size && h[l] > h[m]) m = l;
+    if (r < *size && h[r] > h[m]) m = r;
+    if (m == k) break;
+    int64_t t = h[m];
+    h[m] = h[k];
+    h[k] = t;
+    k = m;
+  }
+  return top;
+}
+
+static int64_t gs_gain(const int32_t* cnt, int K, int zi, int* best) {
+  int b = -1;
+  for (int c = 0; c < K; ++c)
+    if (c != zi && (b < 0 || cnt[c] < cnt[b])) b = c;
+  *best = b;
+  return (int64_t)cnt[zi] - cnt[b];
+}
+
+int64_t oracle_greedy_sequential(const int32_t* rowptr, const int32_t* colidx, int64_t n, int K, uint8_t* z,
+                                 int64_t max_moves) {
+  if (K < 2 || n < 0) return -1;
+  for (int64_t i = 0; i < n; ++i)
+    if (z[i] >= K) return -1;
+  int32_t* cnt = (int32_t*)calloc((size_t)(n > 0 ? n : 1) * K, sizeof(int32_t));
+  int64_t* gain = (int64_t*)malloc((size_t)(n > 0 ? n : 1) * sizeof(int64_t));
+  int64_t cap = n + 16, size = 0;
+  int64_t* heap = (int64_t*)malloc((size_t)cap * sizeof(int64_t));
+  if (!cnt || !gain || !heap) {
+    free(cnt);
+    free(gain);
+    free(heap);
+    return -1;
+  }
+  for (int64_t i = 0; i < n; ++i)
+    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e)
+      if (colidx[e] != i) cnt[i * K + z[colidx[e]]] += 1;
+  int64_t rc = 0;
+  for (int64_t i = 0; i < n && rc == 0; ++i) {
+    int b;
+    gain[i] = gs_gain(cnt + i * K, K, z[i], &b);
+    if (gain[i] > 0) rc = gs_push(&heap, &size, &cap, gs_key(gain[i], i));
+  }
+  int64_t moves = 0;
+  while (rc == 0 && size > 0 && (max_moves < 0 || moves < max_moves)) {
+    const int64_t key = gs_pop(heap, &size);
+    const int64_t g = key >> 32;
+    const int64_t i = 0xFFFFFFFFu - (uint32_t)(key & 0xFFFFFFFF);
+    if (g != gain[i] || g <= 0) continue;  // a stale entry
+    int b;
+    gs_gain(cnt + i * K, K, z[i], &b);
+    const int old = z[i];
+    z[i] = (uint8_t)b;
+    ++moves;
+    for (int32_t e = rowptr[i]; e < rowptr[i + 1]; ++e) {
+      const int64_t j = colidx[e];
+      if (j == i) continue;
+      cnt[j * K + old] -= 1;
+      cnt[j * K + b] += 1;
+    }
+    int bi;
+    gain[i] = gs_gain(cnt + i * K, K, z[i], &bi);
+    if (gain[i] > 0) rc = gs_push(&heap, &size, &cap, gs_key(gain[i], i));
+    for (int32_t e = rowptr[i]; e < rowptr[i + 1] && rc == 0; ++e) {
+      const int64_t j = colidx[e];
+      if (j == i) continue;
+      int bj;
+      const int64_t gj = gs_gain(cnt + j * K, K, z[j], &bj);
+      if (gj != gain[j]) {
+        gain[j] = gj;
+        if (gj > 0) rc = gs_push(&heap, &size, &cap, gs_key(gj, j));
+      }
+    }
+  }
+  free(cnt);
+  free(gain);
+  free(heap);
+  return rc == 0 ? moves : -1;
+}

@@ -110,3 +110,30 @@ def test_greedy_one_million_vertices(lrq):
     rowptr, colidx, _ = I.sbm_graph(n, 4.0, 8.0, seed=1)
     z0 = I.rng(9).integers(0, 3, n).astype(np.uint8)
     _check(lrq, rowptr, colidx, 3, z0)
+
+
+@pytest.mark.slow
+def test_hybrid_greedy_readings_at_one_million_vertices(lrq, capsys):
+    # the hybrid solver's workload (SBM n = 10^6, K = 3): from the rank-1
+    # sweep's best-cut state the GPU's parallel rounds and the oracle's
+    # sequential steepest ascent (the other reading of "steepest ascent")
+    # both end in single-move local optima; the cuts are recorded and must
+    # agree within 1%
+    n = 1_000_000
+    rowptr, colidx, _ = I.sbm_graph(n, 4.0, 8.0, seed=1)
+    rp, ci = _dev(rowptr, np.int32), _dev(colidx, np.int32)
+    tr = lrq.truncate(lrq.laplacian_matrix(rp, ci), 2, max_iter=1000, seed=0, want_c64=False)
+    q = lrq.two_eigvec_q(tr["V"], tr["lam"])
+    sw = lrq.rank1_sweep(q, 3, rp, ci)
+    torch.cuda.synchronize()
+    z0 = sw["zcut"].cpu().numpy()
+    par = _run(lrq, rowptr, colidx, 3, z0)
+    cut_par = int(par["cut"].item())
+    zs, moves = oracle.greedy_sequential(rowptr, colidx, 3, z0)
+    cut_seq = oracle.cut_count(rowptr, colidx, zs)
+    with capsys.disabled():
+        print("\nhybrid greedy at n = 10^6: start cut %d; parallel rounds %d (%d rounds, %d moves); "
+              "sequential steepest ascent %d (%d moves)" % (int(sw["cut"].item()), cut_par, par["rounds"],
+                                                            par["moves"], cut_seq, moves))
+    assert cut_par > int(sw["cut"].item()) and cut_seq > int(sw["cut"].item())
+    assert abs(cut_par - cut_seq) <= 0.01 * cut_seq

@@ -685,3 +685,58 @@ def test_rank1_sampling_probability_at_least_margin(K, n, seed):
     se = math.sqrt(measure * (1 - measure) / S)
     assert abs(hit - measure) < 5 * se + 1e-12
     assert hit >= eta - 5 * se
+
+
+def _steepest_by_scan(rowptr, colidx, K, z0):
+    # plain loops: each step scans every vertex for the largest single-move
+    # gain (ties to the smallest index) and moves it to the smallest label
+    # with the fewest neighbours; the cut must rise by exactly that gain
+    n = len(rowptr) - 1
+    z = np.asarray(z0, dtype=np.int64).copy()
+    moves = 0
+    while True:
+        best_i, best_g, best_c = -1, 0, -1
+        for i in range(n):
+            cnt = [0] * K
+            for e in range(rowptr[i], rowptr[i + 1]):
+                if colidx[e] != i:
+                    cnt[z[colidx[e]]] += 1
+            c = min((c for c in range(K) if c != z[i]), key=lambda c: (cnt[c], c))
+            g = cnt[z[i]] - cnt[c]
+            if g > best_g:
+                best_i, best_g, best_c = i, g, c
+        if best_i < 0:
+            return z.astype(np.uint8), moves
+        before = O.cut_count(rowptr, colidx, z.astype(np.uint8))
+        z[best_i] = best_c
+        assert O.cut_count(rowptr, colidx, z.astype(np.uint8)) == before + best_g
+        moves += 1
+
+
+@pytest.mark.parametrize("n,K,seed", [(60, 3, 1), (90, 2, 2), (70, 4, 3), (50, 5, 4)])
+def test_sequential_steepest_ascent_against_a_scan(n, K, seed):
+    # the heap-based sequential steepest ascent takes the same moves as a
+    # scan for the largest gain, and ends where no single move gains
+    rowptr, colidx, _ = I.sbm_graph(n, 3.0, 6.0, seed=seed)
+    z0 = I.rng(200 + seed).integers(0, K, n).astype(np.uint8)
+    z_ref, m_ref = _steepest_by_scan(rowptr, colidx, K, z0)
+    z, m = O.greedy_sequential(rowptr, colidx, K, z0)
+    assert m == m_ref and np.array_equal(z, z_ref)
+    assert _single_moves(rowptr, colidx, K, z).max() <= 0
+    # a move limit stops it early, at the same prefix of moves
+    z3, m3 = O.greedy_sequential(rowptr, colidx, K, z0, max_moves=3)
+    assert m3 == min(3, m_ref)
+
+
+def test_sequential_and_parallel_readings_both_reach_local_optima():
+    # the two readings of "steepest ascent" end in (possibly different)
+    # single-move local optima from the same start
+    rowptr, colidx, _ = I.sbm_graph(3000, 4.0, 8.0, seed=12)
+    z0 = I.rng(13).integers(0, 3, 3000).astype(np.uint8)
+    zs, ms = O.greedy_sequential(rowptr, colidx, 3, z0)
+    zp, rounds, mp, conv = O.greedy_cut(rowptr, colidx, 3, z0)
+    assert conv and ms > 0 and mp > 0
+    assert _single_moves(rowptr, colidx, 3, zs).max() <= 0
+    assert _single_moves(rowptr, colidx, 3, zp).max() <= 0
+    cs, cp = O.cut_count(rowptr, colidx, zs), O.cut_count(rowptr, colidx, zp)
+    assert abs(cs - cp) <= 0.02 * cs
