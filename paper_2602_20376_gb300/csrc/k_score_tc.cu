@@ -106,8 +106,11 @@ constexpr int kTcMaxNwg = 3;  // rounding warpgroups at most (one per D1 buffer)
 // the number of coordinates per tile.  Tensor memory (512 columns of 128
 // lanes) holds
 //   D1 : ND buffers of N1 = BKG * R columns     GEMM1 projections (F16, one per column)
-//   A2 : ND buffers of KD2 / 4 columns          GEMM2 indicator operand (4 FP8 per column), one per warpgroup
 //   D2 : 2 x NB2 buffers of N2 = 2 * NOUT cols  GEMM2 accumulators, hi | lo, NB2 per stream
+// and shared memory the GEMM2 indicator operand A2 (128 rows x KD2 FP8 bytes
+// per rounding warpgroup).  The cost of a tile is nearly fixed (its
+// hand-offs), so R is the largest that lets three D1 buffers and the
+// accumulators fit.
 template <int K, int KCH>
 struct TcShape {
   static constexpr int BK = (K % 2 == 0) ? K / 2 : K;
@@ -116,16 +119,16 @@ struct TcShape {
   // CUDA cores
   static constexpr int BKG = (K == 3) ? 2 : BK;
   static constexpr int G = (K % 2 == 0) ? K / 2 : K - 1;
-  static constexpr int R = K == 2 ? 128 : (K == 3 || K == 4) ? 64 : K == 7 ? 16 : 32;
+  static constexpr int R = K == 2 ? 128 : (K == 3 || K == 4) ? (KCH == 1 ? 80 : 64) : K == 7 ? 16 : 32;
   static constexpr int ROWS = R;  // coordinates per tile (packing granularity)
   static constexpr int N1 = BKG * R;   // GEMM1 N
   static constexpr int KD2 = G * R;    // GEMM2 reduction length per tile
-  static constexpr int A2COLS = KD2 / 4;
+  static constexpr int A2WORDS = KD2 / 4;  // indicator words (4 FP8 each) per candidate row
   static constexpr int NOUT = KCH == 1 ? 8 : 16;  // real outputs per candidate (>= 2r)
   static constexpr int N2 = 2 * NOUT;             // GEMM2 N: hi and lo halves
-  // D1 and A2 buffers (one each per rounding warpgroup) and accumulators
-  // per stream: the deepest that fit, D1 first
-  static constexpr int cols(int nd, int nb2) { return nd * (N1 + A2COLS) + 2 * nb2 * N2; }
+  // D1 buffers (one per rounding warpgroup) and accumulators per stream:
+  // the deepest that fit, D1 first
+  static constexpr int cols(int nd, int nb2) { return nd * N1 + 2 * nb2 * N2; }
   static constexpr int ND = cols(3, 1) <= 512 ? 3 : 2;
   // rounding warpgroups: warpgroup w owns D1 buffer w, so that every
   // barrier of the pipeline is waited for by one party, phase after phase
@@ -134,17 +137,16 @@ struct TcShape {
   static constexpr int NWG = ND;
   static constexpr int NB2 = cols(ND, 2) <= 512 ? 2 : 1;
   static constexpr int D1_OFF = 0;
-  static constexpr int A2_OFF = ND * N1;
-  static constexpr int D2_OFF = A2_OFF + NWG * A2COLS;
+  static constexpr int D2_OFF = ND * N1;
   static constexpr int TMEM_COLS = D2_OFF + 2 * NB2 * N2;
   static_assert(TMEM_COLS <= 512, "TMEM budget");
   static_assert(N1 % 16 == 0 && N1 <= 256, "GEMM1 N");
   static_assert(KD2 % 32 == 0, "GEMM2 K (FP8 MMAs reduce 32 entries)");
   static_assert(R % 16 == 0 && R <= 128, "rows are processed 16 at a time; magnitudes fit one 256-byte row");
-  static_assert(A2COLS % 8 == 0, "indicator words are stored 8 columns at a time");
-  // coordinates per tensor-memory load: 32 (x16 packed loads) unless the
-  // lines of 32 coordinates would not fit the rounding thread's registers
-  static constexpr int RC = (R >= 32 && BKG * 16 <= 64) ? 32 : 16;
+  // coordinates per tensor-memory load: 32 (x16 packed loads) when they
+  // divide the tile and the lines of 32 coordinates fit the rounding
+  // thread's registers, else 16
+  static constexpr int RC = (R % 32 == 0 && BKG * 16 <= 64) ? 32 : 16;
   // a warpgroup's tiles per accumulation period
   static constexpr int FLUSH = kTcPeriodCoords / R;
   // warps: NWG rounding warpgroups, the fold warpgroup, TMA, GEMM1, two GEMM2
@@ -173,18 +175,23 @@ struct TcLayout {
   static constexpr int STAGE_BYTES = TILE_BYTES;          // a multiple of 256: TMA destinations stay aligned
   static constexpr uint32_t STAGE_TX = TILE_BYTES;
   static constexpr int A1_BYTES = kTcM * 16 * KCH;
+  // GEMM2's A operand per rounding warpgroup: 128 rows x KD2 E4M3 bytes,
+  // K-major core matrices (chunk of 16 along K, then the 128 rows, 16 bytes each)
+  static constexpr int A2S_BYTES = kTcM * Sh::KD2;
   static constexpr int ZERO_BYTES = 4096;
   static constexpr int NBARS = 2 * kTcMaxStages + 2 + 2 + 2 * 3 + 3 * kTcMaxNwg + 4 + 4 + 3;
-  static constexpr int FIXED = 2 * A1_BYTES + ZERO_BYTES + NBARS * 8 + 64;
+  static constexpr int FIXED = 2 * A1_BYTES + Sh::NWG * A2S_BYTES + ZERO_BYTES + NBARS * 8 + 64 + 1024;
   // at least 120 KB of shared memory, so that two CTAs never share an SM
-  // (each holds all 512 TMEM columns); the stage ring takes what is left
-  static constexpr int NS_FIT = (120 * 1024 - FIXED) / STAGE_BYTES;
+  // (each holds all 512 TMEM columns); the stage ring takes what is left of
+  // 200 KB
+  static constexpr int NS_FIT = (200 * 1024 - FIXED) / STAGE_BYTES;
   static constexpr int NS = NS_FIT < kTcMaxStages ? NS_FIT : kTcMaxStages;
   static_assert(NS >= 4, "pipeline depth");
   static constexpr int DIRS_OFF = NS * STAGE_BYTES;
+  static constexpr int A2S_OFF = (DIRS_OFF + 2 * A1_BYTES + 1023) / 1024 * 1024;
   // the zero region lies above every operand: the descriptors' K-direction
   // byte offsets (LBO) to it are positive
-  static constexpr int ZERO_OFF = DIRS_OFF + 2 * A1_BYTES;
+  static constexpr int ZERO_OFF = A2S_OFF + Sh::NWG * A2S_BYTES;
   static constexpr int BAR_OFF = ZERO_OFF + ZERO_BYTES;
   static constexpr int USED = BAR_OFF + NBARS * 8 + 64;
   static constexpr int TOTAL = USED < 120 * 1024 ? 120 * 1024 : USED;
@@ -476,11 +483,12 @@ __global__ void __maxnreg__(96)
         if (!ok) break;
         ptx::tc_fence_after();
         const uint32_t b2 = smem_base + st.idx * L::STAGE_BYTES + L::B2_OFF_IN_STAGE;
-        const uint32_t a2t = tmem + Sh::A2_OFF + w * Sh::A2COLS;
+        // A2 of warpgroup w in shared memory: K chunks of 16 bytes, 128 rows each
+        const uint32_t a2s = smem_base + L::A2S_OFF + w * L::A2S_BYTES;
 #pragma unroll
         for (int q = 0; q < Sh::KD2 / 32; ++q)
-          ptx::mma_e4m3_ts_elect(d2 + pb * Sh::N2, a2t + q * 8, ptx::smem_desc(b2 + q * 2 * lbo_b2, lbo_b2, 128),
-                                 idesc2, (q > 0 || !first) ? 1u : 0u);
+          ptx::mma_e4m3_ss_elect(d2 + pb * Sh::N2, ptx::smem_desc(a2s + q * 2 * kTcM * 16, kTcM * 16, 128),
+                                 ptx::smem_desc(b2 + q * 2 * lbo_b2, lbo_b2, 128), idesc2, (q > 0 || !first) ? 1u : 0u);
         ptx::mma_commit_elect(&a2empty[w]);
         ptx::mma_commit_elect(&sempty[st.idx]);
         if (last) {
@@ -577,7 +585,8 @@ __global__ void __maxnreg__(96)
     const int wg = warp >> 2;
     const int q = warp & 3;
     const uint32_t lane_base = static_cast<uint32_t>(q * 32) << 16;
-    const uint32_t a2_tmem = tmem + lane_base + Sh::A2_OFF + wg * Sh::A2COLS;
+    // this warpgroup's A2 in shared memory; thread row q * 32 + lane
+    uint8_t* const a2s_row = smem + L::A2S_OFF + wg * L::A2S_BYTES + (q * 32 + lane) * 16;
     constexpr int NCH = R / RC;
     Ring<ND> d1;
     Ring<NS> st;
@@ -660,11 +669,14 @@ __global__ void __maxnreg__(96)
         if (g >= NWG) ok = warp_wait(&a2empty[wg], a2ph ^ 1u, abort_flag);
         if (!ok) break;
         ptx::tc_fence_after();
+        // words w .. w + 3 of a class (16 coordinates) are one 16-byte chunk of
+        // the row; chunk c of all 128 rows lies at c * 128 * 16
 #pragma unroll
-        for (int cc = 0; cc < Sh::A2COLS / 8; ++cc)
-          ptx::tmem_st_x8(a2_tmem + cc * 8, *reinterpret_cast<const uint32_t(*)[8]>(&wv[cc * 8]));
-        ptx::tmem_wait_st();
-        ptx::tc_fence_before();
+        for (int cc = 0; cc < Sh::A2WORDS / 4; ++cc)
+          *reinterpret_cast<uint4*>(a2s_row + cc * kTcM * 16) =
+              make_uint4(wv[4 * cc], wv[4 * cc + 1], wv[4 * cc + 2], wv[4 * cc + 3]);
+        // the stores, visible to the tensor core's operand reads
+        ptx::fence_proxy_async_smem();
         __syncwarp();
         if (lane == 0) ptx::mbar_arrive(&a2full[2 * wg + (g & 1)]);
         a2ph ^= 1u;
@@ -1031,8 +1043,8 @@ static int score_impl(const ScorePlan& p, const void* tiles, const void* ct, con
     }                                                              \
   } while (0)
 
-int tc_rows_per_tile(int K) {
-  const bool two = false;
+int tc_rows_per_tile(int K, int r) {
+  const bool two = r > 4;
 #define LRQ_ROWS(k, c) TcShape<k, c>::ROWS
   LRQ_TC_SHAPE_SWITCH(LRQ_ROWS);
 #undef LRQ_ROWS
@@ -1051,8 +1063,8 @@ size_t tc_bytes_tiles(int K, int r, int64_t n_tiles) {
 #undef LRQ_TILE
 }
 
-size_t tc_bytes_indicator_scale(int K, int64_t n_tiles) {
-  return static_cast<size_t>(n_tiles) * static_cast<size_t>(tc_rows_per_tile(K));  // one byte per coordinate
+size_t tc_bytes_indicator_scale(int K, int r, int64_t n_tiles) {
+  return static_cast<size_t>(n_tiles) * static_cast<size_t>(tc_rows_per_tile(K, r));  // one byte per coordinate
 }
 
 size_t tc_bytes_dirs(int r, int64_t c_tiles) {

@@ -18,10 +18,10 @@
 
 namespace lrq {
 
-int tc_rows_per_tile(int K);
+int tc_rows_per_tile(int K, int r);
 int tc_workers_per_cta(int K, int r);
 size_t tc_bytes_tiles(int K, int r, int64_t n_tiles);
-size_t tc_bytes_indicator_scale(int K, int64_t n_tiles);
+size_t tc_bytes_indicator_scale(int K, int r, int64_t n_tiles);
 size_t tc_bytes_dirs(int r, int64_t c_tiles);
 
 static thread_local char g_last_error[512] = {0};
@@ -121,7 +121,7 @@ int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_
   p->c_tiles = ceil_div(S, 128);
   const int64_t S_pad = p->c_tiles * 128;
   if (mode == LRQ_MODE_BF16_TC) {
-    p->rows_per_tile = tc_rows_per_tile(K);
+    p->rows_per_tile = tc_rows_per_tile(K, r);
     p->n_tiles = ceil_div(n, p->rows_per_tile);
     // coordinate chunks: balance (chunk, candidate tile) items over the
     // workers (num_sms CTAs x workers per CTA); of the splits within 1% of
@@ -176,7 +176,7 @@ int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_
     if (with_prep) {
       p->sz_scale = 4 * sizeof(float);
       p->off_scale = take(cur, p->sz_scale);
-      p->sz_iw = tc_bytes_indicator_scale(K, p->n_tiles);
+      p->sz_iw = tc_bytes_indicator_scale(K, r, p->n_tiles);
       p->off_iw = take(cur, p->sz_iw);
     }
   }
@@ -191,13 +191,13 @@ int plan_score(int64_t n, int r, int K, int64_t S, int mode, int top_m, int num_
 int plan_prepare(int64_t n, int r, int K, int mode, PrepLayout* L) {
   std::memset(L, 0, sizeof(*L));
   if (mode != LRQ_MODE_BF16_TC) return LRQ_OK;  // the FP32 path reads V itself
-  L->n_tiles = ceil_div(n, tc_rows_per_tile(K));
+  L->n_tiles = ceil_div(n, tc_rows_per_tile(K, r));
   size_t cur = 0;
   L->off_T = take(cur, 2 * kMaxRank * sizeof(double));
   L->off_Tpart = take(cur, 256 * 2 * kMaxRank * sizeof(double));
   L->off_tiles = take(cur, tc_bytes_tiles(K, r, L->n_tiles));
   L->off_scale = take(cur, 4 * sizeof(float));
-  L->off_iw = take(cur, tc_bytes_indicator_scale(K, L->n_tiles));
+  L->off_iw = take(cur, tc_bytes_indicator_scale(K, r, L->n_tiles));
   L->total = cur;
   return LRQ_OK;
 }
