@@ -81,7 +81,7 @@ def _config(mode: str, world: int):
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
 #       -k regex:score_tc -s 1 -c 1 python bench.py --steps 1 --warmup 1 --no-cpu-baseline --no-learned
 # (one pass); it must be taken again whenever the kernel changes.
-SCALE_TRAFFIC_BYTES = 73.10e6 + 10.76e6
+SCALE_TRAFFIC_BYTES = 71.58e6 + 10.32e6
 
 
 def _traffic(args):
