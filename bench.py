@@ -74,21 +74,22 @@ def _config(mode: str, world: int):
 
 # DRAM bytes (read + write) of one score_tc_kernel launch of the default scale
 # workload (n = 2^20, r = 4, K = 3, S = 2^16, tensor-core mode), from a one-pass
-# ncu capture of the launch after the L2 flush: 73.10 MB read (one pass over
-# the packed coordinate tiles and the directions; candidate tiles that reuse
-# a coordinate tile find it in L2) + 10.76 MB written (the FP64 partial sums,
-# S x 2r doubles per coordinate chunk).  Measured with
+# ncu capture of the launch after the L2 flush: reads are one pass over the
+# packed coordinate tiles and the directions (candidate tiles that reuse a
+# coordinate tile find it in L2), writes the FP64 partial sums (S x 2r doubles
+# per coordinate chunk).  Measured with
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
 #       -k regex:score_tc -s 1 -c 1 python bench.py --steps 1 --warmup 1 --no-cpu-baseline --no-learned
-# (one pass); it must be taken again whenever the kernel changes.
-SCALE_TRAFFIC_BYTES = 71.58e6 + 10.32e6
+# (one pass); it must be taken again whenever the kernel changes, and is None
+# (reported as null) until it has been.
+SCALE_TRAFFIC_BYTES = None
 
 
 def _traffic(args):
     if args.traffic is not None:
         return args.traffic
     if args.mode == "tc" and args.candidates == S and args.workload == "scale":
-        return SCALE_TRAFFIC_BYTES
+        return SCALE_TRAFFIC_BYTES  # None until measured for the current kernel
     return None
 
 

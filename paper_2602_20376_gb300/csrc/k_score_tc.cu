@@ -63,11 +63,13 @@
 //                 phase);
 //   rounding      NWG = ND warpgroups, one thread per candidate row;
 //                 warpgroup w = g % NWG takes tile g and owns D1 buffer w
-//                 and A2 buffer w: one wait, reads the indicator
-//                 magnitudes from the tile's stage, loads D1, releases the
-//                 buffer at once, turns the projections into indicator words
-//                 and stores them into its own A2 buffer (three warpgroups
-//                 hide the latency of their waits);
+//                 and A2 buffer w: one wait, then D1 chunk by chunk (16 or
+//                 32 coordinates), the next chunk's tensor-memory load in
+//                 flight while the current one is rounded with its indicator
+//                 magnitudes (read from the tile's stage); the buffer is
+//                 released once its last chunk is in registers, and the
+//                 indicator words go into the warpgroup's own A2 buffer
+//                 (three warpgroups hide the latency of their waits);
 //   fold          a warpgroup that owns the two-sum partials: per item it
 //                 reads period i of stream 0, then period i of stream 1, for
 //                 i = 0, 1, ..., releases each accumulator, and writes the
@@ -312,7 +314,12 @@ __global__ void __maxnreg__(96)
   constexpr int NWG = Sh::NWG;
 
   extern __shared__ __align__(1024) uint8_t smem[];
-  const int warp = threadIdx.x >> 5;
+  // the warp index read through a shuffle from lane 0: the compiler then
+  // knows it is the same on every lane, so each role's branch is warp-uniform
+  // and the per-tile bookkeeping (ring positions, tile and item counters,
+  // barrier and operand addresses) runs on the uniform datapath instead of
+  // taking 32 lanes of the ALU pipe that the rounding needs
+  const int warp = __shfl_sync(0xffffffffu, static_cast<int>(threadIdx.x >> 5), 0);
   const int lane = threadIdx.x & 31;
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + L::BAR_OFF);
   uint64_t* sfull = bars;                     // [NS]  stage landed (TMA)
@@ -605,40 +612,55 @@ __global__ void __maxnreg__(96)
         ok = warp_wait(&d1full[d1.idx], d1.ph, abort_flag);
         if (!ok) break;
         ptx::tc_fence_after();
-        uint32_t mag[CW];
-        {
-          const uint4* mp = reinterpret_cast<const uint4*>(smem + st.idx * L::STAGE_BYTES + L::MAG_OFF_IN_STAGE);
-#pragma unroll
-          for (int v4 = 0; v4 < CW / 4; ++v4) {
-            const uint4 m4 = mp[v4];
-            mag[4 * v4] = m4.x;
-            mag[4 * v4 + 1] = m4.y;
-            mag[4 * v4 + 2] = m4.z;
-            mag[4 * v4 + 3] = m4.w;
-          }
-        }
+        const uint32_t* const magp =
+            reinterpret_cast<const uint32_t*>(smem + st.idx * L::STAGE_BYTES + L::MAG_OFF_IN_STAGE);
         const uint32_t d1_tmem = tmem + lane_base + Sh::D1_OFF + d1.idx * Sh::N1;
         uint32_t wv[G * CW];
         // D1 holds F16 projections, one per column; a packed load gives two
         // coordinates per register, so one byte permute gathers the signs of
         // four coordinates
-#pragma unroll
-        for (int ch = 0; ch < NCH; ++ch) {
-          uint32_t pl[BKG][RC / 2];
+        // chunk ch + 1 is loaded while chunk ch is rounded (two register sets)
+        uint32_t pl2[2][BKG][RC / 2];
+        auto load_chunk = [&](int ch, uint32_t (&dst)[BKG][RC / 2]) {
 #pragma unroll
           for (int b = 0; b < BKG; ++b) {
             const uint32_t ta = d1_tmem + b * R + ch * RC;
             if constexpr (RC == 32)
-              ptx::tmem_ld_x16_pack16(ta, *reinterpret_cast<uint32_t(*)[16]>(pl[b]));
+              ptx::tmem_ld_x16_pack16(ta, *reinterpret_cast<uint32_t(*)[16]>(dst[b]));
             else
-              ptx::tmem_ld_x8_pack16(ta, *reinterpret_cast<uint32_t(*)[8]>(pl[b]));
+              ptx::tmem_ld_x8_pack16(ta, *reinterpret_cast<uint32_t(*)[8]>(dst[b]));
           }
+        };
+        // after tcgen05.wait::ld: the registers a load wrote are tied to the
+        // wait, so no use of them is scheduled above it
+        auto loaded = [&](uint32_t (&dst)[BKG][RC / 2]) {
           ptx::tmem_wait_ld();
-          if (ch == NCH - 1) {
-            // every projection of the tile is in registers: release D1
-            ptx::tc_fence_before();
-            __syncwarp();
-            if (lane == 0) ptx::mbar_arrive(&d1empty[d1.idx]);
+#pragma unroll
+          for (int b = 0; b < BKG; ++b)
+#pragma unroll
+            for (int i = 0; i < RC / 2; ++i) asm volatile("" : "+r"(dst[b][i]));
+        };
+        auto release_d1 = [&]() {
+          // every projection of the tile is in registers: release D1
+          ptx::tc_fence_before();
+          __syncwarp();
+          if (lane == 0) ptx::mbar_arrive(&d1empty[d1.idx]);
+        };
+        load_chunk(0, pl2[0]);
+        loaded(pl2[0]);
+        if (NCH == 1) release_d1();
+#pragma unroll
+        for (int ch = 0; ch < NCH; ++ch) {
+          uint32_t (&pl)[BKG][RC / 2] = pl2[ch & 1];
+          if (ch + 1 < NCH) load_chunk(ch + 1, pl2[(ch + 1) & 1]);
+          uint32_t mag[RC / 4];
+#pragma unroll
+          for (int v4 = 0; v4 < RC / 16; ++v4) {
+            const uint4 m4 = reinterpret_cast<const uint4*>(magp + ch * (RC / 4))[v4];
+            mag[4 * v4] = m4.x;
+            mag[4 * v4 + 1] = m4.y;
+            mag[4 * v4 + 2] = m4.z;
+            mag[4 * v4 + 3] = m4.w;
           }
 #pragma unroll
           for (int pq = 0; pq < RC / 4; ++pq) {
@@ -659,10 +681,14 @@ __global__ void __maxnreg__(96)
 #pragma unroll
             for (int gc = 0; gc < G; ++gc) {
               if constexpr (K % 2 == 1)
-                wv[gc * CW + wi] = ~nm[gc] & nm[gc + 1] & mag[wi];  // p_{k-1} > 0 and p_k < 0
+                wv[gc * CW + wi] = ~nm[gc] & nm[gc + 1] & mag[pq];  // p_{k-1} > 0 and p_k < 0
               else
-                wv[gc * CW + wi] = (nm[gc] & 0x80808080u) | mag[wi];  // sign(p_m) as +-1
+                wv[gc * CW + wi] = (nm[gc] & 0x80808080u) | mag[pq];  // sign(p_m) as +-1
             }
+          }
+          if (ch + 1 < NCH) {
+            loaded(pl2[(ch + 1) & 1]);
+            if (ch + 1 == NCH - 1) release_d1();
           }
         }
         // the GEMM2 that read this warpgroup's A2 buffer last (its previous tile) is done

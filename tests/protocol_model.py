@@ -15,9 +15,10 @@ the programs the warps of one CTA of the tensor-core scoring kernel run:
   g % 2 == v and waits for A2-full barrier [g % NWG][v] (one per warpgroup
   and stream, so that each is waited for by one stream, phase after phase);
 * NWG = ND rounding warpgroups (four warps each): warpgroup w = g % NWG owns
-  D1 buffer w; it waits for D1 of tile g, reads the indicator magnitudes
-  from the tile's stage, loads D1, releases the buffer, rounds, and stores
-  the indicator operand into its own A2 buffer;
+  D1 buffer w; it waits for D1 of tile g, loads D1 chunk by chunk, releases
+  the buffer once the last chunk is in registers, reads the indicator
+  magnitudes from the tile's stage chunk by chunk (the last ones after the
+  release), rounds, and stores the indicator operand into its own A2 buffer;
 * GEMM2 of tile g (MMA warp g % 2) reads A2[g % NWG] and accumulates into
   the stream's accumulator D2[v][p % NB2], p the index of the tile's
   accumulation period among stream v's periods (a period is at most F of the
@@ -345,13 +346,17 @@ class Cta:
             st = self.stage[g % self.ns]
             if g not in self.stage_seen or st != (g, True):
                 raise ProtocolError("%r reads magnitudes of tile %d from stage holding %r" % (who, g, st))
-            self.mag_read.setdefault(g, set()).add(who)
             if self.d1[d] != g:
                 raise ProtocolError("%r reads D1[%d] holding tile %r, wants %d" % (who, d, self.d1[d], g))
             self.d1_read.setdefault(g, set()).add(who)
             if self.mut != "release_early":
                 self.d1empty[d].arrive()
             yield ("step",)  # the rounding itself
+            # the last chunk's magnitudes are read after the release
+            st = self.stage[g % self.ns]
+            if st != (g, True):
+                raise ProtocolError("%r reads magnitudes of tile %d from stage holding %r" % (who, g, st))
+            self.mag_read.setdefault(g, set()).add(who)
             prev = g - self.nwg
             if prev >= 0 and self.mut != "no_a2_wait":
                 ok = yield self._wait(who, self.a2empty[wg], g // self.nwg - 1)
