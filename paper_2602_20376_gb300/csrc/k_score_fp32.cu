@@ -18,18 +18,20 @@ namespace lrq {
 __global__ void sample_directions_kernel(uint64_t seed, int64_t S, int r, float2* __restrict__ C) {
   int64_t s = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
   if (s >= S) return;
+  // each component is drawn once and kept (r <= kMaxRank)
+  double a[kMaxRank], b[kMaxRank];
   double nrm2 = 0.0;
-  for (int j = 0; j < r; ++j) {
-    double a, b;
-    sphere_component(seed, s, j, &a, &b);
-    nrm2 += a * a + b * b;
+#pragma unroll
+  for (int j = 0; j < kMaxRank; ++j) {
+    if (j < r) {
+      sphere_component(seed, s, j, &a[j], &b[j]);
+      nrm2 += a[j] * a[j] + b[j] * b[j];
+    }
   }
   double inv = 1.0 / sqrt(nrm2);
-  for (int j = 0; j < r; ++j) {
-    double a, b;
-    sphere_component(seed, s, j, &a, &b);
-    C[s * r + j] = make_float2(static_cast<float>(a * inv), static_cast<float>(b * inv));
-  }
+#pragma unroll
+  for (int j = 0; j < kMaxRank; ++j)
+    if (j < r) C[s * r + j] = make_float2(static_cast<float>(a[j] * inv), static_cast<float>(b[j] * inv));
 }
 
 int launch_sample_directions(uint64_t seed, int64_t S, int r, float2* C, cudaStream_t st) {
