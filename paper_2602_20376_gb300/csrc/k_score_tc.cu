@@ -446,9 +446,8 @@ __global__ void __maxnreg__(96)
         ptx::tc_fence_after();
         const uint32_t b1 = smem_base + st.idx * L::STAGE_BYTES + L::B1_OFF_IN_STAGE;
         const uint32_t lbo_b1 = KCH == 2 ? Sh::N1 * 16u : (smem_base + L::ZERO_OFF - b1);
-        ptx::mma_f16_ss_elect(tmem + Sh::D1_OFF + d1.idx * Sh::N1, adesc, ptx::smem_desc(b1, lbo_b1, 128), idesc1,
-                              0u);
-        ptx::mma_commit_elect(&d1full[d1.idx]);
+        ptx::mma_f16_ss_commit(tmem + Sh::D1_OFF + d1.idx * Sh::N1, adesc, ptx::smem_desc(b1, lbo_b1, 128), idesc1,
+                               &d1full[d1.idx]);
         st.next();
         d1.next();
       }
@@ -492,14 +491,26 @@ __global__ void __maxnreg__(96)
         const uint32_t b2 = smem_base + st.idx * L::STAGE_BYTES + L::B2_OFF_IN_STAGE;
         // A2 of warpgroup w in shared memory: K chunks of 16 bytes, 128 rows each
         const uint32_t a2s = smem_base + L::A2S_OFF + w * L::A2S_BYTES;
+        if constexpr (Sh::KD2 / 32 == 5) {
+          uint64_t da[5], db[5];
 #pragma unroll
-        for (int q = 0; q < Sh::KD2 / 32; ++q)
-          ptx::mma_e4m3_ss_elect(d2 + pb * Sh::N2, ptx::smem_desc(a2s + q * 2 * kTcM * 16, kTcM * 16, 128),
-                                 ptx::smem_desc(b2 + q * 2 * lbo_b2, lbo_b2, 128), idesc2, (q > 0 || !first) ? 1u : 0u);
-        ptx::mma_commit_elect(&a2empty[w]);
-        ptx::mma_commit_elect(&sempty[st.idx]);
+          for (int q = 0; q < 5; ++q) {
+            da[q] = ptx::smem_desc(a2s + q * 2 * kTcM * 16, kTcM * 16, 128);
+            db[q] = ptx::smem_desc(b2 + q * 2 * lbo_b2, lbo_b2, 128);
+          }
+          ptx::mma_e4m3_ss_x5_commit(d2 + pb * Sh::N2, da, db, idesc2, first ? 0u : 1u, &a2empty[w], &sempty[st.idx],
+                                     &d2full[v * 2 + pb], last ? 1u : 0u);
+        } else {
+#pragma unroll
+          for (int q = 0; q < Sh::KD2 / 32; ++q)
+            ptx::mma_e4m3_ss_elect(d2 + pb * Sh::N2, ptx::smem_desc(a2s + q * 2 * kTcM * 16, kTcM * 16, 128),
+                                   ptx::smem_desc(b2 + q * 2 * lbo_b2, lbo_b2, 128), idesc2,
+                                   (q > 0 || !first) ? 1u : 0u);
+          ptx::mma_commit_elect(&a2empty[w]);
+          ptx::mma_commit_elect(&sempty[st.idx]);
+          if (last) ptx::mma_commit_elect(&d2full[v * 2 + pb]);
+        }
         if (last) {
-          ptx::mma_commit_elect(&d2full[v * 2 + pb]);
           ++p;
           pos = 0;
         } else {

@@ -202,6 +202,48 @@ __device__ __forceinline__ void mma_e4m3_ss_elect(uint32_t d_tmem, uint64_t a_de
       : "memory");
 }
 
+// Five kind::f8f6f4 MMAs (A and B from shared memory) into one accumulator,
+// then two or three commits, all issued by one lane that a single
+// elect.sync picks: the warp stays converged and pays one election per tile.
+// The first MMA accumulates when `acc0` is non-zero, the others always; the
+// third commit goes out only when `third` is non-zero.
+__device__ __forceinline__ void mma_e4m3_ss_x5_commit(uint32_t d_tmem, const uint64_t (&a)[5], const uint64_t (&b)[5],
+                                                      uint32_t idesc, uint32_t acc0, uint64_t* bar1, uint64_t* bar2,
+                                                      uint64_t* bar3, uint32_t third) {
+  asm volatile(
+      "{\n\t.reg .pred e, p0, t, c3;\n\t"
+      "elect.sync _|e, 0xffffffff;\n\t"
+      "setp.ne.b32 p0, %12, 0;\n\t"
+      "setp.eq.b32 t, %12, %12;\n\t"
+      "setp.ne.b32 c3, %16, 0;\n\t"
+      "and.pred c3, c3, e;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %6, %11, p0;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %2, %7, %11, t;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %3, %8, %11, t;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %4, %9, %11, t;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %5, %10, %11, t;\n\t"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%13];\n\t"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%14];\n\t"
+      "@c3 tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%15];\n\t}" ::"r"(d_tmem),
+      "l"(a[0]), "l"(a[1]), "l"(a[2]), "l"(a[3]), "l"(a[4]), "l"(b[0]), "l"(b[1]), "l"(b[2]), "l"(b[3]), "l"(b[4]),
+      "r"(idesc), "r"(acc0), "r"(smem_u32(bar1)), "r"(smem_u32(bar2)), "r"(smem_u32(bar3)), "r"(third)
+      : "memory");
+}
+
+// One kind::f16 MMA (A and B from shared memory, no accumulation) and its
+// commit, issued by one lane under a single elect.sync.
+__device__ __forceinline__ void mma_f16_ss_commit(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc, uint32_t idesc,
+                                                  uint64_t* bar) {
+  asm volatile(
+      "{\n\t.reg .pred e, z;\n\t"
+      "elect.sync _|e, 0xffffffff;\n\t"
+      "setp.ne.b32 z, %3, %3;\n\t"
+      "@e tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, z;\n\t"
+      "@e tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%4];\n\t}" ::"r"(d_tmem),
+      "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(smem_u32(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void mma_e4m3_ts_elect(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc, uint32_t idesc,
                                                   uint32_t accumulate) {
   asm volatile(
