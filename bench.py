@@ -80,9 +80,9 @@ def _config(mode: str, world: int):
 # per coordinate chunk).  Measured with
 #   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum --clock-control none \
 #       -k regex:score_tc -s 1 -c 1 python bench.py --steps 1 --warmup 1 --no-cpu-baseline --no-learned
-# (one pass): 72.19 MB read + 9.95 MB written.  It must be taken again whenever
+# (one pass): 72.20 MB read + 10.41 MB written.  It must be taken again whenever
 # the kernel changes, and set to None (reported as null) until it has been.
-SCALE_TRAFFIC_BYTES = 72.19e6 + 9.95e6
+SCALE_TRAFFIC_BYTES = 72.20e6 + 10.41e6
 
 
 def _traffic(args):
